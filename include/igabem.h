@@ -1,0 +1,158 @@
+/*
+ * igabem.h -- C ABI of the GB300 isogeometric boundary element library for acoustic scattering.
+ *
+ * The library solves the combined field integral equations of Doelz, Harbrecht and Multerer,
+ * "Solving acoustic scattering problems by the isogeometric boundary element method" (2023):
+ *
+ *   sound-soft  (1/2 + K' - i eta V) du/dn = du_inc/dn - i eta u_inc           (Sec. 2, eq. D2N)
+ *   sound-hard  (1/2 - K  - i eta W) u     = u_inc     - i eta du_inc/dn       (Sec. 4.1, eq. CFIEN2D)
+ *
+ * discretised by Galerkin's method on spline spaces over NURBS patches (Sec. 3), with the
+ * hypersingular operator in Maue's regularised form (Sec. 4.3), the matrix-vector product applied by
+ * an interpolation (black-box) fast multipole method on the reference domain (Sec. 4.4), the systems
+ * solved by restarted GMRES (Sec. 5.1), and the far-field pattern u_inf (Sec. 1) of the result.
+ *
+ * Conventions (all entry points):
+ *   - time dependence exp(-i omega t): G(x,y) = exp(i kappa |x-y|) / (4 pi |x-y|);
+ *     u_inc(x) = exp(i kappa d.x) with |d| = 1;
+ *   - normals d_s F x d_t F point out of the scatterer (the caller's patches must be oriented so);
+ *   - complex numbers are pairs of doubles (re, im), i.e. C99 double _Complex / numpy complex128;
+ *   - a block of R vectors of length N is stored row-major as [N][R] (the R values of one degree of
+ *     freedom are contiguous);
+ *   - array arguments may point to host memory or to device memory of the context's device (the
+ *     library asks the CUDA driver which); host arrays are copied, device arrays are used in place;
+ *   - unless stated otherwise, inputs are copied and the caller keeps ownership of every array;
+ *     handles are owned by the library until the matching *_destroy call;
+ *   - every entry point returns IGABEM_OK (0) or a negative error code and, on error, leaves a
+ *     message for igabem_last_error() of the calling thread; outputs are then unspecified;
+ *   - calls on one context are not thread safe; work is issued on the context's stream and every
+ *     entry point returns after that work has finished, unless stated otherwise.
+ */
+#ifndef IGABEM_H
+#define IGABEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGABEM_OK 0
+#define IGABEM_EINVAL (-1)          /* invalid argument */
+#define IGABEM_ENOMEM (-2)          /* device memory exhausted or admission refused */
+#define IGABEM_ECUDA (-3)           /* a CUDA call failed */
+#define IGABEM_ENOT_CONVERGED (-4)  /* GMRES stopped at max_iter; the density is still written */
+#define IGABEM_ENUMERIC (-5)        /* NaN or Inf met */
+#define IGABEM_ETIMEOUT (-6)        /* a bounded wait ran out */
+
+typedef struct igabem_ctx igabem_ctx;
+typedef struct igabem_geom igabem_geom;
+typedef struct igabem_problem igabem_problem;
+
+typedef enum { IGABEM_SOUND_SOFT = 0, IGABEM_SOUND_HARD = 1 } igabem_bc;
+
+typedef enum {
+  IGABEM_FP64 = 0,        /* every step in FP64 */
+  IGABEM_MIXED_FP32 = 1   /* far field (M2L, moments) and regular near-field quadrature in FP32,
+                             singular quadrature, near-field SpMV, GMRES and residuals in FP64 */
+} igabem_precision;
+
+typedef struct {
+  int degree_p;        /* ansatz degree p >= 0 (p >= 1 for sound-hard) (Sec. 3.3) */
+  int level_m;         /* uniform refinement level m: 2^m x 2^m elements per patch (Sec. 3.3) */
+  double kappa;        /* wavenumber kappa >= 0 */
+  double eta_cfie;     /* CFIE coupling eta (Sec. 2), any real non-zero value; kappa is usual */
+  int bc;              /* igabem_bc */
+  int cheb_q;          /* interpolation points per direction and cluster (Sec. 4.4), 2..16 */
+  int leaf_offset;     /* b: the cluster tree stops at level m - b (leaves of 2^b x 2^b elements) */
+  double eta_adm;      /* admissibility parameter: max(2r_t, 2r_s) <= eta_adm (dist - r_t - r_s) */
+  double kappa_cap;    /* additionally require kappa max(2r) <= kappa_cap (<= 0: no cap) */
+  int gauss_regular;   /* Gauss points per direction on regular element pairs (4) */
+  int gauss_singular;  /* Gauss points per transformed variable on touching pairs (5) */
+  int precision;       /* igabem_precision */
+  int gmres_restart;   /* restart length (30, Sec. 5.1) */
+  int max_iter;        /* iteration limit per right-hand side */
+  double tol;          /* relative residual ||b - A x|| <= tol ||b|| */
+  int no_fmm;          /* 1: treat every element pair as near (dense Galerkin matrix; tests) */
+} igabem_options;
+
+/* Fills the defaults: p = 2, m = 3, kappa = 1, eta_cfie = kappa, sound-soft, q = 7, b = 0,
+   eta_adm = 0.5, no cap, 4 / 5 Gauss points, FP64, restart 30, 1000 iterations, tol 1e-6. */
+void igabem_default_options(igabem_options *opt);
+
+typedef struct {
+  long n_dofs;               /* N: dimension of S^2_{p,m} (soft) or S^0_{p,m} (hard) */
+  long n_patch_dofs;         /* n (2^m+p)^2, the patch-wise coefficient space */
+  long n_elements;           /* n 4^m */
+  long n_clusters;           /* clusters on levels 0 .. m-b */
+  long n_near_pairs;         /* near leaf-cluster pairs */
+  long n_near_element_pairs; /* element pairs inside them */
+  long n_touching_pairs;     /* identical, common-edge and common-vertex element pairs */
+  long n_far_pairs;          /* admissible cluster pairs (M2L) over all levels */
+  size_t device_bytes;       /* device memory held by the problem */
+  double setup_ms;           /* wall time of igabem_problem_create */
+} igabem_info;
+
+typedef struct {
+  int iterations;            /* largest iteration count over the right-hand sides */
+  double rel_residual;       /* largest final ||b - A x|| / ||b|| (recomputed with A) */
+  int n_matvecs;             /* operator applications (one per block of right-hand sides) */
+  double solve_ms;           /* wall time of the call */
+} igabem_solve_info;
+
+/* Last error message of the calling thread ("" if none). */
+const char *igabem_last_error(void);
+
+/* Creates a context on CUDA device `device`.  `stream` is a cudaStream_t of that device (for example
+   PyTorch's current stream) or NULL, in which case the context creates its own stream. */
+int igabem_create(igabem_ctx **out, int device, void *stream);
+void igabem_destroy(igabem_ctx *ctx);
+
+/* Copies a NURBS geometry of n_patches patch maps F_j : [0,1]^2 -> R^3 (Sec. 3.2).  Per patch j:
+     degrees[2j], degrees[2j+1]  = (p1, p2) geometry degrees, 1..6;
+     counts[2j], counts[2j+1]    = (k1, k2) control points per direction;
+     knots: k1+p1+1 values then k2+p2+1 values, p-open on [0,1]; the patches' knot arrays follow
+            each other;
+     ctrl:  k1*k2 control points (x,y,z), index j1*k2 + j2 (j1 along the first parameter);
+     weights: k1*k2 positive weights, same order.
+   All arrays are host memory.  Patches must meet conformingly (Sec. 3.2).  Element boundaries at
+   level m must include every interior knot (knots at multiples of 2^-m); problem creation fails
+   with IGABEM_EINVAL otherwise. */
+int igabem_geometry_create(igabem_ctx *ctx, int n_patches, const int *degrees, const int *counts,
+                           const double *knots, const double *ctrl, const double *weights,
+                           igabem_geom **out);
+void igabem_geometry_destroy(igabem_geom *geom);
+
+/* Sets up a discretised CFIE problem (Sec. 4): spaces, geometry tables, cluster tree and block
+   partition, near-field Galerkin blocks (quadrature of Sec. 4.2-4.3), interpolation data.  The
+   geometry must outlive the problem. */
+int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_problem **out);
+int igabem_problem_info(const igabem_problem *prob, igabem_info *out);
+void igabem_problem_destroy(igabem_problem *prob);
+
+/* Right-hand sides of the CFIE (Sec. 4.1) for n_rhs incident directions dirs (host, [n_rhs][3],
+   unit vectors): b = [N][n_rhs] complex. */
+int igabem_rhs(igabem_problem *prob, int n_rhs, const double *dirs, void *b);
+
+/* y = A x for the discretised CFIE operator A (far field by the fast multipole method unless
+   no_fmm), x and y = [N][n_rhs] complex; x and y must not overlap. */
+int igabem_matvec(igabem_problem *prob, int n_rhs, const void *x, void *y);
+
+/* Solves A x = b(d_r) for the n_rhs directions by GMRES(restart) from x0 = 0; density = [N][n_rhs]
+   complex (du/dn for sound-soft, u for sound-hard).  Returns IGABEM_ENOT_CONVERGED (density
+   written) if a right-hand side missed the tolerance within max_iter iterations. */
+int igabem_solve(igabem_problem *prob, int n_rhs, const double *dirs, void *density,
+                 igabem_solve_info *info);
+
+/* Far-field pattern (Sec. 1) of n_rhs densities at n_dir unit directions xhat ([n_dir][3], host):
+     sound-soft u_inf(x^) = -1/(4 pi) int exp(-i kappa x^.y) t(y) dsigma_y,
+     sound-hard u_inf(x^) = -i kappa/(4 pi) int (x^.n_y) exp(-i kappa x^.y) u(y) dsigma_y,
+   with the regular Gauss rule on every element; uinf = [n_dir][n_rhs] complex. */
+int igabem_farfield(igabem_problem *prob, int n_rhs, const void *density, int n_dir,
+                    const double *xhat, void *uinf);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGABEM_H */

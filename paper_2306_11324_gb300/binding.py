@@ -1,0 +1,218 @@
+"""ctypes binding of libigabem.so (include/igabem.h): the same entry points, argument marshalling only.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA memory of the context's
+device); complex arrays are complex128 in the [N][R] layout of the C ABI.  Every computation runs in
+the CUDA library: if it is not built this module raises on import of the library, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctypes.c_double,
+                                                ctypes.c_void_p, ctypes.c_size_t)
+
+IGABEM_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOT_CONVERGED", -5: "ENUMERIC", -6: "ETIMEOUT"}
+SOUND_SOFT, SOUND_HARD = 0, 1
+FP64, MIXED_FP32 = 0, 1
+
+
+class igabem_options(ctypes.Structure):
+    _fields_ = [("degree_p", c_int), ("level_m", c_int), ("kappa", c_double), ("eta_cfie", c_double),
+                ("bc", c_int), ("cheb_q", c_int), ("leaf_offset", c_int), ("eta_adm", c_double),
+                ("kappa_cap", c_double), ("gauss_regular", c_int), ("gauss_singular", c_int),
+                ("precision", c_int), ("gmres_restart", c_int), ("max_iter", c_int), ("tol", c_double),
+                ("no_fmm", c_int)]
+
+
+class igabem_info(ctypes.Structure):
+    _fields_ = [("n_dofs", c_long), ("n_patch_dofs", c_long), ("n_elements", c_long),
+                ("n_clusters", c_long), ("n_near_pairs", c_long), ("n_near_element_pairs", c_long),
+                ("n_touching_pairs", c_long), ("n_far_pairs", c_long), ("device_bytes", c_size_t),
+                ("setup_ms", c_double)]
+
+
+class igabem_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("rel_residual", c_double), ("n_matvecs", c_int),
+                ("solve_ms", c_double)]
+
+
+class IgabemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+# name -> (restype, argtypes); the complete list of entry points declared in include/igabem.h
+SIGNATURES = {
+    "igabem_last_error": (ctypes.c_char_p, []),
+    "igabem_default_options": (None, [ctypes.POINTER(igabem_options)]),
+    "igabem_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_void_p]),
+    "igabem_destroy": (None, [c_void_p]),
+    "igabem_geometry_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, ctypes.POINTER(c_void_p)]),
+    "igabem_geometry_destroy": (None, [c_void_p]),
+    "igabem_problem_create": (c_int, [c_void_p, ctypes.POINTER(igabem_options), ctypes.POINTER(c_void_p)]),
+    "igabem_problem_info": (c_int, [c_void_p, ctypes.POINTER(igabem_info)]),
+    "igabem_problem_destroy": (None, [c_void_p]),
+    "igabem_rhs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "igabem_matvec": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "igabem_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
+    "igabem_farfield": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+}
+
+
+def lib(path: str | None = None):
+    """Load libigabem.so (building it in-tree if the sources changed) and declare its symbols."""
+    global _LIB
+    if _LIB is None:
+        path = path or _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != IGABEM_OK:
+        raise IgabemError(rc, lib().igabem_last_error().decode())
+
+
+def _ptr(a):
+    """Device or host address of a numpy array or torch tensor (kept alive by the caller)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _is_torch(a):
+    return hasattr(a, "data_ptr")
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _like(ref, shape):
+    """complex128 output in the memory of `ref` (numpy or torch, same device)."""
+    if _is_torch(ref):
+        import torch
+        return torch.empty(shape, dtype=torch.complex128, device=ref.device)
+    return np.empty(shape, dtype=np.complex128)
+
+
+def igabem_last_error() -> str:
+    return lib().igabem_last_error().decode()
+
+
+def igabem_default_options(**kw) -> igabem_options:
+    o = igabem_options()
+    lib().igabem_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def igabem_create(device: int = 0, stream: int | None = None):
+    h = c_void_p()
+    _check(lib().igabem_create(ctypes.byref(h), device, c_void_p(stream) if stream else None))
+    return h
+
+
+def igabem_destroy(ctx):
+    lib().igabem_destroy(ctx)
+
+
+def igabem_geometry_create(ctx, patches):
+    """patches: objects with p1, p2, knots1, knots2, ctrl (k1,k2,3), weights (k1,k2)."""
+    deg = _host([[p.p1, p.p2] for p in patches], np.int32)
+    cnt = _host([[p.ctrl.shape[0], p.ctrl.shape[1]] for p in patches], np.int32)
+    knots = _host(np.concatenate([np.concatenate([p.knots1, p.knots2]) for p in patches]), np.float64)
+    ctrl = _host(np.concatenate([np.asarray(p.ctrl).reshape(-1, 3) for p in patches]), np.float64)
+    w = _host(np.concatenate([np.asarray(p.weights).reshape(-1) for p in patches]), np.float64)
+    h = c_void_p()
+    _check(lib().igabem_geometry_create(ctx, len(patches), _ptr(deg), _ptr(cnt), _ptr(knots),
+                                        _ptr(ctrl), _ptr(w), ctypes.byref(h)))
+    return h
+
+
+def igabem_geometry_destroy(geom):
+    lib().igabem_geometry_destroy(geom)
+
+
+def igabem_problem_create(geom, opt: igabem_options):
+    h = c_void_p()
+    _check(lib().igabem_problem_create(geom, ctypes.byref(opt), ctypes.byref(h)))
+    return h
+
+
+def igabem_problem_info(prob) -> dict:
+    i = igabem_info()
+    _check(lib().igabem_problem_info(prob, ctypes.byref(i)))
+    return {k: getattr(i, k) for k, _ in igabem_info._fields_}
+
+
+def igabem_problem_destroy(prob):
+    lib().igabem_problem_destroy(prob)
+
+
+def _ncols(a):
+    return 1 if len(a.shape) == 1 else int(a.shape[1])
+
+
+def igabem_rhs(prob, dirs, n_dofs: int, out=None):
+    d = _host(dirs, np.float64).reshape(-1, 3)
+    R = d.shape[0]
+    out = np.empty((n_dofs, R), np.complex128) if out is None else out
+    _check(lib().igabem_rhs(prob, R, _ptr(d), _ptr(out)))
+    return out
+
+
+def igabem_matvec(prob, x, y=None):
+    R = _ncols(x)
+    y = _like(x, tuple(x.shape)) if y is None else y
+    _check(lib().igabem_matvec(prob, R, _ptr(x), _ptr(y)))
+    return y
+
+
+def igabem_solve(prob, dirs, n_dofs: int, density=None, raise_on_not_converged=True):
+    d = _host(dirs, np.float64).reshape(-1, 3)
+    R = d.shape[0]
+    density = np.empty((n_dofs, R), np.complex128) if density is None else density
+    info = igabem_solve_info()
+    rc = lib().igabem_solve(prob, R, _ptr(d), _ptr(density), ctypes.byref(info))
+    if rc != IGABEM_OK and (raise_on_not_converged or rc != -4):
+        _check(rc)
+    return density, {k: getattr(info, k) for k, _ in igabem_solve_info._fields_}
+
+
+def igabem_farfield(prob, density, xhat, out=None):
+    R = _ncols(density)
+    xh = _host(xhat, np.float64).reshape(-1, 3)
+    out = _like(density, (xh.shape[0], R)) if out is None else out
+    _check(lib().igabem_farfield(prob, R, _ptr(density), xh.shape[0], _ptr(xh), _ptr(out)))
+    return out
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/igabem.h (for the export check)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "igabem.h")
+    src = open(hdr).read()
+    return sorted(set(re.findall(r"\b(igabem_[a-z_]+)\s*\(", src)))

@@ -1,0 +1,672 @@
+// C ABI of the library (include/igabem.h): handles, memory placement, problem set-up and the GMRES
+// driver.  The kernels live in k_*.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace igabem {
+
+namespace {
+thread_local std::string g_error;
+
+struct Failure {
+  int code;
+};
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class F> int guarded(F &&f) {
+  try {
+    g_error.clear();
+    f();
+    return IGABEM_OK;
+  } catch (const Failure &e) {
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    g_error = "host memory exhausted";
+    return IGABEM_ENOMEM;
+  } catch (const std::exception &e) {
+    g_error = e.what();
+    return IGABEM_EINVAL;
+  }
+}
+}  // namespace
+
+void set_error(const std::string &msg) { g_error = msg; }
+
+void fail(int code, const std::string &msg) {
+  g_error = msg;
+  throw Failure{code};
+}
+
+void Arena::reserve(size_t bytes) {
+  release();
+  cap = bytes;
+  off = 0;
+  if (bytes == 0) return;
+  cudaError_t e = cudaMalloc(&base, bytes);
+  if (e != cudaSuccess) {
+    base = nullptr;
+    cap = 0;
+    cudaGetLastError();
+    fail(IGABEM_ENOMEM, "device allocation of " + std::to_string(bytes >> 20) + " MiB failed: " +
+                            cudaGetErrorString(e));
+  }
+}
+
+void *Arena::take(size_t bytes) {
+  size_t a = (bytes + 255) & ~size_t(255);
+  if (off + a > cap) fail(IGABEM_ENOMEM, "arena exhausted (internal sizing error)");
+  void *p = base + off;
+  off += a;
+  return p;
+}
+
+void Arena::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = off = 0;
+}
+
+// sizes of the per-call work buffers for R columns
+struct WorkPlan {
+  size_t bytes = 0;
+};
+
+}  // namespace igabem
+
+using namespace igabem;
+
+struct ProblemWork {
+  int R = 0;
+  int gmres_m = 0;
+  Arena arena;
+  double *xX, *yleaf, *gq, *xin, *yout, *red;
+  std::vector<void *> xhat, yhat;
+  // GMRES
+  double *V, *w, *x, *b, *r, *hdev, *nrm, *sdev, *ydev;
+};
+
+namespace {
+
+std::vector<ProblemWork *> g_unused;  // placeholder to keep the translation unit simple
+
+struct ProblemExt {
+  ProblemWork work;
+};
+
+ProblemExt *ext(igabem_problem *p);
+
+}  // namespace
+
+// The problem object carries its work buffers in a side table keyed by the handle.
+#include <map>
+#include <mutex>
+static std::map<const igabem_problem *, ProblemExt *> g_ext;
+static std::mutex g_ext_mu;
+
+namespace {
+ProblemExt *ext(igabem_problem *p) {
+  std::lock_guard<std::mutex> lk(g_ext_mu);
+  auto it = g_ext.find(p);
+  if (it == g_ext.end()) it = g_ext.emplace(p, new ProblemExt()).first;
+  return it->second;
+}
+
+void ensure_work(igabem_problem *P, int R, bool with_gmres) {
+  ProblemWork &W = ext(P)->work;
+  const HostSetup &S = P->S;
+  int m = std::max(1, P->opt.gmres_restart);
+  if (W.R >= R && (!with_gmres || W.gmres_m >= m)) return;
+  R = std::max(R, W.R);
+  if (with_gmres) W.gmres_m = std::max(W.gmres_m, m);
+  const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
+  const size_t cz = 2 * sizeof(double);
+  const long nleaf = S.lev[S.L].n;
+  std::vector<size_t> lev(S.L + 1, 0);
+  size_t total = 0;
+  auto add = [&](size_t n) { total += (n + 255) & ~size_t(255); return n; };
+  add(S.NX * R * cz);
+  add(nleaf * S.nL * R * cz);
+  add((size_t)S.E * nq * C * R * cz);
+  add(S.N * R * cz);
+  add(S.N * R * cz);
+  add((size_t)34 * 304 * R * cz + 4096);
+  for (int l = 0; l <= S.L; ++l) {
+    if (l >= S.lmin) {
+      add((size_t)S.lev[l].n * Q * C * R * cz);
+      add((size_t)S.lev[l].n * Q * C * R * cz);
+    }
+  }
+  if (W.gmres_m) {
+    add((size_t)(W.gmres_m + 1) * S.N * R * cz);
+    for (int k = 0; k < 4; ++k) add(S.N * R * cz);
+    add((size_t)(W.gmres_m + 2) * R * cz);
+    add(R * sizeof(double));
+    add(R * sizeof(double));
+    add((size_t)(W.gmres_m + 1) * R * cz);
+  }
+  W.arena.reserve(total);
+  W.R = R;
+  W.xX = W.arena.get<double>(S.NX * R * 2);
+  W.yleaf = W.arena.get<double>(nleaf * S.nL * R * 2);
+  W.gq = W.arena.get<double>((size_t)S.E * nq * C * R * 2);
+  W.xin = W.arena.get<double>(S.N * R * 2);
+  W.yout = W.arena.get<double>(S.N * R * 2);
+  W.red = W.arena.get<double>((size_t)34 * 304 * R * 2 + 512);
+  W.xhat.assign(S.L + 1, nullptr);
+  W.yhat.assign(S.L + 1, nullptr);
+  for (int l = S.lmin; l <= S.L; ++l) {
+    W.xhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
+    W.yhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
+  }
+  if (W.gmres_m) {
+    W.V = W.arena.get<double>((size_t)(W.gmres_m + 1) * S.N * R * 2);
+    W.w = W.arena.get<double>(S.N * R * 2);
+    W.x = W.arena.get<double>(S.N * R * 2);
+    W.b = W.arena.get<double>(S.N * R * 2);
+    W.r = W.arena.get<double>(S.N * R * 2);
+    W.hdev = W.arena.get<double>((size_t)(W.gmres_m + 2) * R * 2);
+    W.nrm = W.arena.get<double>(R);
+    W.sdev = W.arena.get<double>(R);
+    W.ydev = W.arena.get<double>((size_t)(W.gmres_m + 1) * R * 2);
+  }
+  DeviceProblem &d = P->d;
+  d.max_rhs = R;
+  d.xX = W.xX;
+  d.yleaf = W.yleaf;
+  d.gq = W.gq;
+  d.xin = W.xin;
+  d.yout = W.yout;
+  d.red = W.red;
+  d.xhat = W.xhat;
+  d.yhat = W.yhat;
+}
+
+template <class T> T *upload(Arena &A, const std::vector<T> &v, cudaStream_t st) {
+  T *p = A.get<T>(std::max<size_t>(v.size(), 1));
+  if (!v.empty()) IGA_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return p;
+}
+
+template <class T> size_t bytes_of(const std::vector<T> &v) {
+  return ((std::max<size_t>(v.size(), 1) * sizeof(T)) + 255) & ~size_t(255);
+}
+
+void matvec_dev(igabem_problem *P, int R, const double *x, double *y) {
+  launch_matvec(P->d, P->S, P->opt, R, x, y, P->geom->ctx->stream);
+}
+
+// Complex Givens rotation [[c, s], [-conj(s), conj(c)]], c = conj(a)/den, s = conj(b)/den.
+struct Col {
+  std::vector<std::complex<double>> H, cs, sn, g;
+  int k = 0;
+  bool done = false;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *igabem_last_error(void) { return g_error.c_str(); }
+
+void igabem_default_options(igabem_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->degree_p = 2;
+  o->level_m = 3;
+  o->kappa = 1.0;
+  o->eta_cfie = 1.0;
+  o->bc = IGABEM_SOUND_SOFT;
+  o->cheb_q = 7;
+  o->leaf_offset = 0;
+  o->eta_adm = 0.5;
+  o->kappa_cap = 0.0;
+  o->gauss_regular = 4;
+  o->gauss_singular = 5;
+  o->precision = IGABEM_FP64;
+  o->gmres_restart = 30;
+  o->max_iter = 1000;
+  o->tol = 1e-6;
+  o->no_fmm = 0;
+}
+
+int igabem_create(igabem_ctx **out, int device, void *stream) {
+  return guarded([&] {
+    if (!out) fail(IGABEM_EINVAL, "out is NULL");
+    int n = 0;
+    IGA_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) fail(IGABEM_EINVAL, "no such CUDA device");
+    IGA_CUDA(cudaSetDevice(device));
+    auto *c = new igabem_ctx();
+    c->device = device;
+    if (stream) {
+      c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      IGA_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    *out = c;
+  });
+}
+
+void igabem_destroy(igabem_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int igabem_geometry_create(igabem_ctx *ctx, int n_patches, const int *degrees, const int *counts,
+                           const double *knots, const double *ctrl, const double *weights,
+                           igabem_geom **out) {
+  return guarded([&] {
+    if (!ctx || !out || !degrees || !counts || !knots || !ctrl || !weights || n_patches <= 0)
+      fail(IGABEM_EINVAL, "invalid geometry arguments");
+    auto *g = new igabem_geom();
+    g->ctx = ctx;
+    long ko = 0, co = 0;
+    for (int j = 0; j < n_patches; ++j) {
+      Patch P;
+      P.p1 = degrees[2 * j]; P.p2 = degrees[2 * j + 1];
+      P.k1 = counts[2 * j]; P.k2 = counts[2 * j + 1];
+      if (P.p1 < 1 || P.p1 > 6 || P.p2 < 1 || P.p2 > 6 || P.k1 <= P.p1 || P.k2 <= P.p2) {
+        delete g;
+        fail(IGABEM_EINVAL, "patch " + std::to_string(j) + ": degrees must lie in 1..6, counts > degrees");
+      }
+      P.kn1.assign(knots + ko, knots + ko + P.k1 + P.p1 + 1);
+      ko += P.k1 + P.p1 + 1;
+      P.kn2.assign(knots + ko, knots + ko + P.k2 + P.p2 + 1);
+      ko += P.k2 + P.p2 + 1;
+      for (const auto *kn : {&P.kn1, &P.kn2}) {
+        int p = kn == &P.kn1 ? P.p1 : P.p2;
+        bool ok = true;
+        for (size_t i = 1; i < kn->size(); ++i) ok = ok && (*kn)[i] >= (*kn)[i - 1];
+        for (int i = 0; i <= p; ++i) ok = ok && (*kn)[i] == 0.0 && (*kn)[kn->size() - 1 - i] == 1.0;
+        if (!ok) {
+          delete g;
+          fail(IGABEM_EINVAL, "patch " + std::to_string(j) + ": knots must be p-open on [0,1] and sorted");
+        }
+      }
+      P.hw.resize(4L * P.k1 * P.k2);
+      for (long i = 0; i < (long)P.k1 * P.k2; ++i) {
+        double w = weights[co + i];
+        if (!(w > 0)) {
+          delete g;
+          fail(IGABEM_EINVAL, "weights must be positive");
+        }
+        for (int c = 0; c < 3; ++c) P.hw[4 * i + c] = w * ctrl[3 * (co + i) + c];
+        P.hw[4 * i + 3] = w;
+      }
+      co += (long)P.k1 * P.k2;
+      g->patches.push_back(std::move(P));
+    }
+    *out = g;
+  });
+}
+
+void igabem_geometry_destroy(igabem_geom *geom) { delete geom; }
+
+int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_problem **out) {
+  return guarded([&] {
+    if (!geom || !opt || !out) fail(IGABEM_EINVAL, "invalid problem arguments");
+    if (opt->precision != IGABEM_FP64 && opt->precision != IGABEM_MIXED_FP32)
+      fail(IGABEM_EINVAL, "unknown precision");
+    if (!(opt->eta_adm > 0)) fail(IGABEM_EINVAL, "eta_adm must be positive");
+    if (!(opt->kappa >= 0)) fail(IGABEM_EINVAL, "kappa must be >= 0");
+    double t0 = now_ms();
+    IGA_CUDA(cudaSetDevice(geom->ctx->device));
+    auto *P = new igabem_problem();
+    P->geom = geom;
+    P->opt = *opt;
+    try {
+      HostSetup &S = P->S;
+      build_setup(geom->patches, *opt, S);
+      cudaStream_t st = geom->ctx->stream;
+      const int Q = S.q * S.q, nq = S.ng * S.ng;
+      const long nleaf = S.lev[S.L].n;
+      std::vector<int> near_tgt(S.near_src.size());
+      for (long t = 0; t < nleaf; ++t)
+        for (int k = S.near_ptr[t]; k < S.near_ptr[t + 1]; ++k) near_tgt[k] = (int)t;
+      std::vector<double> rules[3];
+      const Rule4 *R4[3] = {&S.r_id, &S.r_edge, &S.r_vert};
+      for (int k = 0; k < 3; ++k) {
+        const Rule4 &r = *R4[k];
+        for (const auto *v : {&r.x1, &r.x2, &r.y1, &r.y2, &r.w}) rules[k].insert(rules[k].end(), v->begin(), v->end());
+      }
+      // --- size the arena ---
+      size_t total = 0;
+      total += bytes_of(S.edeg) + bytes_of(S.eoff) + bytes_of(S.ebez) + bytes_of(S.corners);
+      size_t gst = (size_t)S.E * nq;
+      total += 13 * ((gst * sizeof(double) + 255) & ~size_t(255));
+      total += bytes_of(S.phi1) + bytes_of(S.dphi1) + bytes_of(S.ext1) + bytes_of(S.gx) + bytes_of(S.gw);
+      for (int k = 0; k < 3; ++k) total += bytes_of(rules[k]);
+      total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) + bytes_of(S.g2x_idx);
+      total += bytes_of(S.near_ptr) + bytes_of(S.near_src) + bytes_of(near_tgt);
+      total += bytes_of(S.cheb) + bytes_of(S.T1) + bytes_of(S.LG1);
+      for (int l = 0; l <= S.L; ++l) {
+        total += bytes_of(S.lev[l].far_ptr) + bytes_of(S.lev[l].far_src);
+        total += ((size_t)7 * S.lev[l].n * Q * sizeof(double) + 255) & ~size_t(255);
+        total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
+      }
+      size_t blk_bytes = S.near_src.size() * (size_t)S.nL * S.nL * 2 * sizeof(double);
+      total += (blk_bytes + 255) & ~size_t(255);
+      P->arena.reserve(total);
+      Arena &A = P->arena;
+      DeviceProblem &d = P->d;
+      d.edeg = upload(A, S.edeg, st);
+      d.eoff = upload(A, S.eoff, st);
+      d.ebez = upload(A, S.ebez, st);
+      d.corners = upload(A, S.corners, st);
+      d.gpx = A.get<double>(3 * gst);
+      d.gpn = A.get<double>(3 * gst);
+      d.gpa = A.get<double>(gst);
+      d.gfs = A.get<double>(3 * gst);
+      d.gft = A.get<double>(3 * gst);
+      d.phi1 = upload(A, S.phi1, st);
+      d.dphi1 = upload(A, S.dphi1, st);
+      d.ext1 = upload(A, S.ext1, st);
+      d.gx = upload(A, S.gx, st);
+      d.gw = upload(A, S.gw, st);
+      for (int k = 0; k < 3; ++k) {
+        d.rule[k] = upload(A, rules[k], st);
+        d.rule_n[k] = (int)R4[k]->w.size();
+      }
+      d.touch = upload(A, S.touch, st);
+      d.touch_blk = upload(A, S.touch_blk, st);
+      d.x2g = upload(A, S.x2g, st);
+      d.g2x_ptr = upload(A, S.g2x_ptr, st);
+      d.g2x_idx = upload(A, S.g2x_idx, st);
+      d.near_ptr = upload(A, S.near_ptr, st);
+      d.near_src = upload(A, S.near_src, st);
+      d.near_tgt = upload(A, near_tgt, st);
+      double *cheb = upload(A, S.cheb, st);
+      d.T1 = upload(A, S.T1, st);
+      d.LG1 = upload(A, S.LG1, st);
+      d.far_ptr.assign(S.L + 1, nullptr);
+      d.far_src.assign(S.L + 1, nullptr);
+      d.nodes.assign(S.L + 1, nullptr);
+      d.nodes32.assign(S.L + 1, nullptr);
+      for (int l = 0; l <= S.L; ++l) {
+        d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
+        d.far_src[l] = upload(A, S.lev[l].far_src, st);
+        d.nodes[l] = A.get<double>((size_t)7 * S.lev[l].n * Q);
+        d.nodes32[l] = A.get<float>((size_t)7 * S.lev[l].n * Q);
+      }
+      d.blk = A.get<double>(S.near_src.size() * (size_t)S.nL * S.nL * 2);
+      IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
+      launch_gauss_geometry(d, S, st);
+      launch_node_geometry(d, S, cheb, st);
+      launch_near_field(d, S, *opt, st);
+      IGA_CUDA(cudaStreamSynchronize(st));
+      IGA_CUDA(cudaGetLastError());
+      igabem_info &I = P->info;
+      I.n_dofs = S.N;
+      I.n_patch_dofs = S.NX;
+      I.n_elements = S.E;
+      long ncl = 0;
+      for (auto &lv : S.lev) ncl += lv.n;
+      I.n_clusters = ncl;
+      I.n_near_pairs = (long)S.near_src.size();
+      I.n_near_element_pairs = I.n_near_pairs << (4 * S.b);
+      I.n_touching_pairs = (long)S.touch.size() / 5;
+      I.n_far_pairs = S.n_far;
+      I.device_bytes = A.cap;
+      I.setup_ms = now_ms() - t0;
+    } catch (...) {
+      P->arena.release();
+      delete P;
+      throw;
+    }
+    *out = P;
+  });
+}
+
+int igabem_problem_info(const igabem_problem *prob, igabem_info *out) {
+  return guarded([&] {
+    if (!prob || !out) fail(IGABEM_EINVAL, "NULL argument");
+    *out = prob->info;
+    std::lock_guard<std::mutex> lk(g_ext_mu);
+    auto it = g_ext.find(prob);
+    if (it != g_ext.end()) out->device_bytes += it->second->work.arena.cap;
+  });
+}
+
+void igabem_problem_destroy(igabem_problem *prob) {
+  if (!prob) return;
+  {
+    std::lock_guard<std::mutex> lk(g_ext_mu);
+    auto it = g_ext.find(prob);
+    if (it != g_ext.end()) {
+      it->second->work.arena.release();
+      delete it->second;
+      g_ext.erase(it);
+    }
+  }
+  prob->arena.release();
+  delete prob;
+}
+
+int igabem_rhs(igabem_problem *P, int n_rhs, const double *dirs, void *b) {
+  return guarded([&] {
+    if (!P || !dirs || !b || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid rhs arguments");
+    IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+    ensure_work(P, n_rhs, false);
+    cudaStream_t st = P->geom->ctx->stream;
+    ProblemWork &W = ext(P)->work;
+    double *ddir = W.red;  // 3 n_rhs doubles fit in the reduction scratch
+    IGA_CUDA(cudaMemcpyAsync(ddir, dirs, 3 * sizeof(double) * n_rhs, cudaMemcpyHostToDevice, st));
+    bool dev = is_device_ptr(b);
+    double *out = dev ? static_cast<double *>(b) : W.yout;
+    launch_rhs(P->d, P->S, P->opt, n_rhs, ddir, out, st);
+    if (!dev)
+      IGA_CUDA(cudaMemcpyAsync(b, out, P->S.N * n_rhs * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
+  return guarded([&] {
+    if (!P || !x || !y || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid matvec arguments");
+    IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+    ensure_work(P, n_rhs, false);
+    cudaStream_t st = P->geom->ctx->stream;
+    ProblemWork &W = ext(P)->work;
+    size_t bytes = P->S.N * n_rhs * 2 * sizeof(double);
+    bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+    const double *xi = dx ? static_cast<const double *>(x) : W.xin;
+    double *yo = dy ? static_cast<double *>(y) : W.yout;
+    if (!dx) IGA_CUDA(cudaMemcpyAsync(W.xin, x, bytes, cudaMemcpyHostToDevice, st));
+    matvec_dev(P, n_rhs, xi, yo);
+    if (!dy) IGA_CUDA(cudaMemcpyAsync(y, yo, bytes, cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density, igabem_solve_info *info) {
+  int status = IGABEM_OK;
+  int rc = guarded([&] {
+    if (!P || !dirs || !density || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid solve arguments");
+    double t0 = now_ms();
+    IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+    ensure_work(P, n_rhs, true);
+    cudaStream_t st = P->geom->ctx->stream;
+    ProblemWork &W = ext(P)->work;
+    const HostSetup &S = P->S;
+    const long N = S.N;
+    const int R = n_rhs, m = std::max(1, P->opt.gmres_restart);
+    const double tol = P->opt.tol;
+    const size_t vb = N * R * 2 * sizeof(double);
+    IGA_CUDA(cudaMemcpyAsync(W.red, dirs, 3 * sizeof(double) * R, cudaMemcpyHostToDevice, st));
+    launch_rhs(P->d, S, P->opt, R, W.red, W.b, st);
+    std::vector<double> bn(R), beta(R), hn(R), s(R);
+    auto norms = [&](const double *v, std::vector<double> &out) {
+      launch_norms(v, N, R, W.red, W.nrm, st);
+      IGA_CUDA(cudaMemcpyAsync(out.data(), W.nrm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+      IGA_CUDA(cudaStreamSynchronize(st));
+    };
+    norms(W.b, bn);
+    IGA_CUDA(cudaMemsetAsync(W.x, 0, vb, st));
+    IGA_CUDA(cudaMemcpyAsync(W.r, W.b, vb, cudaMemcpyDeviceToDevice, st));
+    beta = bn;
+    std::vector<int> its(R, 0);
+    std::vector<char> active(R);
+    for (int r = 0; r < R; ++r) active[r] = beta[r] > tol * bn[r];
+    int n_mv = 0;
+    const int maxit = std::max(1, P->opt.max_iter);
+    using cd = std::complex<double>;
+    std::vector<double> hbuf(2 * (m + 1) * R);
+    auto any_active = [&] { return std::any_of(active.begin(), active.end(), [](char c) { return c; }); };
+    auto max_its = [&] { return *std::max_element(its.begin(), its.end()); };
+    while (any_active() && max_its() < maxit) {
+      std::vector<Col> col(R);
+      for (int r = 0; r < R; ++r) {
+        col[r].H.assign((m + 1) * m, 0.0);
+        col[r].cs.assign(m, 0.0);
+        col[r].sn.assign(m, 0.0);
+        col[r].g.assign(m + 1, 0.0);
+        col[r].g[0] = beta[r];
+        col[r].done = !active[r];
+        s[r] = active[r] ? 1.0 / beta[r] : 0.0;
+      }
+      IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+      launch_scale(W.r, W.sdev, W.V, N, R, st);
+      for (int j = 0; j < m; ++j) {
+        double *Vj = W.V + (size_t)j * N * R * 2;
+        matvec_dev(P, R, Vj, W.w);
+        ++n_mv;
+        std::vector<cd> h((j + 1) * R, 0.0);
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+          launch_multidot(W.V, j + 1, W.w, N, R, W.red, W.hdev, st);
+          launch_multiaxpy(W.V, j + 1, W.hdev, W.w, N, R, st);
+          IGA_CUDA(cudaMemcpyAsync(hbuf.data(), W.hdev, (j + 1) * R * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          IGA_CUDA(cudaStreamSynchronize(st));
+          for (int i = 0; i < (j + 1) * R; ++i) h[i] += cd(hbuf[2 * i], hbuf[2 * i + 1]);
+        }
+        norms(W.w, hn);
+        for (int r = 0; r < R; ++r) s[r] = (!col[r].done && hn[r] > 0) ? 1.0 / hn[r] : 0.0;
+        IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_scale(W.w, W.sdev, W.V + (size_t)(j + 1) * N * R * 2, N, R, st);
+        bool all_done = true;
+        for (int r = 0; r < R; ++r) {
+          Col &c = col[r];
+          if (c.done) continue;
+          for (int i = 0; i <= j; ++i) c.H[i * m + j] = h[i * R + r];
+          c.H[(j + 1) * m + j] = hn[r];
+          for (int i = 0; i < j; ++i) {
+            cd t = c.cs[i] * c.H[i * m + j] + c.sn[i] * c.H[(i + 1) * m + j];
+            c.H[(i + 1) * m + j] = -std::conj(c.sn[i]) * c.H[i * m + j] + std::conj(c.cs[i]) * c.H[(i + 1) * m + j];
+            c.H[i * m + j] = t;
+          }
+          cd a = c.H[j * m + j], bb = c.H[(j + 1) * m + j];
+          double den = std::sqrt(std::norm(a) + std::norm(bb));
+          c.cs[j] = den > 0 ? std::conj(a) / den : 1.0;
+          c.sn[j] = den > 0 ? std::conj(bb) / den : 0.0;
+          c.H[j * m + j] = den;
+          c.H[(j + 1) * m + j] = 0.0;
+          c.g[j + 1] = -std::conj(c.sn[j]) * c.g[j];
+          c.g[j] = c.cs[j] * c.g[j];
+          c.k = j + 1;
+          its[r]++;
+          if (std::abs(c.g[j + 1]) <= tol * bn[r] || its[r] >= maxit || hn[r] == 0.0) c.done = true;
+          if (!std::isfinite(std::abs(c.g[j + 1]))) fail(IGABEM_ENUMERIC, "GMRES met a non-finite value");
+          all_done = all_done && c.done;
+        }
+        if (all_done) break;
+      }
+      // x += V y with y = H^-1 g per column (zero beyond the column's Krylov dimension)
+      std::vector<double> Y(2 * (m + 1) * R, 0.0);
+      int kmax = 0;
+      for (int r = 0; r < R; ++r) {
+        Col &c = col[r];
+        if (!active[r]) continue;
+        std::vector<cd> y(c.k);
+        for (int i = c.k - 1; i >= 0; --i) {
+          cd acc = c.g[i];
+          for (int k = i + 1; k < c.k; ++k) acc -= c.H[i * m + k] * y[k];
+          y[i] = acc / c.H[i * m + i];
+        }
+        for (int i = 0; i < c.k; ++i) {
+          Y[2 * (i * R + r)] = y[i].real();
+          Y[2 * (i * R + r) + 1] = y[i].imag();
+        }
+        kmax = std::max(kmax, c.k);
+      }
+      IGA_CUDA(cudaMemcpyAsync(W.ydev, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+      matvec_dev(P, R, W.x, W.w);
+      ++n_mv;
+      launch_sub(W.b, W.w, W.r, N * R * 2, st);
+      norms(W.r, beta);
+      for (int r = 0; r < R; ++r) {
+        if (!std::isfinite(beta[r])) fail(IGABEM_ENUMERIC, "GMRES met a non-finite residual");
+        active[r] = beta[r] > tol * bn[r];
+      }
+    }
+    bool dev = is_device_ptr(density);
+    if (dev)
+      IGA_CUDA(cudaMemcpyAsync(density, W.x, vb, cudaMemcpyDeviceToDevice, st));
+    else
+      IGA_CUDA(cudaMemcpyAsync(density, W.x, vb, cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+    double worst = 0;
+    for (int r = 0; r < R; ++r) worst = std::max(worst, bn[r] > 0 ? beta[r] / bn[r] : 0.0);
+    if (info) {
+      info->iterations = max_its();
+      info->rel_residual = worst;
+      info->n_matvecs = n_mv;
+      info->solve_ms = now_ms() - t0;
+    }
+    if (worst > tol) {
+      status = IGABEM_ENOT_CONVERGED;
+      set_error("GMRES did not reach the tolerance within max_iter");
+    }
+  });
+  return rc != IGABEM_OK ? rc : status;
+}
+
+int igabem_farfield(igabem_problem *P, int n_rhs, const void *density, int n_dir, const double *xhat,
+                    void *uinf) {
+  return guarded([&] {
+    if (!P || !density || !xhat || !uinf || n_rhs <= 0 || n_dir <= 0) fail(IGABEM_EINVAL, "invalid far-field arguments");
+    IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+    ensure_work(P, n_rhs, false);
+    cudaStream_t st = P->geom->ctx->stream;
+    ProblemWork &W = ext(P)->work;
+    size_t db = P->S.N * n_rhs * 2 * sizeof(double);
+    bool dd = is_device_ptr(density), du = is_device_ptr(uinf);
+    const double *dens = dd ? static_cast<const double *>(density) : W.xin;
+    if (!dd) IGA_CUDA(cudaMemcpyAsync(W.xin, density, db, cudaMemcpyHostToDevice, st));
+    // directions and the result need their own device space
+    double *dx = nullptr, *du_ = nullptr;
+    IGA_CUDA(cudaMallocAsync(&dx, 3 * sizeof(double) * n_dir, st));
+    IGA_CUDA(cudaMallocAsync(&du_, 2 * sizeof(double) * n_dir * n_rhs, st));
+    IGA_CUDA(cudaMemcpyAsync(dx, xhat, 3 * sizeof(double) * n_dir, cudaMemcpyHostToDevice, st));
+    launch_farfield(P->d, P->S, P->opt, n_rhs, dens, n_dir, dx, du_, st);
+    IGA_CUDA(cudaMemcpyAsync(uinf, du_, 2 * sizeof(double) * n_dir * n_rhs,
+                             du ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaFreeAsync(dx, st));
+    IGA_CUDA(cudaFreeAsync(du_, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,607 @@
+// Host set-up of a discretised CFIE problem: geometry extraction, quadrature rules, spaces,
+// touching element pairs, cluster tree and block partition (Sec. 3 and 4 of Doelz, Harbrecht and
+// Multerer).  Plain C++; everything here runs once per problem.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace igabem {
+
+// ----------------------------------------------------------------------------------------------
+// Gauss-Legendre rule: roots of P_n by Newton's method from cos(pi (i + 3/4) / (n + 1/2)),
+// weights 2 / ((1 - x^2) P_n'(x)^2), mapped to [0, 1].
+
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+    }
+    x[i] = 0.5 * (1.0 - z);  // ascending on [0, 1]
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// B-splines (Sec. 3.1): the p+1 functions that do not vanish on knot span mu, by the triangular
+// Cox-de Boor scheme, and their first derivatives.
+
+static int find_span(const std::vector<double> &kn, int p, double x) {
+  int k = (int)kn.size() - p - 1;
+  if (x >= kn[k]) return k - 1;
+  int lo = p, hi = k;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (x < kn[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+static void span_basis(const std::vector<double> &kn, int p, int mu, double x, double *N,
+                       double *dN) {
+  std::vector<double> left(p + 1), right(p + 1), prev(p + 1);
+  N[0] = 1.0;
+  for (int d = 1; d <= p; ++d) {
+    left[d] = x - kn[mu + 1 - d];
+    right[d] = kn[mu + d] - x;
+    if (d == p && dN) std::copy(N, N + p, prev.begin());
+    double saved = 0.0;
+    for (int r = 0; r < d; ++r) {
+      double den = right[r + 1] + left[d - r];
+      double t = den != 0.0 ? N[r] / den : 0.0;
+      N[r] = saved + right[r + 1] * t;
+      saved = left[d - r] * t;
+    }
+    N[d] = saved;
+  }
+  if (!dN) return;
+  if (p == 0) {
+    dN[0] = 0.0;
+    return;
+  }
+  // d/dx b_j^p = p/(xi_{j+p}-xi_j) b_j^{p-1} - p/(xi_{j+p+1}-xi_{j+1}) b_{j+1}^{p-1},
+  // j = mu-p+i; prev[i'] = b_{mu-p+1+i'}^{p-1}
+  for (int i = 0; i <= p; ++i) {
+    int j = mu - p + i;
+    double v = 0.0;
+    if (i >= 1) {
+      double den = kn[j + p] - kn[j];
+      if (den > 0) v += p / den * prev[i - 1];
+    }
+    if (i <= p - 1) {
+      double den = kn[j + p + 1] - kn[j + 1];
+      if (den > 0) v -= p / den * prev[i];
+    }
+    dN[i] = v;
+  }
+}
+
+// Homogeneous point (and derivatives) of a patch at (s, t), evaluated with the polynomial piece of
+// spans (m1, m2).
+static void patch_h(const Patch &P, int m1, int m2, double s, double t, double H[4], double Hs[4],
+                    double Ht[4]) {
+  double b1[8], d1[8], b2[8], d2[8];
+  span_basis(P.kn1, P.p1, m1, s, b1, d1);
+  span_basis(P.kn2, P.p2, m2, t, b2, d2);
+  for (int c = 0; c < 4; ++c) H[c] = Hs[c] = Ht[c] = 0.0;
+  for (int i = 0; i <= P.p1; ++i)
+    for (int j = 0; j <= P.p2; ++j) {
+      const double *h = &P.hw[((m1 - P.p1 + i) * P.k2 + (m2 - P.p2 + j)) * 4];
+      for (int c = 0; c < 4; ++c) {
+        H[c] += b1[i] * b2[j] * h[c];
+        Hs[c] += d1[i] * b2[j] * h[c];
+        Ht[c] += b1[i] * d2[j] * h[c];
+      }
+    }
+}
+
+static void patch_eval(const Patch &P, double s, double t, double F[3], double Fs[3] = nullptr,
+                       double Ft[3] = nullptr) {
+  double H[4], Hs[4], Ht[4];
+  patch_h(P, find_span(P.kn1, P.p1, s), find_span(P.kn2, P.p2, t), s, t, H, Hs, Ht);
+  for (int c = 0; c < 3; ++c) {
+    F[c] = H[c] / H[3];
+    if (Fs) Fs[c] = (Hs[c] - F[c] * Hs[3]) / H[3];
+    if (Ft) Ft[c] = (Ht[c] - F[c] * Ht[3]) / H[3];
+  }
+}
+
+static double bernstein(int n, int k, double u) {
+  double c = 1.0;
+  for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+  return c * std::pow(u, k) * std::pow(1.0 - u, n - k);
+}
+
+// Inverse of the Bernstein collocation matrix V[i][k] = B_k^n(i/n) (Gauss-Jordan).
+static std::vector<double> bernstein_collocation_inverse(int n) {
+  int s = n + 1;
+  std::vector<double> A(s * s), I(s * s, 0.0);
+  for (int i = 0; i < s; ++i) {
+    for (int k = 0; k < s; ++k) A[i * s + k] = n == 0 ? 1.0 : bernstein(n, k, double(i) / n);
+    I[i * s + i] = 1.0;
+  }
+  for (int c = 0; c < s; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < s; ++r)
+      if (std::fabs(A[r * s + c]) > std::fabs(A[piv * s + c])) piv = r;
+    for (int k = 0; k < s; ++k) {
+      std::swap(A[c * s + k], A[piv * s + k]);
+      std::swap(I[c * s + k], I[piv * s + k]);
+    }
+    double d = A[c * s + c];
+    for (int k = 0; k < s; ++k) {
+      A[c * s + k] /= d;
+      I[c * s + k] /= d;
+    }
+    for (int r = 0; r < s; ++r)
+      if (r != c) {
+        double f = A[r * s + c];
+        for (int k = 0; k < s; ++k) {
+          A[r * s + k] -= f * A[c * s + k];
+          I[r * s + k] -= f * I[c * s + k];
+        }
+      }
+  }
+  return I;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Regularising transforms for touching element pairs (same derivation as documented with the
+// device quadrature): identical 8 regions, common edge 6, common vertex 4; ns points per variable.
+
+static void rule_identical(const std::vector<double> &gx, const std::vector<double> &gw, Rule4 &R) {
+  int n = (int)gx.size();
+  for (int s1 = 0; s1 < 2; ++s1)
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int tri = 0; tri < 2; ++tri)
+        for (int a = 0; a < n; ++a)
+          for (int b = 0; b < n; ++b)
+            for (int c = 0; c < n; ++c)
+              for (int d = 0; d < n; ++d) {
+                double xi = gx[a], eta = gx[b], t1 = gx[c], t2 = gx[d];
+                double z1 = tri == 0 ? xi : xi * eta, z2 = tri == 0 ? xi * eta : xi;
+                double b1 = (1 - z1) * t1, b2 = (1 - z2) * t2;
+                double jac = xi * (1 - z1) * (1 - z2);
+                double x1 = s1 == 0 ? b1 : b1 + z1, y1 = s1 == 0 ? b1 + z1 : b1;
+                double x2 = s2 == 0 ? b2 : b2 + z2, y2 = s2 == 0 ? b2 + z2 : b2;
+                R.x1.push_back(x1); R.x2.push_back(x2); R.y1.push_back(y1); R.y2.push_back(y2);
+                R.w.push_back(gw[a] * gw[b] * gw[c] * gw[d] * jac);
+              }
+}
+
+static void rule_edge(const std::vector<double> &gx, const std::vector<double> &gw, Rule4 &R) {
+  int n = (int)gx.size();
+  for (int sz = 0; sz < 2; ++sz)
+    for (int pyr = 0; pyr < 3; ++pyr)
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+          for (int c = 0; c < n; ++c)
+            for (int d = 0; d < n; ++d) {
+              double xi = gx[a], e1 = gx[b], e2 = gx[c], t = gx[d];
+              double x1, y1, z;
+              if (pyr == 0) { x1 = xi; y1 = xi * e1; z = xi * e2; }
+              else if (pyr == 1) { y1 = xi; x1 = xi * e1; z = xi * e2; }
+              else { z = xi; x1 = xi * e1; y1 = xi * e2; }
+              double bb = (1 - z) * t, jac = xi * xi * (1 - z);
+              double x2 = sz == 0 ? bb : bb + z, y2 = sz == 0 ? bb + z : bb;
+              R.x1.push_back(x1); R.x2.push_back(x2); R.y1.push_back(y1); R.y2.push_back(y2);
+              R.w.push_back(gw[a] * gw[b] * gw[c] * gw[d] * jac);
+            }
+}
+
+static void rule_vertex(const std::vector<double> &gx, const std::vector<double> &gw, Rule4 &R) {
+  int n = (int)gx.size();
+  for (int big = 0; big < 4; ++big)
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b)
+        for (int c = 0; c < n; ++c)
+          for (int d = 0; d < n; ++d) {
+            double xi = gx[a], e[3] = {gx[b], gx[c], gx[d]}, co[4];
+            co[big] = xi;
+            for (int i = 0, k = 0; i < 4; ++i)
+              if (i != big) co[i] = xi * e[k++];
+            R.x1.push_back(co[0]); R.x2.push_back(co[1]); R.y1.push_back(co[2]); R.y2.push_back(co[3]);
+            R.w.push_back(gw[a] * gw[b] * gw[c] * gw[d] * xi * xi * xi);
+          }
+}
+
+// The eight symmetries of the unit square, in the order identity, rotations by 90/180/270
+// degrees, then these composed with the diagonal reflection; applied to corner coordinates.
+static void d4(int k, int u, int v, int &ou, int &ov) {
+  int a = u, b = v;
+  if (k >= 4) std::swap(a, b);  // S(u,v) = (v,u), applied first
+  for (int r = 0; r < (k & 3); ++r) {  // R(u,v) = (1-v, u)
+    int na = 1 - b, nb = a;
+    a = na;
+    b = nb;
+  }
+  ou = a;
+  ov = b;
+}
+
+// ----------------------------------------------------------------------------------------------
+// spatial hash of points (coincidence within tol)
+
+struct PointHash {
+  double cell;
+  std::unordered_map<long long, std::vector<int>> map;
+  static long long key(long long a, long long b, long long c) {
+    return (a * 73856093LL) ^ (b * 19349663LL) ^ (c * 83492791LL);
+  }
+  long long ci(double v) const { return (long long)std::floor(v / cell); }
+  void insert(const double *x, int id) { map[key(ci(x[0]), ci(x[1]), ci(x[2]))].push_back(id); }
+  template <class F> void near(const double *x, F f) const {
+    long long a = ci(x[0]), b = ci(x[1]), c = ci(x[2]);
+    for (long long i = a - 1; i <= a + 1; ++i)
+      for (long long j = b - 1; j <= b + 1; ++j)
+        for (long long k = c - 1; k <= c + 1; ++k) {
+          auto it = map.find(key(i, j, k));
+          if (it != map.end())
+            for (int id : it->second) f(id);
+        }
+  }
+};
+
+static double dist3(const double *a, const double *b) {
+  return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
+                   (a[2] - b[2]) * (a[2] - b[2]));
+}
+
+// ----------------------------------------------------------------------------------------------
+
+void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S) {
+  const int np = (int)patches.size();
+  const int m = opt.level_m, p = opt.degree_p;
+  if (m < 0 || m > 12) fail(IGABEM_EINVAL, "level_m must lie in 0..12");
+  if (p < 0 || p > 6) fail(IGABEM_EINVAL, "degree_p must lie in 0..6");
+  S.hard = opt.bc == IGABEM_SOUND_HARD;
+  if (S.hard && p < 1) fail(IGABEM_EINVAL, "sound-hard problems need degree_p >= 1");
+  S.np = np; S.m = m; S.p = p; S.n1 = 1 << m; S.h = 1.0 / S.n1;
+  S.E = np * S.n1 * S.n1; S.nb = S.n1 + p; S.nloc = (p + 1) * (p + 1);
+  S.NX = (long)np * S.nb * S.nb;
+  S.ng = opt.gauss_regular; S.ns = opt.gauss_singular;
+  if (S.ng < 1 || S.ng > 8 || S.ns < 1 || S.ns > 10) fail(IGABEM_EINVAL, "quadrature orders out of range");
+
+  // --- per-element rational Bezier nets ---
+  S.edeg.resize(2 * S.E);
+  S.eoff.resize(S.E);
+  long off = 0;
+  for (int j = 0; j < np; ++j) {
+    const Patch &P = patches[j];
+    for (const std::vector<double> *kn : {&P.kn1, &P.kn2})
+      for (double x : *kn) {
+        double y = x * S.n1;
+        if (std::fabs(y - std::round(y)) > 1e-9)
+          fail(IGABEM_EINVAL, "patch " + std::to_string(j) +
+                                  ": a knot is not an element boundary at this level m");
+      }
+    for (int e = 0; e < S.n1 * S.n1; ++e) {
+      int id = j * S.n1 * S.n1 + e;
+      S.edeg[2 * id] = P.p1; S.edeg[2 * id + 1] = P.p2;
+      S.eoff[id] = off;
+      off += 4L * (P.p1 + 1) * (P.p2 + 1);
+    }
+  }
+  S.ebez.assign(off, 0.0);
+  S.corners.assign(12L * S.E, 0.0);
+  for (int j = 0; j < np; ++j) {
+    const Patch &P = patches[j];
+    std::vector<double> V1 = bernstein_collocation_inverse(P.p1), V2 = bernstein_collocation_inverse(P.p2);
+    int s1 = P.p1 + 1, s2 = P.p2 + 1;
+    std::vector<double> samp(s1 * s2 * 4), tmp(s1 * s2 * 4);
+    for (int ix = 0; ix < S.n1; ++ix)
+      for (int iy = 0; iy < S.n1; ++iy) {
+        int id = (j * S.n1 + ix) * S.n1 + iy;
+        double smid = (ix + 0.5) * S.h, tmid = (iy + 0.5) * S.h;
+        int m1 = find_span(P.kn1, P.p1, smid), m2 = find_span(P.kn2, P.p2, tmid);
+        for (int a = 0; a < s1; ++a)
+          for (int b = 0; b < s2; ++b) {
+            double u = P.p1 ? double(a) / P.p1 : 0.0, v = P.p2 ? double(b) / P.p2 : 0.0;
+            double H[4], Hs[4], Ht[4];
+            patch_h(P, m1, m2, (ix + u) * S.h, (iy + v) * S.h, H, Hs, Ht);
+            for (int c = 0; c < 4; ++c) samp[(a * s2 + b) * 4 + c] = H[c];
+          }
+        // coefficients = V1^-1 samp V2^-T (per component)
+        for (int a = 0; a < s1; ++a)
+          for (int b = 0; b < s2; ++b)
+            for (int c = 0; c < 4; ++c) {
+              double acc = 0;
+              for (int k = 0; k < s1; ++k) acc += V1[a * s1 + k] * samp[(k * s2 + b) * 4 + c];
+              tmp[(a * s2 + b) * 4 + c] = acc;
+            }
+        double *out = &S.ebez[S.eoff[id]];
+        for (int a = 0; a < s1; ++a)
+          for (int b = 0; b < s2; ++b)
+            for (int c = 0; c < 4; ++c) {
+              double acc = 0;
+              for (int k = 0; k < s2; ++k) acc += V2[b * s2 + k] * tmp[(a * s2 + k) * 4 + c];
+              out[(a * s2 + b) * 4 + c] = acc;
+            }
+        const int ca[4] = {0, P.p1, 0, P.p1}, cb[4] = {0, 0, P.p2, P.p2};
+        for (int c = 0; c < 4; ++c) {
+          const double *hw = &out[(ca[c] * s2 + cb[c]) * 4];
+          for (int k = 0; k < 3; ++k) S.corners[(id * 4 + c) * 3 + k] = hw[k] / hw[3];
+        }
+      }
+  }
+  S.scale = 0;
+  for (double v : S.corners) S.scale = std::max(S.scale, std::fabs(v));
+
+  // --- quadrature ---
+  gauss_legendre01(S.ng, S.gx, S.gw);
+  std::vector<double> sx, sw;
+  gauss_legendre01(S.ns, sx, sw);
+  rule_identical(sx, sw, S.r_id);
+  rule_edge(sx, sw, S.r_edge);
+  rule_vertex(sx, sw, S.r_vert);
+
+  // --- ansatz space: knot vector Xi_{p,m}, tables per element column ---
+  std::vector<double> kn;
+  for (int i = 0; i <= p; ++i) kn.push_back(0.0);
+  for (int i = 1; i < S.n1; ++i) kn.push_back(double(i) / S.n1);
+  for (int i = 0; i <= p; ++i) kn.push_back(1.0);
+  S.phi1.assign((size_t)S.n1 * S.ng * (p + 1), 0.0);
+  S.dphi1.assign(S.phi1.size(), 0.0);
+  S.ext1.assign((size_t)S.n1 * (p + 1) * (p + 1), 0.0);
+  std::vector<double> Vinv = bernstein_collocation_inverse(p);
+  for (int ix = 0; ix < S.n1; ++ix) {
+    double N[8], dN[8];
+    for (int q = 0; q < S.ng; ++q) {
+      span_basis(kn, p, ix + p, (ix + S.gx[q]) * S.h, N, dN);
+      for (int a = 0; a <= p; ++a) {
+        S.phi1[(ix * S.ng + q) * (p + 1) + a] = N[a];
+        S.dphi1[(ix * S.ng + q) * (p + 1) + a] = dN[a];
+      }
+    }
+    std::vector<double> smp((p + 1) * (p + 1));
+    for (int i = 0; i <= p; ++i) {
+      double u = p ? double(i) / p : 0.0;
+      span_basis(kn, p, ix + p, (ix + u) * S.h, N, nullptr);
+      for (int a = 0; a <= p; ++a) smp[i * (p + 1) + a] = N[a];
+    }
+    for (int a = 0; a <= p; ++a)
+      for (int c = 0; c <= p; ++c) {
+        double acc = 0;
+        for (int i = 0; i <= p; ++i) acc += Vinv[c * (p + 1) + i] * smp[i * (p + 1) + a];
+        S.ext1[(ix * (p + 1) + a) * (p + 1) + c] = acc;
+      }
+  }
+
+  // --- touching element pairs ---
+  const double tol = 1e-10 * S.scale;
+  PointHash ph;
+  ph.cell = std::max(1e-7 * S.scale, 1e-300);
+  for (int i = 0; i < 4 * S.E; ++i) ph.insert(&S.corners[3L * i], i);
+  std::unordered_map<long long, int> shared;  // (e*E+f) -> bitmask of e's corners shared with f
+  for (int i = 0; i < 4 * S.E; ++i) {
+    int e = i / 4;
+    ph.near(&S.corners[3L * i], [&](int k) {
+      int f = k / 4;
+      if (f != e && dist3(&S.corners[3L * i], &S.corners[3L * k]) <= tol)
+        shared[(long long)e * S.E + f] |= 1 << (i % 4);
+    });
+  }
+  S.touch.clear();
+  for (int e = 0; e < S.E; ++e) {
+    S.touch.insert(S.touch.end(), {e, e, 0, 0, 0});
+  }
+  std::vector<std::pair<long long, int>> sh(shared.begin(), shared.end());
+  std::sort(sh.begin(), sh.end());
+  for (auto &kv : sh) {
+    int e = int(kv.first / S.E), f = int(kv.first % S.E);
+    int nsh = __builtin_popcount(kv.second);
+    if (nsh > 2) fail(IGABEM_EINVAL, "two elements share more than an edge");
+    int kind = nsh == 2 ? 2 : 1;
+    int te = -1, tf = -1;
+    for (int a = 0; a < 8 && te < 0; ++a)
+      for (int b = 0; b < 8; ++b) {
+        int u, v;
+        d4(a, 0, 0, u, v); const double *pe0 = &S.corners[(e * 4 + u + 2 * v) * 3];
+        d4(b, 0, 0, u, v); const double *pf0 = &S.corners[(f * 4 + u + 2 * v) * 3];
+        if (dist3(pe0, pf0) > tol) continue;
+        if (kind == 2) {
+          d4(a, 0, 1, u, v); const double *pe1 = &S.corners[(e * 4 + u + 2 * v) * 3];
+          d4(b, 0, 1, u, v); const double *pf1 = &S.corners[(f * 4 + u + 2 * v) * 3];
+          if (dist3(pe1, pf1) > tol) continue;
+        }
+        te = a; tf = b;
+        break;
+      }
+    if (te < 0) fail(IGABEM_EINVAL, "touching pair without a canonical position");
+    S.touch.insert(S.touch.end(), {e, f, kind, te, tf});
+  }
+
+  // --- continuous space: glue patch-wise functions with coinciding Greville anchors ---
+  S.x2g.resize(S.NX);
+  if (!S.hard) {
+    std::iota(S.x2g.begin(), S.x2g.end(), 0);
+    S.N = S.NX;
+  } else {
+    std::vector<double> grev(S.nb);
+    for (int i = 0; i < S.nb; ++i) {
+      double acc = 0;
+      for (int k = 1; k <= p; ++k) acc += kn[i + k];
+      grev[i] = acc / p;
+    }
+    std::vector<double> anchor(3 * S.NX);
+    for (int j = 0; j < np; ++j)
+      for (int i1 = 0; i1 < S.nb; ++i1)
+        for (int i2 = 0; i2 < S.nb; ++i2)
+          patch_eval(patches[j], grev[i1], grev[i2], &anchor[3 * (((long)j * S.nb + i1) * S.nb + i2)]);
+    PointHash ah;
+    ah.cell = 1e-6 * S.scale;
+    for (long X = 0; X < S.NX; ++X) ah.insert(&anchor[3 * X], (int)X);
+    std::vector<int> cls(S.NX);
+    for (long X = 0; X < S.NX; ++X) {
+      int best = (int)X;
+      ah.near(&anchor[3 * X], [&](int k) {
+        if (dist3(&anchor[3 * X], &anchor[3L * k]) <= 1e-9 * S.scale) best = std::min(best, k);
+      });
+      cls[X] = best;
+    }
+    std::vector<int> mins(cls.begin(), cls.end());
+    std::sort(mins.begin(), mins.end());
+    mins.erase(std::unique(mins.begin(), mins.end()), mins.end());
+    for (long X = 0; X < S.NX; ++X)
+      S.x2g[X] = int(std::lower_bound(mins.begin(), mins.end(), cls[X]) - mins.begin());
+    S.N = (long)mins.size();
+  }
+  S.g2x_ptr.assign(S.N + 1, 0);
+  for (long X = 0; X < S.NX; ++X) S.g2x_ptr[S.x2g[X] + 1]++;
+  for (long i = 0; i < S.N; ++i) S.g2x_ptr[i + 1] += S.g2x_ptr[i];
+  S.g2x_idx.assign(S.NX, 0);
+  {
+    std::vector<int> fill(S.g2x_ptr.begin(), S.g2x_ptr.end() - 1);
+    for (long X = 0; X < S.NX; ++X) S.g2x_idx[fill[S.x2g[X]]++] = (int)X;
+  }
+
+  // --- cluster tree and block partition (Sec. 4.4) ---
+  S.no_fmm = opt.no_fmm != 0;
+  S.b = S.no_fmm ? m : opt.leaf_offset;
+  if (S.b < 0 || S.b > m) fail(IGABEM_EINVAL, "leaf_offset must lie in 0..level_m");
+  S.L = m - S.b;
+  S.q = opt.cheb_q;
+  if (S.q < 2 || S.q > 16) fail(IGABEM_EINVAL, "cheb_q must lie in 2..16");
+  S.nL1 = (1 << S.b) + p;
+  S.nL = S.nL1 * S.nL1;
+  S.lev.assign(S.L + 1, TreeLevel{});
+  for (int l = 0; l <= S.L; ++l) {
+    TreeLevel &T = S.lev[l];
+    int nl = 1 << l;
+    T.n = np * nl * nl;
+    T.center.assign(3L * T.n, 0.0);
+    T.radius.assign(T.n, 0.0);
+    for (int j = 0; j < np; ++j)
+      for (int cx = 0; cx < nl; ++cx)
+        for (int cy = 0; cy < nl; ++cy) {
+          int t = (j * nl + cx) * nl + cy;
+          double *c = &T.center[3L * t];
+          patch_eval(patches[j], (cx + 0.5) / nl, (cy + 0.5) / nl, c);
+          double r = 0;
+          for (int a = 0; a <= 8; ++a)
+            for (int b = 0; b <= 8; ++b) {
+              double F[3];
+              patch_eval(patches[j], (cx + a / 8.0) / nl, (cy + b / 8.0) / nl, F);
+              r = std::max(r, dist3(F, c));
+            }
+          T.radius[t] = r;
+        }
+  }
+  const double cap = opt.kappa_cap > 0 ? opt.kappa_cap : INFINITY;
+  auto admissible = [&](int l, int t, int s) {
+    if (S.no_fmm) return false;
+    const TreeLevel &T = S.lev[l];
+    double rt = T.radius[t], rs = T.radius[s];
+    double diam = std::max(2 * rt, 2 * rs);
+    double dist = dist3(&T.center[3L * t], &T.center[3L * s]) - rt - rs;
+    if (dist <= 0 || diam > opt.eta_adm * dist) return false;
+    return opt.kappa * diam <= cap;
+  };
+  std::vector<std::pair<int, int>> cand, nxt, near;
+  for (int t = 0; t < np; ++t)
+    for (int s = 0; s < np; ++s) cand.push_back({t, s});
+  S.n_far = 0;
+  S.lmin = S.L + 1;
+  for (int l = 0; l <= S.L; ++l) {
+    std::vector<std::pair<int, int>> far;
+    nxt.clear();
+    int nl = 1 << l, nc = 2 * nl;
+    for (auto [t, s] : cand) {
+      if (admissible(l, t, s)) {
+        far.push_back({t, s});
+      } else if (l == S.L) {
+        near.push_back({t, s});
+      } else {
+        int jt = t / (nl * nl), xt = (t / nl) % nl, yt = t % nl;
+        int js = s / (nl * nl), xs = (s / nl) % nl, ys = s % nl;
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b)
+            nxt.push_back({(jt * nc + 2 * xt + (a >> 1)) * nc + 2 * yt + (a & 1),
+                           (js * nc + 2 * xs + (b >> 1)) * nc + 2 * ys + (b & 1)});
+      }
+    }
+    std::sort(far.begin(), far.end());
+    TreeLevel &T = S.lev[l];
+    T.far_ptr.assign(T.n + 1, 0);
+    for (auto &pr : far) T.far_ptr[pr.first + 1]++;
+    for (int i = 0; i < T.n; ++i) T.far_ptr[i + 1] += T.far_ptr[i];
+    T.far_src.resize(far.size());
+    for (size_t i = 0; i < far.size(); ++i) T.far_src[i] = far[i].second;
+    if (!far.empty()) S.lmin = std::min(S.lmin, l);
+    S.n_far += (long)far.size();
+    cand.swap(nxt);
+  }
+  std::sort(near.begin(), near.end());
+  int nleaf = S.lev[S.L].n;
+  S.near_ptr.assign(nleaf + 1, 0);
+  for (auto &pr : near) S.near_ptr[pr.first + 1]++;
+  for (int i = 0; i < nleaf; ++i) S.near_ptr[i + 1] += S.near_ptr[i];
+  S.near_src.resize(near.size());
+  for (size_t i = 0; i < near.size(); ++i) S.near_src[i] = near[i].second;
+
+  // touching pair -> near block
+  int npt = (int)S.touch.size() / 5;
+  S.touch_blk.resize(npt);
+  const int nlL = 1 << S.L, bsh = S.b;
+  auto leaf_of = [&](int e) {
+    int j = e / (S.n1 * S.n1), ix = (e / S.n1) % S.n1, iy = e % S.n1;
+    return (j * nlL + (ix >> bsh)) * nlL + (iy >> bsh);
+  };
+  for (int i = 0; i < npt; ++i) {
+    int te = leaf_of(S.touch[5 * i]), tf = leaf_of(S.touch[5 * i + 1]);
+    auto b0 = S.near_src.begin() + S.near_ptr[te], b1 = S.near_src.begin() + S.near_ptr[te + 1];
+    auto it = std::lower_bound(b0, b1, tf);
+    if (it == b1 || *it != tf) fail(IGABEM_EINVAL, "touching pair outside the near field");
+    S.touch_blk[i] = int(it - S.near_src.begin());
+  }
+
+  // --- interpolation tables ---
+  S.cheb.resize(S.q);
+  for (int a = 0; a < S.q; ++a) S.cheb[a] = 0.5 + 0.5 * std::cos((2 * a + 1) * M_PI / (2 * S.q));
+  auto lag = [&](int a, double s) {
+    double v = 1.0;
+    for (int k = 0; k < S.q; ++k)
+      if (k != a) v *= (s - S.cheb[k]) / (S.cheb[a] - S.cheb[k]);
+    return v;
+  };
+  S.T1.resize(2L * S.q * S.q);
+  for (int c = 0; c < 2; ++c)
+    for (int a = 0; a < S.q; ++a)
+      for (int a2 = 0; a2 < S.q; ++a2)
+        S.T1[(c * S.q + a) * S.q + a2] = lag(a, 0.5 * c + 0.5 * S.cheb[a2]);
+  int nb2 = 1 << S.b;
+  S.LG1.resize((size_t)nb2 * S.ng * S.q);
+  for (int o = 0; o < nb2; ++o)
+    for (int g = 0; g < S.ng; ++g)
+      for (int a = 0; a < S.q; ++a)
+        S.LG1[(o * S.ng + g) * S.q + a] = lag(a, (o + S.gx[g]) / nb2);
+}
+
+}  // namespace igabem

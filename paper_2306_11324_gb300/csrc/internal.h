@@ -1,0 +1,166 @@
+// Internal declarations shared by the host set-up, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/igabem.h"
+
+namespace igabem {
+
+// ----------------------------------------------------------------------------------------------
+// errors
+
+struct Error {
+  int code;
+  std::string msg;
+};
+void set_error(const std::string &msg);
+[[noreturn]] void fail(int code, const std::string &msg);
+
+#define IGA_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      ::igabem::fail(IGABEM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+// ----------------------------------------------------------------------------------------------
+// geometry input (host copy)
+
+struct Patch {
+  int p1, p2, k1, k2;
+  std::vector<double> kn1, kn2;  // knot vectors
+  std::vector<double> hw;        // homogeneous control net (w x, w y, w z, w), index (j1*k2+j2)*4
+};
+
+// ----------------------------------------------------------------------------------------------
+// device arena: one allocation per problem, bump-allocated in 256-byte steps
+
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, off = 0;
+  void reserve(size_t bytes);
+  void *take(size_t bytes);
+  template <class T> T *get(size_t n) { return static_cast<T *>(take(n * sizeof(T))); }
+  void release();
+};
+
+// ----------------------------------------------------------------------------------------------
+// host set-up products (plain arrays, uploaded once)
+
+struct Rule4 {  // a rule on [0,1]^4 for touching element pairs, canonical position
+  std::vector<double> x1, x2, y1, y2, w;
+};
+
+struct TreeLevel {
+  int n;                            // clusters on the level (n_patches 4^l)
+  std::vector<double> center;       // 3 per cluster
+  std::vector<double> radius;
+  std::vector<int> far_ptr, far_src;  // admissible pairs, CSR by target cluster
+};
+
+struct HostSetup {
+  // discretisation
+  int np = 0, m = 0, n1 = 0, E = 0, p = 0, nb = 0, nloc = 0;
+  long NX = 0, N = 0;
+  double h = 0, scale = 0;
+  bool hard = false;
+  // per-element rational Bezier geometry
+  std::vector<int> edeg;       // 2 per element
+  std::vector<long> eoff;      // offset (in doubles) of the element's homogeneous net
+  std::vector<double> ebez;    // nets, 4 doubles per control point, index (i*(pg2+1)+j)
+  std::vector<double> corners; // 4 corners x 3 per element, local (0,0),(1,0),(0,1),(1,1)
+  // quadrature
+  int ng = 4, ns = 5;
+  std::vector<double> gx, gw;          // Gauss rule on [0,1] (ng points)
+  Rule4 r_id, r_edge, r_vert;
+  // ansatz basis: per element column ix, Gauss point q, function a: value and d/ds
+  std::vector<double> phi1, dphi1;     // [n1][ng][p+1]
+  std::vector<double> ext1;            // Bernstein extraction [n1][p+1 (fn)][p+1 (bern)]
+  // touching pairs (e, f, kind 0/1/2, Te, Tf)
+  std::vector<int> touch;              // 5 ints per pair
+  // continuous space gluing
+  std::vector<int> x2g;                // NX
+  std::vector<int> g2x_ptr, g2x_idx;   // CSR N -> X
+  // tree
+  int L = 0, b = 0, q = 7, nL1 = 0, nL = 0, lmin = 0;
+  bool no_fmm = false;
+  std::vector<TreeLevel> lev;
+  std::vector<int> near_ptr, near_src; // near leaf pairs, CSR by target leaf
+  std::vector<int> touch_blk;          // per touching pair: index of its near leaf pair
+  long n_far = 0;
+  // interpolation tables
+  std::vector<double> cheb;            // normalised Chebyshev nodes t_a on [0,1]
+  std::vector<double> T1;              // [2][q][q]: L_a(parent) at child node a'
+  std::vector<double> LG1;             // [2^b][ng][q]: leaf Lagrange at Gauss points
+};
+
+void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S);
+
+// Gauss-Legendre rule on [0,1] (Newton iteration on P_n).
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w);
+
+}  // namespace igabem
+
+// ----------------------------------------------------------------------------------------------
+// handles
+
+struct igabem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+};
+
+struct igabem_geom {
+  igabem_ctx *ctx = nullptr;
+  std::vector<igabem::Patch> patches;
+};
+
+namespace igabem {
+
+// device copies of the set-up and the working buffers of a problem
+struct DeviceProblem {
+  // element tables
+  int *edeg;
+  long *eoff;
+  double *ebez;
+  double *gpx, *gpn, *gpa, *gfs, *gft;    // Gauss-point geometry: [3][E*ng*ng] or [E*ng*ng]
+  double *phi1, *dphi1, *ext1, *gx, *gw;
+  double *rule[3];                          // singular rules (5 arrays each, SoA)
+  int rule_n[3];
+  double *corners;
+  int *touch, *touch_blk;
+  int *x2g, *g2x_ptr, *g2x_idx;
+  // tree
+  int *near_ptr, *near_src, *near_tgt;
+  std::vector<int *> far_ptr, far_src;       // per level
+  std::vector<double *> nodes;               // per level: [7][n*q*q] (x, n~, a) node geometry
+  std::vector<float *> nodes32;
+  double *T1, *LG1;
+  // near-field blocks (column-major nL x nL per near pair)
+  double *blk;                               // complex FP64: 2 doubles per entry
+  // work buffers, sized for max_rhs columns
+  int max_rhs = 0;
+  double *xX = nullptr;                      // X-space input [NX][R] complex
+  double *yleaf = nullptr;                   // leaf-local outputs [n_leaf][nL][R] complex
+  double *gq = nullptr;                      // channel values at Gauss points [E][nq][C][R]
+  std::vector<void *> xhat, yhat;            // expansions per level [n][q*q][C][R]
+  double *xin = nullptr, *yout = nullptr;    // device staging of caller vectors [N][R]
+  double *red = nullptr;                     // reduction scratch
+};
+
+}  // namespace igabem
+
+struct igabem_problem {
+  igabem_geom *geom = nullptr;
+  igabem_options opt{};
+  igabem::HostSetup S;
+  igabem::Arena arena;
+  igabem::DeviceProblem d{};
+  igabem_info info{};
+};

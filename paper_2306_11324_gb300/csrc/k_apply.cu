@@ -1,0 +1,381 @@
+// Application of the discretised CFIE operator: near-field block SpMV plus the interpolation fast
+// multipole method on the reference domain (Sec. 4.4): leaf moments (P2M), upward transfers (M2M),
+// coupling of admissible cluster pairs with kernel samples generated on the fly (M2L), downward
+// transfers (L2L), evaluation and testing at the Gauss points (L2P).
+#include <algorithm>
+
+#include "internal.h"
+#include "k_common.cuh"
+#include "kernels.h"
+
+namespace igabem {
+
+namespace {
+
+struct Dims {
+  int np, m, n1, p, nb, b, L, q, Q, nL1, nL, ng, nq, C, R, CR;
+  long NX, N, E;
+  double h, kappa, eta;
+  bool hard;
+};
+
+Dims dims(const HostSetup &S, const igabem_options &o, int R) {
+  Dims D;
+  D.np = S.np; D.m = S.m; D.n1 = S.n1; D.p = S.p; D.nb = S.nb; D.b = S.b; D.L = S.L; D.q = S.q;
+  D.Q = S.q * S.q; D.nL1 = S.nL1; D.nL = S.nL; D.ng = S.ng; D.nq = S.ng * S.ng;
+  D.C = S.hard ? 7 : 1; D.R = R; D.CR = D.C * R;
+  D.NX = S.NX; D.N = S.N; D.E = S.E; D.h = S.h; D.kappa = o.kappa; D.eta = o.eta_cfie;
+  D.hard = S.hard;
+  return D;
+}
+
+inline int grid_for(long n, int block = 256) {
+  return (int)std::max<long>(1, std::min<long>((n + block - 1) / block, 152L * 32));
+}
+
+#define GRID_STRIDE(i, n) \
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
+
+// x_X[X][r] = x[x2g[X]][r]
+__global__ void k_gather_in(Dims D, const int *__restrict__ x2g, const double2 *__restrict__ x,
+                            double2 *__restrict__ xX) {
+  GRID_STRIDE(i, D.NX * D.R) {
+    long X = i / D.R;
+    int r = int(i % D.R);
+    xX[i] = x[(long)x2g[X] * D.R + r];
+  }
+}
+
+__device__ inline long xindex(const Dims &D, int j, int i1, int i2) {
+  return ((long)j * D.nb + i1) * D.nb + i2;
+}
+
+// y_leaf[t][i][r] = sum over near blocks (t, s) of B[j][i] x_s[j][r]  (B includes 1/2 M)
+__global__ void k_near_spmv(Dims D, const int *__restrict__ near_ptr, const int *__restrict__ near_src,
+                            const double2 *__restrict__ blk, const double2 *__restrict__ xX,
+                            double2 *__restrict__ yleaf) {
+  const int t = blockIdx.x;
+  const int nlL = 1 << D.L, e1 = 1 << D.b;
+  for (int o = threadIdx.x; o < D.nL * D.R; o += blockDim.x) {
+    int i = o / D.R, r = o % D.R;
+    double2 acc = cmk(0, 0);
+    for (int k = near_ptr[t]; k < near_ptr[t + 1]; ++k) {
+      int s = near_src[k];
+      int js = s / (nlL * nlL), cx = (s / nlL) % nlL, cy = s % nlL;
+      const double2 *B = blk + (size_t)k * D.nL * D.nL;
+      for (int jj = 0; jj < D.nL; ++jj) {
+        long X = xindex(D, js, cx * e1 + jj / D.nL1, cy * e1 + jj % D.nL1);
+        acc = cadd(acc, cmul(B[(size_t)jj * D.nL + i], xX[X * D.R + r]));
+      }
+    }
+    yleaf[((size_t)t * D.nL + i) * D.R + r] = acc;
+  }
+}
+
+struct Tables {
+  const double *phi1, *dphi1, *gw, *LG1, *T1;
+  const double *gpn, *gfs, *gft;  // Gauss-point geometry (SoA, stride E*nq)
+};
+
+// P2M: xhat[t][a][c][r] = sum_{e in t, q} L_a(q) f_c(q), with the channel fields (weighted by
+// w_q h^2) of u = sum_l x_l psi_l:  soft c0 = u;  hard c0 = u, c1..3 = d_s u d_t F - d_t u d_s F,
+// c4..6 = n~ u.
+__global__ void k_p2m(Dims D, Tables T, const double2 *__restrict__ xX, double2 *__restrict__ xhat) {
+  const int nlL = 1 << D.L, e1 = 1 << D.b, p1 = D.p + 1;
+  const long nleaf = (long)D.np * nlL * nlL;
+  const long gst = D.E * D.nq;
+  GRID_STRIDE(o, nleaf * D.Q * D.CR) {
+    long t = o / (D.Q * D.CR);
+    int a = int((o / D.CR) % D.Q), cr = int(o % D.CR), c = cr / D.R, r = cr % D.R;
+    int j = int(t / (nlL * nlL)), cx = int((t / nlL) % nlL), cy = int(t % nlL);
+    int a1 = a / D.q, a2 = a % D.q;
+    double2 acc = cmk(0, 0);
+    for (int ox = 0; ox < e1; ++ox)
+      for (int oy = 0; oy < e1; ++oy) {
+        int ix = cx * e1 + ox, iy = cy * e1 + oy;
+        long e = ((long)j * D.n1 + ix) * D.n1 + iy;
+        for (int q1 = 0; q1 < D.ng; ++q1)
+          for (int q2 = 0; q2 < D.ng; ++q2) {
+            double Lq = T.LG1[(ox * D.ng + q1) * D.q + a1] * T.LG1[(oy * D.ng + q2) * D.q + a2];
+            double W = T.gw[q1] * T.gw[q2] * D.h * D.h * Lq;
+            double2 u = cmk(0, 0), us = cmk(0, 0), ut = cmk(0, 0);
+            for (int ka = 0; ka < p1; ++ka) {
+              double bs = T.phi1[(ix * D.ng + q1) * p1 + ka], ds = T.dphi1[(ix * D.ng + q1) * p1 + ka];
+              for (int kb = 0; kb < p1; ++kb) {
+                double bt = T.phi1[(iy * D.ng + q2) * p1 + kb], dt = T.dphi1[(iy * D.ng + q2) * p1 + kb];
+                double2 xv = xX[xindex(D, j, ix + ka, iy + kb) * D.R + r];
+                u = cadd(u, cscale(xv, bs * bt));
+                if (c >= 1 && c <= 3) {
+                  us = cadd(us, cscale(xv, ds * bt));
+                  ut = cadd(ut, cscale(xv, bs * dt));
+                }
+              }
+            }
+            long iq = e * D.nq + q1 * D.ng + q2;
+            double2 f;
+            if (c == 0) {
+              f = u;
+            } else if (c <= 3) {
+              int d = c - 1;
+              f = csub(cscale(us, T.gft[d * gst + iq]), cscale(ut, T.gfs[d * gst + iq]));
+            } else {
+              f = cscale(u, T.gpn[(c - 4) * gst + iq]);
+            }
+            acc = cadd(acc, cscale(f, W));
+          }
+      }
+    xhat[o] = acc;
+  }
+}
+
+// M2M from level l+1 to level l: xhat_l[t][a][cr] = sum_children sum_b T(c, a, b) xhat_{l+1}[b]
+__global__ void k_m2m(Dims D, int l, const double *__restrict__ T1, const double2 *__restrict__ child,
+                      double2 *__restrict__ parent) {
+  const int nl = 1 << l, nc = 2 * nl;
+  const long n = (long)D.np * nl * nl;
+  GRID_STRIDE(o, n * D.Q * D.CR) {
+    long t = o / (D.Q * D.CR);
+    int a = int((o / D.CR) % D.Q), cr = int(o % D.CR);
+    int j = int(t / (nl * nl)), cx = int((t / nl) % nl), cy = int(t % nl);
+    int a1 = a / D.q, a2 = a % D.q;
+    double2 acc = cmk(0, 0);
+    for (int c1 = 0; c1 < 2; ++c1)
+      for (int c2 = 0; c2 < 2; ++c2) {
+        long tc = ((long)j * nc + 2 * cx + c1) * nc + 2 * cy + c2;
+        const double2 *src = child + tc * D.Q * D.CR;
+        for (int b1 = 0; b1 < D.q; ++b1) {
+          double t1 = T1[(c1 * D.q + a1) * D.q + b1];
+          for (int b2 = 0; b2 < D.q; ++b2)
+            acc = cadd(acc, cscale(src[(b1 * D.q + b2) * D.CR + cr], t1 * T1[(c2 * D.q + a2) * D.q + b2]));
+        }
+      }
+    parent[o] = acc;
+  }
+}
+
+// L2L from level l to level l+1: yhat_{l+1}[t][b][cr] += sum_a T(c, a, b) yhat_l[parent][a][cr]
+__global__ void k_l2l(Dims D, int l, const double *__restrict__ T1, const double2 *__restrict__ parent,
+                      double2 *__restrict__ child) {
+  const int nc = 2 << l, nl = 1 << l;
+  const long n = (long)D.np * nc * nc;
+  GRID_STRIDE(o, n * D.Q * D.CR) {
+    long t = o / (D.Q * D.CR);
+    int b = int((o / D.CR) % D.Q), cr = int(o % D.CR);
+    int j = int(t / (nc * nc)), x = int((t / nc) % nc), y = int(t % nc);
+    int c1 = x & 1, c2 = y & 1;
+    long tp = ((long)j * nl + (x >> 1)) * nl + (y >> 1);
+    int b1 = b / D.q, b2 = b % D.q;
+    const double2 *src = parent + tp * D.Q * D.CR;
+    double2 acc = child[o];
+    for (int a1 = 0; a1 < D.q; ++a1) {
+      double t1 = T1[(c1 * D.q + a1) * D.q + b1];
+      for (int a2 = 0; a2 < D.q; ++a2)
+        acc = cadd(acc, cscale(src[(a1 * D.q + a2) * D.CR + cr], t1 * T1[(c2 * D.q + a2) * D.q + b2]));
+    }
+    child[o] = acc;
+  }
+}
+
+// M2L on level l: yhat[t][a][cr] = sum_{s in far(t)} sum_b S_ts(a, b) xhat[s][b][cr], with the kernel
+// samples between the Chebyshev nodes generated on the fly:
+//   soft: S = a_y G'(r)/r (x-y).n~_x - i eta a_x a_y G      (pull-back of K' - i eta V)
+//   hard: channel 0: S = a_x G'(r)/r (y-x).n~_y  (pull-back of K);  channels 1..6: S = G.
+constexpr int M2L_BT = 16;   // source nodes per tile
+constexpr int M2L_MO = 4;    // outputs per thread
+
+__global__ void k_m2l(Dims D, int ncl, const int *__restrict__ far_ptr, const int *__restrict__ far_src,
+                      const double *__restrict__ nodes, const double2 *__restrict__ xhat,
+                      double2 *__restrict__ yhat, int crc) {
+  extern __shared__ double2 smem[];
+  const int t = blockIdx.x;
+  const int cr0 = blockIdx.y * crc, ncr = min(crc, D.CR - cr0);
+  if (ncr <= 0) return;
+  const int ntypes = D.hard ? 2 : 1;
+  double2 *S = smem;                                   // [ntypes][Q][BT]
+  double2 *Xs = S + ntypes * D.Q * M2L_BT;             // [BT][crc]
+  const long NQ = (long)ncl * D.Q;
+  double2 acc[M2L_MO];
+  for (int k = 0; k < M2L_MO; ++k) acc[k] = cmk(0, 0);
+  const int nout = D.Q * ncr;
+  for (int k = far_ptr[t]; k < far_ptr[t + 1]; ++k) {
+    const int s = far_src[k];
+    for (int b0 = 0; b0 < D.Q; b0 += M2L_BT) {
+      const int nbt = min(M2L_BT, D.Q - b0);
+      for (int i = threadIdx.x; i < D.Q * nbt; i += blockDim.x) {
+        int a = i / nbt, bb = i % nbt;
+        long ia = (long)t * D.Q + a, ib = (long)s * D.Q + b0 + bb;
+        double x[3] = {nodes[ia], nodes[NQ + ia], nodes[2 * NQ + ia]};
+        double y[3] = {nodes[ib], nodes[NQ + ib], nodes[2 * NQ + ib]};
+        double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        KernelVals kv = helmholtz(D.kappa, r);
+        double ax = nodes[6 * NQ + ia], ay = nodes[6 * NQ + ib];
+        if (!D.hard) {
+          double dn = d[0] * nodes[3 * NQ + ia] + d[1] * nodes[4 * NQ + ia] + d[2] * nodes[5 * NQ + ia];
+          double2 kp = cscale(kv.dGr, ay * dn), v = cscale(kv.G, ax * ay);
+          S[a * M2L_BT + bb] = cmk(kp.x + D.eta * v.y, kp.y - D.eta * v.x);
+        } else {
+          double dn = -(d[0] * nodes[3 * NQ + ib] + d[1] * nodes[4 * NQ + ib] + d[2] * nodes[5 * NQ + ib]);
+          S[a * M2L_BT + bb] = cscale(kv.dGr, ax * dn);
+          S[D.Q * M2L_BT + a * M2L_BT + bb] = kv.G;
+        }
+      }
+      for (int i = threadIdx.x; i < nbt * ncr; i += blockDim.x) {
+        int bb = i / ncr, c = i % ncr;
+        Xs[bb * crc + c] = xhat[((long)s * D.Q + b0 + bb) * D.CR + cr0 + c];
+      }
+      __syncthreads();
+      for (int k2 = 0; k2 < M2L_MO; ++k2) {
+        int o = threadIdx.x + k2 * blockDim.x;
+        if (o >= nout) break;
+        int a = o / ncr, c = o % ncr;
+        int type = (D.hard && (cr0 + c) / D.R >= 1) ? 1 : 0;
+        const double2 *Sr = S + type * D.Q * M2L_BT + a * M2L_BT;
+        double2 v = acc[k2];
+        for (int bb = 0; bb < nbt; ++bb) v = cadd(v, cmul(Sr[bb], Xs[bb * crc + c]));
+        acc[k2] = v;
+      }
+      __syncthreads();
+    }
+  }
+  for (int k2 = 0; k2 < M2L_MO; ++k2) {
+    int o = threadIdx.x + k2 * blockDim.x;
+    if (o >= nout) break;
+    int a = o / ncr, c = o % ncr;
+    yhat[((long)t * D.Q + a) * D.CR + cr0 + c] = acc[k2];
+  }
+}
+
+// L2P, step 1: channel values at the Gauss points, g[e][q][cr] = sum_a L_a(q) yhat_leaf[a][cr]
+__global__ void k_l2p_eval(Dims D, Tables T, const double2 *__restrict__ yhat, double2 *__restrict__ g) {
+  const int nlL = 1 << D.L, e1 = 1 << D.b;
+  GRID_STRIDE(o, D.E * D.nq * D.CR) {
+    long e = o / (D.nq * D.CR);
+    int q = int((o / D.CR) % D.nq), cr = int(o % D.CR);
+    int j = int(e / (D.n1 * D.n1)), ix = int((e / D.n1) % D.n1), iy = int(e % D.n1);
+    long t = ((long)j * nlL + (ix >> D.b)) * nlL + (iy >> D.b);
+    int ox = ix & (e1 - 1), oy = iy & (e1 - 1), q1 = q / D.ng, q2 = q % D.ng;
+    const double2 *src = yhat + t * D.Q * D.CR;
+    double2 acc = cmk(0, 0);
+    for (int a1 = 0; a1 < D.q; ++a1) {
+      double l1 = T.LG1[(ox * D.ng + q1) * D.q + a1];
+      for (int a2 = 0; a2 < D.q; ++a2)
+        acc = cadd(acc, cscale(src[(a1 * D.q + a2) * D.CR + cr], l1 * T.LG1[(oy * D.ng + q2) * D.q + a2]));
+    }
+    g[o] = acc;
+  }
+}
+
+// L2P, step 2: test against the leaf-local functions and add to y_leaf:
+//   soft: y_i += sum_q w_q h^2 psi_i(q) g0(q)
+//   hard: y_i += sum_q w_q h^2 [-psi_i g0 - i eta (c_i . g_curl - kappa^2 psi_i n~ . g_n)]
+__global__ void k_l2p_test(Dims D, Tables T, const double2 *__restrict__ g, double2 *__restrict__ yleaf) {
+  const int nlL = 1 << D.L, e1 = 1 << D.b, p1 = D.p + 1;
+  const long nleaf = (long)D.np * nlL * nlL;
+  const long gst = D.E * D.nq;
+  GRID_STRIDE(o, nleaf * D.nL * D.R) {
+    long t = o / (D.nL * D.R);
+    int i = int((o / D.R) % D.nL), r = int(o % D.R);
+    int j = int(t / (nlL * nlL)), cx = int((t / nlL) % nlL), cy = int(t % nlL);
+    int i1 = cx * e1 + i / D.nL1, i2 = cy * e1 + i % D.nL1;
+    double2 acc = cmk(0, 0);
+    for (int ix = max(cx * e1, i1 - D.p); ix <= min(cx * e1 + e1 - 1, i1); ++ix)
+      for (int iy = max(cy * e1, i2 - D.p); iy <= min(cy * e1 + e1 - 1, i2); ++iy) {
+        long e = ((long)j * D.n1 + ix) * D.n1 + iy;
+        int ka = i1 - ix, kb = i2 - iy;
+        for (int q1 = 0; q1 < D.ng; ++q1)
+          for (int q2 = 0; q2 < D.ng; ++q2) {
+            double bs = T.phi1[(ix * D.ng + q1) * p1 + ka], bt = T.phi1[(iy * D.ng + q2) * p1 + kb];
+            double W = T.gw[q1] * T.gw[q2] * D.h * D.h;
+            long iq = e * D.nq + q1 * D.ng + q2;
+            const double2 *gv = g + iq * D.CR;
+            if (!D.hard) {
+              acc = cadd(acc, cscale(gv[r], W * bs * bt));
+            } else {
+              double ds = T.dphi1[(ix * D.ng + q1) * p1 + ka] * bt;
+              double dt = bs * T.dphi1[(iy * D.ng + q2) * p1 + kb];
+              double2 w = cscale(gv[r], -bs * bt);  // -K
+              double2 wc = cmk(0, 0);
+              for (int d = 0; d < 3; ++d) {
+                double cd = ds * T.gft[d * gst + iq] - dt * T.gfs[d * gst + iq];
+                wc = cadd(wc, cscale(gv[(1 + d) * D.R + r], cd));
+                wc = csub(wc, cscale(gv[(4 + d) * D.R + r], D.kappa * D.kappa * bs * bt * T.gpn[d * gst + iq]));
+              }
+              // - i eta wc
+              w = cadd(w, cmk(D.eta * wc.y, -D.eta * wc.x));
+              acc = cadd(acc, cscale(w, W));
+            }
+          }
+      }
+    yleaf[o] = cadd(yleaf[o], acc);
+  }
+}
+
+// y[i][r] = sum_{X in g2x(i)} sum_{leaves t containing X} y_leaf[t][local(X)][r]
+__global__ void k_gather_out(Dims D, const int *__restrict__ g2x_ptr, const int *__restrict__ g2x_idx,
+                             const double2 *__restrict__ yleaf, double2 *__restrict__ y) {
+  const int nlL = 1 << D.L, e1 = 1 << D.b;
+  GRID_STRIDE(o, D.N * D.R) {
+    long gi = o / D.R;
+    int r = int(o % D.R);
+    double2 acc = cmk(0, 0);
+    for (int k = g2x_ptr[gi]; k < g2x_ptr[gi + 1]; ++k) {
+      long X = g2x_idx[k];
+      int j = int(X / ((long)D.nb * D.nb)), i1 = int((X / D.nb) % D.nb), i2 = int(X % D.nb);
+      int cx0 = max(0, (i1 - D.nL1 + e1) / e1), cx1 = min(nlL - 1, i1 / e1);
+      int cy0 = max(0, (i2 - D.nL1 + e1) / e1), cy1 = min(nlL - 1, i2 / e1);
+      for (int cx = cx0; cx <= cx1; ++cx)
+        for (int cy = cy0; cy <= cy1; ++cy) {
+          int li = (i1 - cx * e1) * D.nL1 + (i2 - cy * e1);
+          long t = ((long)j * nlL + cx) * nlL + cy;
+          acc = cadd(acc, yleaf[((size_t)t * D.nL + li) * D.R + r]);
+        }
+    }
+    y[o] = acc;
+  }
+}
+
+}  // namespace
+
+void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                   const double *x, double *y, cudaStream_t st) {
+  Dims D = dims(S, o, R);
+  const int nleaf = S.lev[S.L].n;
+  k_gather_in<<<grid_for(D.NX * R), 256, 0, st>>>(D, d.x2g, reinterpret_cast<const double2 *>(x),
+                                                   reinterpret_cast<double2 *>(d.xX));
+  k_near_spmv<<<nleaf, 128, 0, st>>>(D, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
+                                     reinterpret_cast<const double2 *>(d.xX),
+                                     reinterpret_cast<double2 *>(d.yleaf));
+  if (S.n_far > 0) {
+    Tables T{d.phi1, d.dphi1, d.gw, d.LG1, d.T1, d.gpn, d.gfs, d.gft};
+    auto X = [&](int l) { return reinterpret_cast<double2 *>(d.xhat[l]); };
+    auto Y = [&](int l) { return reinterpret_cast<double2 *>(d.yhat[l]); };
+    long nleafQ = (long)nleaf * D.Q * D.CR;
+    k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
+    for (int l = S.L - 1; l >= S.lmin; --l) {
+      long n = (long)S.lev[l].n * D.Q * D.CR;
+      k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+    }
+    int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
+    int ntypes = D.hard ? 2 : 1;
+    size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
+    IGA_CUDA(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int l = S.lmin; l <= S.L; ++l) {
+      dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);
+      k_m2l<<<grid, 256, smem, st>>>(D, S.lev[l].n, d.far_ptr[l], d.far_src[l], d.nodes[l], X(l), Y(l), crc);
+    }
+    for (int l = S.lmin; l < S.L; ++l) {
+      long n = (long)S.lev[l + 1].n * D.Q * D.CR;
+      k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+    }
+    k_l2p_eval<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, Y(S.L), reinterpret_cast<double2 *>(d.gq));
+    k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.gq),
+                                                                  reinterpret_cast<double2 *>(d.yleaf));
+  }
+  k_gather_out<<<grid_for(D.N * R), 256, 0, st>>>(D, d.g2x_ptr, d.g2x_idx,
+                                                   reinterpret_cast<const double2 *>(d.yleaf),
+                                                   reinterpret_cast<double2 *>(y));
+  IGA_CUDA(cudaGetLastError());
+}
+
+}  // namespace igabem

@@ -1,0 +1,427 @@
+// Set-up kernels: geometry tables at Gauss points and interpolation nodes, and the near-field
+// Galerkin blocks (Sec. 4.2-4.3 with the quadrature rules for regular and touching element pairs).
+#include "internal.h"
+#include "k_common.cuh"
+#include "kernels.h"
+
+namespace igabem {
+
+// ----------------------------------------------------------------------------------------------
+// geometry at the Gauss points of every element: x, n~ = d_s F x d_t F, a = |n~|, d_s F, d_t F
+
+__global__ void k_gauss_geometry(const int *__restrict__ edeg, const long *__restrict__ eoff,
+                                 const double *__restrict__ ebez, const double *__restrict__ gx,
+                                 int E, int ng, double n1, double *gpx, double *gpn, double *gpa,
+                                 double *gfs, double *gft) {
+  long tot = (long)E * ng * ng;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+    int e = int(i / (ng * ng)), q = int(i % (ng * ng));
+    double F[3], Fu[3], Fv[3], fs[3], ft[3], n[3];
+    bez_eval(ebez + eoff[e], edeg[2 * e], edeg[2 * e + 1], gx[q / ng], gx[q % ng], F, Fu, Fv);
+    for (int k = 0; k < 3; ++k) {
+      fs[k] = Fu[k] * n1;  // d/ds = 2^m d/du
+      ft[k] = Fv[k] * n1;
+    }
+    cross3(fs, ft, n);
+    for (int k = 0; k < 3; ++k) {
+      gpx[k * tot + i] = F[k];
+      gpn[k * tot + i] = n[k];
+      gfs[k * tot + i] = fs[k];
+      gft[k * tot + i] = ft[k];
+    }
+    gpa[i] = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  }
+}
+
+// geometry at the Chebyshev nodes of every cluster of level l: [7][n_clusters*q*q] = x, n~, a
+__global__ void k_node_geometry(const int *__restrict__ edeg, const long *__restrict__ eoff,
+                                const double *__restrict__ ebez, const double *__restrict__ cheb,
+                                int n_clusters, int l, int q, int n1, double *out, float *out32) {
+  long tot = (long)n_clusters * q * q;
+  int nl = 1 << l;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+    int t = int(i / (q * q)), a = int(i % (q * q));
+    int j = t / (nl * nl), cx = (t / nl) % nl, cy = t % nl;
+    double s = (cx + cheb[a / q]) / nl, tt = (cy + cheb[a % q]) / nl;
+    int ix = min(int(s * n1), n1 - 1), iy = min(int(tt * n1), n1 - 1);
+    int e = (j * n1 + ix) * n1 + iy;
+    double F[3], Fu[3], Fv[3], fs[3], ft[3], n[3];
+    bez_eval(ebez + eoff[e], edeg[2 * e], edeg[2 * e + 1], s * n1 - ix, tt * n1 - iy, F, Fu, Fv);
+    for (int k = 0; k < 3; ++k) {
+      fs[k] = Fu[k] * n1;
+      ft[k] = Fv[k] * n1;
+    }
+    cross3(fs, ft, n);
+    double v[7] = {F[0], F[1], F[2], n[0], n[1], n[2], sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2])};
+    for (int k = 0; k < 7; ++k) {
+      out[k * tot + i] = v[k];
+      out32[k * tot + i] = (float)v[k];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Kernel of the CFIE for one point pair, split as  ks psi_k(x) psi_l(y) + gc c_k(x) . c_l(y):
+//   sound-soft  ks = a_y G'(r)/r (x-y).n~_x - i eta a_x a_y G,  gc = 0            (K' - i eta V)
+//   sound-hard  ks = -a_x G'(r)/r (y-x).n~_y + i eta kappa^2 (n~_x.n~_y) G,  gc = -i eta G
+//                                                                        (-K - i eta W, Maue)
+
+struct PairKernel {
+  double2 ks, gc;
+};
+
+__device__ inline PairKernel cfie_kernel(bool hard, double kappa, double eta, const double *x,
+                                         const double *nx, double ax, const double *y,
+                                         const double *ny, double ay) {
+  double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+  double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  KernelVals kv = helmholtz(kappa, r);
+  PairKernel pk;
+  if (!hard) {
+    double dn = d[0] * nx[0] + d[1] * nx[1] + d[2] * nx[2];
+    double2 kp = cscale(kv.dGr, ay * dn);
+    double2 v = cscale(kv.G, ax * ay);
+    pk.ks = cmk(kp.x + eta * v.y, kp.y - eta * v.x);  // kp - i eta v
+    pk.gc = cmk(0.0, 0.0);
+  } else {
+    double dn = -(d[0] * ny[0] + d[1] * ny[1] + d[2] * ny[2]);
+    double2 kk = cscale(kv.dGr, ax * dn);
+    double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+    double2 g = kv.G;
+    // -kk + i eta kappa^2 nn G
+    double f = eta * kappa * kappa * nn;
+    pk.ks = cmk(-kk.x - f * g.y, -kk.y + f * g.x);
+    pk.gc = cmk(eta * g.y, -eta * g.x);  // -i eta G
+  }
+  return pk;
+}
+
+// ----------------------------------------------------------------------------------------------
+// regular element pairs of the near field: tensor Gauss rule on both elements
+
+struct NearArgs {
+  const double *gpx, *gpn, *gpa, *gfs, *gft;  // Gauss-point geometry, SoA with stride gstride
+  const double *phi1, *dphi1, *ext1, *gw, *corners;
+  const int *edeg;
+  const long *eoff;
+  const double *ebez;
+  const int *near_tgt, *near_src;
+  long gstride;
+  int n1, ng, p, nloc, b, nL1, nL, L;
+  double h, kappa, eta, tol;
+  bool hard;
+  double2 *blk;
+};
+
+__device__ inline int leaf_local(int ix, int iy, int ka, int kb, int b, int nL1) {
+  int mask = (1 << b) - 1;
+  return ((ix & mask) + ka) * nL1 + (iy & mask) + kb;
+}
+
+__device__ inline void block_add(double2 *B, int nL, int row, int col, double2 v) {
+  double2 *dst = B + (size_t)col * nL + row;
+  atomicAdd(&dst->x, v.x);
+  atomicAdd(&dst->y, v.y);
+}
+
+// basis value and d/ds, d/dt of local function k at Gauss point q of element column (ix, iy)
+__device__ inline void basis_gp(const NearArgs &A, int ix, int iy, int k, int q, double &v,
+                                double &ds, double &dt) {
+  int p1 = A.p + 1, ka = k / p1, kb = k % p1, q1 = q / A.ng, q2 = q % A.ng;
+  double b1 = A.phi1[(ix * A.ng + q1) * p1 + ka], b2 = A.phi1[(iy * A.ng + q2) * p1 + kb];
+  v = b1 * b2;
+  ds = A.dphi1[(ix * A.ng + q1) * p1 + ka] * b2;
+  dt = b1 * A.dphi1[(iy * A.ng + q2) * p1 + kb];
+}
+
+// c_k = d_s psi_k d_t F - d_t psi_k d_s F at Gauss point q of element e
+__device__ inline void curl_gp(const NearArgs &A, long iq, double ds, double dt, double c[3]) {
+  for (int d = 0; d < 3; ++d)
+    c[d] = ds * A.gft[d * A.gstride + iq] - dt * A.gfs[d * A.gstride + iq];
+}
+
+__device__ inline bool touching(const NearArgs &A, int e, int f) {
+  if (e == f) return true;
+  for (int c = 0; c < 16; ++c) {
+    const double *pa = A.corners + (e * 4 + (c >> 2)) * 3, *pb = A.corners + (f * 4 + (c & 3)) * 3;
+    double dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+    if (sqrt(dx * dx + dy * dy + dz * dz) <= A.tol) return true;
+  }
+  return false;
+}
+
+// One block of threads per near leaf pair, one warp per element pair (touching pairs skipped:
+// k_near_singular integrates them).  Block entry (k of e, l of f) +=
+//   sum_{q,r} w_q w_r h^4 [ks(q,r) psi_k(q) psi_l(r) + gc(q,r) c_k(q) . c_l(r)].
+__global__ void k_near_regular(NearArgs A) {
+  extern __shared__ double2 sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int nq = A.ng * A.ng, nloc = A.nloc, p1 = A.p + 1;
+  const int per = 2 * nq * nq + 4 * nq * nloc;
+  double2 *ks = sm + warp * per, *gc = ks + nq * nq, *T = gc + nq * nq, *Tc = T + nq * nloc;
+  const int bid = blockIdx.x;
+  const int tgt = A.near_tgt[bid], src = A.near_src[bid];
+  const int nlL = 1 << A.L, ne1 = 1 << A.b;
+  const int jt = tgt / (nlL * nlL), cxt = (tgt / nlL) % nlL, cyt = tgt % nlL;
+  const int js = src / (nlL * nlL), cxs = (src / nlL) % nlL, cys = src % nlL;
+  double2 *B = A.blk + (size_t)bid * A.nL * A.nL;
+  const long st = A.gstride;
+  const double h4 = A.h * A.h * A.h * A.h;
+  const int npair = ne1 * ne1 * ne1 * ne1;
+  for (int pr = warp; pr < npair; pr += nwarp) {
+    int et = pr / (ne1 * ne1), es = pr % (ne1 * ne1);
+    int ixe = cxt * ne1 + et / ne1, iye = cyt * ne1 + et % ne1;
+    int ixf = cxs * ne1 + es / ne1, iyf = cys * ne1 + es % ne1;
+    int e = (jt * A.n1 + ixe) * A.n1 + iye, f = (js * A.n1 + ixf) * A.n1 + iyf;
+    if (touching(A, e, f)) continue;  // warp-uniform
+    for (int i = lane; i < nq * nq; i += 32) {
+      int q = i / nq, r = i % nq;
+      long iq = (long)e * nq + q, ir = (long)f * nq + r;
+      double x[3] = {A.gpx[iq], A.gpx[st + iq], A.gpx[2 * st + iq]};
+      double nx[3] = {A.gpn[iq], A.gpn[st + iq], A.gpn[2 * st + iq]};
+      double y[3] = {A.gpx[ir], A.gpx[st + ir], A.gpx[2 * st + ir]};
+      double ny[3] = {A.gpn[ir], A.gpn[st + ir], A.gpn[2 * st + ir]};
+      PairKernel pk = cfie_kernel(A.hard, A.kappa, A.eta, x, nx, A.gpa[iq], y, ny, A.gpa[ir]);
+      double w = A.gw[q / A.ng] * A.gw[q % A.ng] * A.gw[r / A.ng] * A.gw[r % A.ng] * h4;
+      ks[i] = cscale(pk.ks, w);
+      gc[i] = cscale(pk.gc, w);
+    }
+    __syncwarp();
+    for (int i = lane; i < nq * nloc; i += 32) {
+      int q = i / nloc, l = i % nloc;
+      double2 t = cmk(0, 0), c0 = cmk(0, 0), c1 = cmk(0, 0), c2 = cmk(0, 0);
+      for (int r = 0; r < nq; ++r) {
+        double v, ds, dt;
+        basis_gp(A, ixf, iyf, l, r, v, ds, dt);
+        t = cadd(t, cscale(ks[q * nq + r], v));
+        if (A.hard) {
+          double cl[3];
+          curl_gp(A, (long)f * nq + r, ds, dt, cl);
+          double2 g = gc[q * nq + r];
+          c0 = cadd(c0, cscale(g, cl[0]));
+          c1 = cadd(c1, cscale(g, cl[1]));
+          c2 = cadd(c2, cscale(g, cl[2]));
+        }
+      }
+      T[i] = t;
+      if (A.hard) {
+        Tc[i] = c0;
+        Tc[nq * nloc + i] = c1;
+        Tc[2 * nq * nloc + i] = c2;
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < nloc * nloc; i += 32) {
+      int k = i / nloc, l = i % nloc;
+      double2 acc = cmk(0, 0);
+      for (int q = 0; q < nq; ++q) {
+        double v, ds, dt;
+        basis_gp(A, ixe, iye, k, q, v, ds, dt);
+        acc = cadd(acc, cscale(T[q * nloc + l], v));
+        if (A.hard) {
+          double ck[3];
+          curl_gp(A, (long)e * nq + q, ds, dt, ck);
+          for (int d = 0; d < 3; ++d) acc = cadd(acc, cscale(Tc[d * nq * nloc + q * nloc + l], ck[d]));
+        }
+      }
+      block_add(B, A.nL, leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1),
+                leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1), acc);
+    }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// touching element pairs: regularising transforms (identical 8, common edge 6, common vertex 4
+// regions) with the canonical position given by the square symmetries (Te, Tf) found on the host.
+// For identical pairs the half mass matrix 1/2 M (regular Gauss rule) is added as well.
+
+struct SingArgs {
+  NearArgs A;
+  const int *touch, *touch_blk;
+  const double *rule[3];  // per kind: x1, x2, y1, y2, w arrays of n points, concatenated
+  int rule_n[3];
+};
+
+// basis values (and d/ds, d/dt) of the nloc local functions at local point (u, v) of element
+// column (ix, iy), by Bernstein extraction
+__device__ inline void basis_at(const NearArgs &A, int ix, int iy, double u, double v, double *val,
+                                double *ds, double *dt) {
+  int p = A.p, p1 = p + 1;
+  double Bu[8], dBu[8], Bv[8], dBv[8];
+  bernstein_all(p, u, Bu, dBu);
+  bernstein_all(p, v, Bv, dBv);
+  double fu[8], dfu[8], fv[8], dfv[8];
+  for (int a = 0; a <= p; ++a) {
+    double s0 = 0, s1 = 0, t0 = 0, t1 = 0;
+    for (int c = 0; c <= p; ++c) {
+      double ea = A.ext1[(ix * p1 + a) * p1 + c], eb = A.ext1[(iy * p1 + a) * p1 + c];
+      s0 += ea * Bu[c]; s1 += ea * dBu[c];
+      t0 += eb * Bv[c]; t1 += eb * dBv[c];
+    }
+    fu[a] = s0; dfu[a] = s1 * A.n1; fv[a] = t0; dfv[a] = t1 * A.n1;
+  }
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= p; ++b) {
+      val[a * p1 + b] = fu[a] * fv[b];
+      if (ds) {
+        ds[a * p1 + b] = dfu[a] * fv[b];
+        dt[a * p1 + b] = fu[a] * dfv[b];
+      }
+    }
+}
+
+constexpr int SING_CHUNK = 64;
+constexpr int SING_MAXACC = 20;
+
+__global__ void k_near_singular(SingArgs S) {
+  const NearArgs &A = S.A;
+  extern __shared__ double smd[];
+  const int nloc = A.nloc, p1 = A.p + 1;
+  // shared: ks[C], gc[C] (complex), phx[C][nloc], phy[C][nloc], cx[C][nloc][3], cy[C][nloc][3]
+  double2 *ks = reinterpret_cast<double2 *>(smd), *gc = ks + SING_CHUNK;
+  double *phx = reinterpret_cast<double *>(gc + SING_CHUNK), *phy = phx + SING_CHUNK * nloc;
+  double *cxs = phy + SING_CHUNK * nloc, *cys = cxs + 3 * SING_CHUNK * nloc;
+  const int pid = blockIdx.x;
+  const int e = S.touch[5 * pid], f = S.touch[5 * pid + 1], kind = S.touch[5 * pid + 2];
+  const int te = S.touch[5 * pid + 3], tf = S.touch[5 * pid + 4];
+  const int ri = kind == 0 ? 0 : (kind == 2 ? 1 : 2);
+  const int npt = S.rule_n[ri];
+  const double *R = S.rule[ri];
+  const int n1 = A.n1;
+  const int ixe = (e / n1) % n1, iye = e % n1, ixf = (f / n1) % n1, iyf = f % n1;
+  const double h4 = A.h * A.h * A.h * A.h;
+  double2 acc[SING_MAXACC];
+  for (int i = 0; i < SING_MAXACC; ++i) acc[i] = cmk(0, 0);
+  for (int c0 = 0; c0 < npt; c0 += SING_CHUNK) {
+    int cn = min(SING_CHUNK, npt - c0);
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+      int ip = c0 + t;
+      double ue, ve, uf, vf;
+      d4_apply(te, R[ip], R[npt + ip], ue, ve);
+      d4_apply(tf, R[2 * npt + ip], R[3 * npt + ip], uf, vf);
+      double w = R[4 * npt + ip] * h4;
+      double X[3], Xu[3], Xv[3], Y[3], Yu[3], Yv[3], fs[3], ft[3], gs[3], gt[3], nx[3], ny[3];
+      bez_eval(A.ebez + A.eoff[e], A.edeg[2 * e], A.edeg[2 * e + 1], ue, ve, X, Xu, Xv);
+      bez_eval(A.ebez + A.eoff[f], A.edeg[2 * f], A.edeg[2 * f + 1], uf, vf, Y, Yu, Yv);
+      for (int k = 0; k < 3; ++k) {
+        fs[k] = Xu[k] * n1; ft[k] = Xv[k] * n1; gs[k] = Yu[k] * n1; gt[k] = Yv[k] * n1;
+      }
+      cross3(fs, ft, nx);
+      cross3(gs, gt, ny);
+      double ax = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
+      double ay = sqrt(ny[0] * ny[0] + ny[1] * ny[1] + ny[2] * ny[2]);
+      PairKernel pk = cfie_kernel(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay);
+      ks[t] = cscale(pk.ks, w);
+      gc[t] = cscale(pk.gc, w);
+      double dsx[49], dtx[49], dsy[49], dty[49];
+      basis_at(A, ixe, iye, ue, ve, phx + t * nloc, dsx, dtx);
+      basis_at(A, ixf, iyf, uf, vf, phy + t * nloc, dsy, dty);
+      if (A.hard) {
+        for (int k = 0; k < nloc; ++k)
+          for (int d = 0; d < 3; ++d) {
+            cxs[(t * nloc + k) * 3 + d] = dsx[k] * ft[d] - dtx[k] * fs[d];
+            cys[(t * nloc + k) * 3 + d] = dsy[k] * gt[d] - dty[k] * gs[d];
+          }
+      }
+    }
+    __syncthreads();
+    int slot = 0;
+    for (int i = threadIdx.x; i < nloc * nloc; i += blockDim.x, ++slot) {
+      int k = i / nloc, l = i % nloc;
+      double2 a = acc[slot];
+      for (int t = 0; t < cn; ++t) {
+        a = cadd(a, cscale(ks[t], phx[t * nloc + k] * phy[t * nloc + l]));
+        if (A.hard) {
+          const double *ck = cxs + (t * nloc + k) * 3, *cl = cys + (t * nloc + l) * 3;
+          a = cadd(a, cscale(gc[t], ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2]));
+        }
+      }
+      acc[slot] = a;
+    }
+    __syncthreads();
+  }
+  double2 *B = A.blk + (size_t)S.touch_blk[pid] * A.nL * A.nL;
+  const int nq = A.ng * A.ng;
+  int slot = 0;
+  for (int i = threadIdx.x; i < nloc * nloc; i += blockDim.x, ++slot) {
+    int k = i / nloc, l = i % nloc;
+    double2 a = acc[slot];
+    if (kind == 0) {  // + 1/2 M_kl = 1/2 sum_q w_q h^2 a_q psi_k psi_l
+      double m = 0;
+      for (int q = 0; q < nq; ++q) {
+        double vk, vl, d1, d2;
+        basis_gp(A, ixe, iye, k, q, vk, d1, d2);
+        basis_gp(A, ixe, iye, l, q, vl, d1, d2);
+        m += A.gw[q / A.ng] * A.gw[q % A.ng] * A.gpa[(long)e * nq + q] * vk * vl;
+      }
+      a.x += 0.5 * m * A.h * A.h;
+    }
+    block_add(B, A.nL, leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1),
+              leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1), a);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// launchers
+
+void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st) {
+  long tot = (long)S.E * S.ng * S.ng;
+  int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+  k_gauss_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, d.gx, S.E, S.ng, (double)S.n1,
+                                         d.gpx, d.gpn, d.gpa, d.gfs, d.gft);
+}
+
+void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st) {
+  for (int l = 0; l <= S.L; ++l) {
+    long tot = (long)S.lev[l].n * S.q * S.q;
+    int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, cheb, S.lev[l].n, l, S.q, S.n1,
+                                          d.nodes[l], d.nodes32[l]);
+  }
+}
+
+static NearArgs near_args(const DeviceProblem &d, const HostSetup &S, const igabem_options &o) {
+  NearArgs A;
+  A.gpx = d.gpx; A.gpn = d.gpn; A.gpa = d.gpa; A.gfs = d.gfs; A.gft = d.gft;
+  A.phi1 = d.phi1; A.dphi1 = d.dphi1; A.ext1 = d.ext1; A.gw = d.gw; A.corners = d.corners;
+  A.edeg = d.edeg; A.eoff = d.eoff; A.ebez = d.ebez;
+  A.near_tgt = d.near_tgt; A.near_src = d.near_src;
+  A.gstride = (long)S.E * S.ng * S.ng;
+  A.n1 = S.n1; A.ng = S.ng; A.p = S.p; A.nloc = S.nloc; A.b = S.b; A.nL1 = S.nL1; A.nL = S.nL;
+  A.L = S.L; A.h = S.h; A.kappa = o.kappa; A.eta = o.eta_cfie; A.tol = 1e-10 * S.scale;
+  A.hard = S.hard;
+  A.blk = reinterpret_cast<double2 *>(d.blk);
+  return A;
+}
+
+void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
+                       cudaStream_t st) {
+  NearArgs A = near_args(d, S, o);
+  int nblk = (int)S.near_src.size();
+  if (nblk > 0) {
+    int nq = S.ng * S.ng;
+    size_t per = (size_t)(2 * nq * nq + 4 * nq * S.nloc) * sizeof(double2);
+    int warps = 4;
+    size_t smem = per * warps;
+    IGA_CUDA(cudaFuncSetAttribute(k_near_regular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_near_regular<<<nblk, 32 * warps, smem, st>>>(A);
+    IGA_CUDA(cudaGetLastError());
+  }
+  SingArgs SA;
+  SA.A = A;
+  SA.touch = d.touch;
+  SA.touch_blk = d.touch_blk;
+  for (int k = 0; k < 3; ++k) {
+    SA.rule[k] = d.rule[k];
+    SA.rule_n[k] = d.rule_n[k];
+  }
+  int npt = (int)S.touch.size() / 5;
+  if (S.nloc * S.nloc > SING_MAXACC * 128) fail(IGABEM_EINVAL, "degree_p too large for the singular kernel");
+  size_t smem = (size_t)SING_CHUNK * (4 + 8 * S.nloc) * sizeof(double);
+  IGA_CUDA(cudaFuncSetAttribute(k_near_singular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_near_singular<<<npt, 128, smem, st>>>(SA);
+  IGA_CUDA(cudaGetLastError());
+}
+
+}  // namespace igabem

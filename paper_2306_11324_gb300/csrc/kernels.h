@@ -1,0 +1,42 @@
+// Kernel launchers (host functions defined in the .cu files).
+#pragma once
+
+#include "internal.h"
+
+namespace igabem {
+
+// set-up (k_setup.cu)
+void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
+void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st);
+void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
+                       cudaStream_t st);
+
+// operator application (k_apply.cu): y = A x for R columns, x and y device [N][R] complex
+void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                   const double *x, double *y, cudaStream_t st);
+
+// right-hand sides and far field (k_solver.cu)
+void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                const double *dirs_dev, double *b, cudaStream_t st);
+void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                     const double *dens, int n_dir, const double *xhat_dev, double *uinf,
+                     cudaStream_t st);
+
+// GMRES vector kernels (k_solver.cu); vectors [N][R] complex, per-column results [.][R]
+// h[i][r] = sum_n conj(V_i[n][r]) w[n][r] for i < nv (V_i = V + i*N*R)
+void launch_multidot(const double *V, int nv, const double *w, long N, int R, double *red,
+                     double *h, cudaStream_t st);
+// w[n][r] -= sum_i V_i[n][r] h[i][r]
+void launch_multiaxpy(const double *V, int nv, const double *h, double *w, long N, int R,
+                      cudaStream_t st);
+// x[n][r] += sum_i V_i[n][r] y[i][r]
+void launch_update(const double *V, int nv, const double *y, double *x, long N, int R,
+                   cudaStream_t st);
+// nrm[r] = ||w[:, r]||_2
+void launch_norms(const double *w, long N, int R, double *red, double *nrm, cudaStream_t st);
+// w[n][r] *= s[r] (real), dst may equal w
+void launch_scale(const double *w, const double *s, double *dst, long N, int R, cudaStream_t st);
+// r = b - y
+void launch_sub(const double *b, const double *y, double *r, long n, cudaStream_t st);
+
+}  // namespace igabem

@@ -1,0 +1,82 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element, on
+small seeded problems that span several clusters and leaf blocks."""
+import numpy as np
+import pytest
+
+from oracle import assemble as A
+from oracle import farfield, fmm, mie, solve
+from paper_2306_11324_gb300 import binding as B
+from paper_2306_11324_gb300 import inputs
+from tests import gpu_util as G
+from tests import oracle_cache as C
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10        # same definitions in FP64: only rounding order differs
+DIRS = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8], [0.0, -1.0, 0.0]])
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_rhs(hard):
+    prob, info = G.problem(level_m=2, degree_p=1, kappa=1.0, eta_cfie=1.0, bc=int(hard), no_fmm=1)
+    b = B.igabem_rhs(prob, DIRS, info["n_dofs"])
+    sp = C.sphere_space(2, 1, hard)
+    ref = A.rhs(sp, 1.0, 1.0, DIRS, hard)
+    assert info["n_dofs"] == sp.N
+    assert G.rel(b, ref) < FP64_TOL
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_dense_matvec_matches_exact_galerkin_matrix(hard):
+    """no_fmm: every element pair in the near field, i.e. the exact ("mode A") Galerkin matrix."""
+    prob, info = G.problem(level_m=2, degree_p=1, kappa=1.0, eta_cfie=1.0, bc=int(hard), no_fmm=1)
+    sp = C.sphere_space(2, 1, hard)
+    Amat = C.cfie(2, 1, 1.0, 1.0, hard)
+    x = inputs.random_complex(sp.N, seed=1234, cols=2)
+    y = B.igabem_matvec(prob, x)
+    assert G.rel(y, Amat @ x) < FP64_TOL
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("hard,leaf,q", [(False, 2, 3), (False, 1, 5), (True, 2, 3)])
+def test_fmm_matvec_matches_interpolated_kernel_matrix(hard, leaf, q):
+    """FMM matvec = the oracle's mode-B matrix (interpolated kernel on admissible blocks)."""
+    m, p, kappa = 2, 1, 1.0
+    prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard),
+                           cheb_q=q, leaf_offset=m - leaf, eta_adm=0.5)
+    assert info["n_far_pairs"] == sum(len(f) for f in C.tree(m, p, leaf, 0.5, q, kappa, hard).far)
+    sp = C.sphere_space(m, p, hard)
+    Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
+    x = inputs.random_complex(sp.N, seed=1234)
+    y = B.igabem_matvec(prob, x)
+    assert G.rel(y, Amat @ x) < FP64_TOL
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_farfield(hard):
+    prob, info = G.problem(level_m=2, degree_p=1, kappa=2.0, eta_cfie=2.0, bc=int(hard), no_fmm=1)
+    sp = C.sphere_space(2, 1, hard)
+    x = inputs.random_complex(sp.N, seed=7, cols=2)
+    xh = inputs.fibonacci_directions(37)
+    u = B.igabem_farfield(prob, x, xh)
+    ref = np.stack([farfield.far_field(sp, 2.0, x[:, r], xh, hard) for r in range(2)], axis=1)
+    assert G.rel(u, ref) < FP64_TOL
+    B.igabem_problem_destroy(prob)
+
+
+def test_solve_sound_soft_sphere():
+    """GMRES(30) on the GPU reaches the oracle's LU solution; the far field matches Mie."""
+    prob, info = G.problem(level_m=2, degree_p=1, kappa=1.0, eta_cfie=1.0, no_fmm=1, tol=1e-10)
+    sp = C.sphere_space(2, 1)
+    Amat = C.cfie(2, 1, 1.0, 1.0, False)
+    d = np.array([[0.0, 0.0, 1.0]])
+    x, sinfo = B.igabem_solve(prob, d, info["n_dofs"])
+    ref = solve.lu_solve(Amat, A.rhs(sp, 1.0, 1.0, d[0], False))
+    assert sinfo["rel_residual"] <= 1e-10
+    assert G.rel(x[:, 0], ref) < 1e-8
+    xh = inputs.fibonacci_directions(100)
+    u = B.igabem_farfield(prob, x, xh)[:, 0]
+    assert G.rel(u, mie.mie_far_field(1.0, xh)) < 2e-4
+    B.igabem_problem_destroy(prob)

@@ -100,6 +100,36 @@ typedef struct {
   double solve_ms;           /* wall time of the call */
 } igabem_solve_info;
 
+/* Phases of the per-problem profile. */
+enum {
+  IGABEM_PH_SETUP_TABLES = 0,  /* geometry at Gauss points and interpolation nodes */
+  IGABEM_PH_SETUP_NEAR,        /* near-field Galerkin quadrature (regular and touching pairs) */
+  IGABEM_PH_GATHER,            /* global <-> patch-wise / leaf-local vector gathers */
+  IGABEM_PH_NEAR,              /* near-field block SpMV */
+  IGABEM_PH_P2M,               /* leaf moments */
+  IGABEM_PH_M2M,               /* upward transfers */
+  IGABEM_PH_M2L,               /* admissible-pair couplings with on-the-fly kernel samples */
+  IGABEM_PH_L2L,               /* downward transfers */
+  IGABEM_PH_L2P,               /* evaluation and testing at the Gauss points */
+  IGABEM_PH_KRYLOV,            /* GMRES vector kernels */
+  IGABEM_PH_RHS,               /* right-hand sides */
+  IGABEM_PH_FARFIELD,          /* far-field pattern */
+  IGABEM_NPHASE
+};
+
+typedef struct {
+  long launches;                 /* kernels launched for the problem (always counted) */
+  double ms[IGABEM_NPHASE];      /* device time per phase, CUDA events (only while enabled) */
+  long calls[IGABEM_NPHASE];     /* timed executions per phase */
+  long phase_launches[IGABEM_NPHASE]; /* kernels launched per phase (always counted) */
+} igabem_profile;
+
+/* Turns per-phase timing with CUDA events on the context's stream on (1) or off (0). */
+int igabem_profile_enable(igabem_problem *prob, int on);
+
+/* Copies the problem's counters; reset != 0 clears them afterwards. */
+int igabem_profile_get(igabem_problem *prob, igabem_profile *out, int reset);
+
 /* Last error message of the calling thread ("" if none). */
 const char *igabem_last_error(void);
 

@@ -43,6 +43,15 @@ class igabem_solve_info(ctypes.Structure):
                 ("solve_ms", c_double)]
 
 
+PHASES = ["setup_tables", "setup_near", "gather", "near", "p2m", "m2m", "m2l", "l2l", "l2p", "krylov",
+          "rhs", "farfield"]
+
+
+class igabem_profile(ctypes.Structure):
+    _fields_ = [("launches", c_long), ("ms", c_double * len(PHASES)), ("calls", c_long * len(PHASES)),
+                ("phase_launches", c_long * len(PHASES))]
+
+
 class IgabemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -67,6 +76,8 @@ SIGNATURES = {
     "igabem_matvec": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
     "igabem_farfield": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    "igabem_profile_enable": (c_int, [c_void_p, c_int]),
+    "igabem_profile_get": (c_int, [c_void_p, ctypes.POINTER(igabem_profile), c_int]),
 }
 
 
@@ -208,6 +219,18 @@ def igabem_farfield(prob, density, xhat, out=None):
     out = _like(density, (xh.shape[0], R)) if out is None else out
     _check(lib().igabem_farfield(prob, R, _ptr(density), xh.shape[0], _ptr(xh), _ptr(out)))
     return out
+
+
+def igabem_profile_enable(prob, on: bool = True):
+    _check(lib().igabem_profile_enable(prob, 1 if on else 0))
+
+
+def igabem_profile_get(prob, reset: bool = False) -> dict:
+    p = igabem_profile()
+    _check(lib().igabem_profile_get(prob, ctypes.byref(p), 1 if reset else 0))
+    return {"launches": p.launches,
+            "phases": {name: {"ms": p.ms[i], "calls": p.calls[i], "launches": p.phase_launches[i]}
+                       for i, name in enumerate(PHASES)}}
 
 
 def header_symbols() -> list[str]:

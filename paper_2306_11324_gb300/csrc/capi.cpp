@@ -87,11 +87,6 @@ void Arena::release() {
   cap = off = 0;
 }
 
-// sizes of the per-call work buffers for R columns
-struct WorkPlan {
-  size_t bytes = 0;
-};
-
 }  // namespace igabem
 
 using namespace igabem;
@@ -107,8 +102,6 @@ struct ProblemWork {
 };
 
 namespace {
-
-std::vector<ProblemWork *> g_unused;  // placeholder to keep the translation unit simple
 
 struct ProblemExt {
   ProblemWork work;
@@ -372,6 +365,7 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
       P->arena.reserve(total);
       Arena &A = P->arena;
       DeviceProblem &d = P->d;
+      d.prof = &P->prof;
       d.edeg = upload(A, S.edeg, st);
       d.eoff = upload(A, S.eoff, st);
       d.ebez = upload(A, S.ebez, st);
@@ -418,6 +412,7 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
       launch_near_field(d, S, *opt, st);
       IGA_CUDA(cudaStreamSynchronize(st));
       IGA_CUDA(cudaGetLastError());
+      P->prof.flush();
       igabem_info &I = P->info;
       I.n_dofs = S.N;
       I.n_patch_dofs = S.NX;
@@ -465,6 +460,27 @@ void igabem_problem_destroy(igabem_problem *prob) {
   delete prob;
 }
 
+int igabem_profile_enable(igabem_problem *P, int on) {
+  return guarded([&] {
+    if (!P) fail(IGABEM_EINVAL, "NULL problem");
+    P->prof.on = on != 0;
+  });
+}
+
+int igabem_profile_get(igabem_problem *P, igabem_profile *out, int reset) {
+  return guarded([&] {
+    if (!P || !out) fail(IGABEM_EINVAL, "NULL argument");
+    P->prof.flush();
+    out->launches = P->prof.launches;
+    for (int i = 0; i < IGABEM_NPHASE; ++i) {
+      out->ms[i] = P->prof.ms[i];
+      out->calls[i] = P->prof.calls[i];
+      out->phase_launches[i] = P->prof.phase_launches[i];
+    }
+    if (reset) P->prof.reset();
+  });
+}
+
 int igabem_rhs(igabem_problem *P, int n_rhs, const double *dirs, void *b) {
   return guarded([&] {
     if (!P || !dirs || !b || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid rhs arguments");
@@ -480,6 +496,7 @@ int igabem_rhs(igabem_problem *P, int n_rhs, const double *dirs, void *b) {
     if (!dev)
       IGA_CUDA(cudaMemcpyAsync(b, out, P->S.N * n_rhs * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IGA_CUDA(cudaStreamSynchronize(st));
+    P->prof.flush();
   });
 }
 
@@ -498,6 +515,7 @@ int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
     matvec_dev(P, n_rhs, xi, yo);
     if (!dy) IGA_CUDA(cudaMemcpyAsync(y, yo, bytes, cudaMemcpyDeviceToHost, st));
     IGA_CUDA(cudaStreamSynchronize(st));
+    P->prof.flush();
   });
 }
 
@@ -519,7 +537,10 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     launch_rhs(P->d, S, P->opt, R, W.red, W.b, st);
     std::vector<double> bn(R), beta(R), hn(R), s(R);
     auto norms = [&](const double *v, std::vector<double> &out) {
-      launch_norms(v, N, R, W.red, W.nrm, st);
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_norms(v, N, R, W.red, W.nrm, st);
+      }
       IGA_CUDA(cudaMemcpyAsync(out.data(), W.nrm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
       IGA_CUDA(cudaStreamSynchronize(st));
     };
@@ -548,15 +569,21 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
         s[r] = active[r] ? 1.0 / beta[r] : 0.0;
       }
       IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
-      launch_scale(W.r, W.sdev, W.V, N, R, st);
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_scale(W.r, W.sdev, W.V, N, R, st);
+      }
       for (int j = 0; j < m; ++j) {
         double *Vj = W.V + (size_t)j * N * R * 2;
         matvec_dev(P, R, Vj, W.w);
         ++n_mv;
         std::vector<cd> h((j + 1) * R, 0.0);
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          launch_multidot(W.V, j + 1, W.w, N, R, W.red, W.hdev, st);
-          launch_multiaxpy(W.V, j + 1, W.hdev, W.w, N, R, st);
+          {
+            Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+            launch_multidot(W.V, j + 1, W.w, N, R, W.red, W.hdev, st);
+            launch_multiaxpy(W.V, j + 1, W.hdev, W.w, N, R, st);
+          }
           IGA_CUDA(cudaMemcpyAsync(hbuf.data(), W.hdev, (j + 1) * R * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
           IGA_CUDA(cudaStreamSynchronize(st));
           for (int i = 0; i < (j + 1) * R; ++i) h[i] += cd(hbuf[2 * i], hbuf[2 * i + 1]);
@@ -564,7 +591,10 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
         norms(W.w, hn);
         for (int r = 0; r < R; ++r) s[r] = (!col[r].done && hn[r] > 0) ? 1.0 / hn[r] : 0.0;
         IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
-        launch_scale(W.w, W.sdev, W.V + (size_t)(j + 1) * N * R * 2, N, R, st);
+        {
+          Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+          launch_scale(W.w, W.sdev, W.V + (size_t)(j + 1) * N * R * 2, N, R, st);
+        }
         bool all_done = true;
         for (int r = 0; r < R; ++r) {
           Col &c = col[r];
@@ -611,10 +641,16 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
         kmax = std::max(kmax, c.k);
       }
       IGA_CUDA(cudaMemcpyAsync(W.ydev, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-      launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+      }
       matvec_dev(P, R, W.x, W.w);
       ++n_mv;
-      launch_sub(W.b, W.w, W.r, N * R * 2, st);
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_sub(W.b, W.w, W.r, N * R * 2, st);
+      }
       norms(W.r, beta);
       for (int r = 0; r < R; ++r) {
         if (!std::isfinite(beta[r])) fail(IGABEM_ENUMERIC, "GMRES met a non-finite residual");
@@ -627,6 +663,7 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     else
       IGA_CUDA(cudaMemcpyAsync(density, W.x, vb, cudaMemcpyDeviceToHost, st));
     IGA_CUDA(cudaStreamSynchronize(st));
+    P->prof.flush();
     double worst = 0;
     for (int r = 0; r < R; ++r) worst = std::max(worst, bn[r] > 0 ? beta[r] / bn[r] : 0.0);
     if (info) {
@@ -666,6 +703,7 @@ int igabem_farfield(igabem_problem *P, int n_rhs, const void *density, int n_dir
     IGA_CUDA(cudaFreeAsync(dx, st));
     IGA_CUDA(cudaFreeAsync(du_, st));
     IGA_CUDA(cudaStreamSynchronize(st));
+    P->prof.flush();
   });
 }
 

@@ -123,8 +123,41 @@ struct igabem_geom {
 
 namespace igabem {
 
+// Per-problem profile: launch counters (always) and per-phase CUDA-event timing (when enabled).
+struct Profiler {
+  bool on = false;
+  long launches = 0;
+  long phase_launches[IGABEM_NPHASE] = {};
+  double ms[IGABEM_NPHASE] = {};
+  long calls[IGABEM_NPHASE] = {};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t event();
+  void flush();  // accumulates pending event pairs; call after the stream has been synchronised
+  void reset();
+  ~Profiler();
+};
+
+// Scope of one phase on a stream: records start/stop events when timing is on, and makes
+// note_launch() count launches against this phase.
+class Phase {
+ public:
+  Phase(Profiler *p, int phase, cudaStream_t st);
+  ~Phase();
+
+ private:
+  Profiler *p_;
+  int ph_;
+  cudaStream_t st_;
+  cudaEvent_t a_ = nullptr;
+  Profiler *prev_p_;
+  int prev_ph_;
+};
+void note_launch();
+
 // device copies of the set-up and the working buffers of a problem
 struct DeviceProblem {
+  Profiler *prof = nullptr;
   // element tables
   int *edeg;
   long *eoff;
@@ -157,6 +190,7 @@ struct DeviceProblem {
 }  // namespace igabem
 
 struct igabem_problem {
+  igabem::Profiler prof;
   igabem_geom *geom = nullptr;
   igabem_options opt{};
   igabem::HostSetup S;

@@ -341,40 +341,73 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
                    const double *x, double *y, cudaStream_t st) {
   Dims D = dims(S, o, R);
   const int nleaf = S.lev[S.L].n;
-  k_gather_in<<<grid_for(D.NX * R), 256, 0, st>>>(D, d.x2g, reinterpret_cast<const double2 *>(x),
-                                                   reinterpret_cast<double2 *>(d.xX));
-  k_near_spmv<<<nleaf, 128, 0, st>>>(D, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
-                                     reinterpret_cast<const double2 *>(d.xX),
-                                     reinterpret_cast<double2 *>(d.yleaf));
+  {
+    Phase ph(d.prof, IGABEM_PH_GATHER, st);
+    k_gather_in<<<grid_for(D.NX * R), 256, 0, st>>>(D, d.x2g, reinterpret_cast<const double2 *>(x),
+                                                     reinterpret_cast<double2 *>(d.xX));
+    note_launch();
+  }
+  {
+    Phase ph(d.prof, IGABEM_PH_NEAR, st);
+    k_near_spmv<<<nleaf, 128, 0, st>>>(D, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
+                                       reinterpret_cast<const double2 *>(d.xX),
+                                       reinterpret_cast<double2 *>(d.yleaf));
+    note_launch();
+  }
   if (S.n_far > 0) {
     Tables T{d.phi1, d.dphi1, d.gw, d.LG1, d.T1, d.gpn, d.gfs, d.gft};
     auto X = [&](int l) { return reinterpret_cast<double2 *>(d.xhat[l]); };
     auto Y = [&](int l) { return reinterpret_cast<double2 *>(d.yhat[l]); };
     long nleafQ = (long)nleaf * D.Q * D.CR;
-    k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
-    for (int l = S.L - 1; l >= S.lmin; --l) {
-      long n = (long)S.lev[l].n * D.Q * D.CR;
-      k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+    {
+      Phase ph(d.prof, IGABEM_PH_P2M, st);
+      k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
+      note_launch();
+    }
+    {
+      Phase ph(d.prof, IGABEM_PH_M2M, st);
+      for (int l = S.L - 1; l >= S.lmin; --l) {
+        long n = (long)S.lev[l].n * D.Q * D.CR;
+        k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+        note_launch();
+      }
     }
     int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
     int ntypes = D.hard ? 2 : 1;
     size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
     IGA_CUDA(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (int l = S.lmin; l <= S.L; ++l) {
-      dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);
-      k_m2l<<<grid, 256, smem, st>>>(D, S.lev[l].n, d.far_ptr[l], d.far_src[l], d.nodes[l], X(l), Y(l), crc);
+    {
+      Phase ph(d.prof, IGABEM_PH_M2L, st);
+      for (int l = S.lmin; l <= S.L; ++l) {
+        dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);
+        k_m2l<<<grid, 256, smem, st>>>(D, S.lev[l].n, d.far_ptr[l], d.far_src[l], d.nodes[l], X(l), Y(l), crc);
+        note_launch();
+      }
     }
-    for (int l = S.lmin; l < S.L; ++l) {
-      long n = (long)S.lev[l + 1].n * D.Q * D.CR;
-      k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+    {
+      Phase ph(d.prof, IGABEM_PH_L2L, st);
+      for (int l = S.lmin; l < S.L; ++l) {
+        long n = (long)S.lev[l + 1].n * D.Q * D.CR;
+        k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+        note_launch();
+      }
     }
-    k_l2p_eval<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, Y(S.L), reinterpret_cast<double2 *>(d.gq));
-    k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.gq),
-                                                                  reinterpret_cast<double2 *>(d.yleaf));
+    {
+      Phase ph(d.prof, IGABEM_PH_L2P, st);
+      k_l2p_eval<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, Y(S.L), reinterpret_cast<double2 *>(d.gq));
+      note_launch();
+      k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.gq),
+                                                                    reinterpret_cast<double2 *>(d.yleaf));
+      note_launch();
+    }
   }
-  k_gather_out<<<grid_for(D.N * R), 256, 0, st>>>(D, d.g2x_ptr, d.g2x_idx,
-                                                   reinterpret_cast<const double2 *>(d.yleaf),
-                                                   reinterpret_cast<double2 *>(y));
+  {
+    Phase ph(d.prof, IGABEM_PH_GATHER, st);
+    k_gather_out<<<grid_for(D.N * R), 256, 0, st>>>(D, d.g2x_ptr, d.g2x_idx,
+                                                     reinterpret_cast<const double2 *>(d.yleaf),
+                                                     reinterpret_cast<double2 *>(y));
+    note_launch();
+  }
   IGA_CUDA(cudaGetLastError());
 }
 

@@ -366,18 +366,22 @@ __global__ void k_near_singular(SingArgs S) {
 // launchers
 
 void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st) {
+  Phase ph(d.prof, IGABEM_PH_SETUP_TABLES, st);
   long tot = (long)S.E * S.ng * S.ng;
   int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
   k_gauss_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, d.gx, S.E, S.ng, (double)S.n1,
                                          d.gpx, d.gpn, d.gpa, d.gfs, d.gft);
+  note_launch();
 }
 
 void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st) {
+  Phase ph(d.prof, IGABEM_PH_SETUP_TABLES, st);
   for (int l = 0; l <= S.L; ++l) {
     long tot = (long)S.lev[l].n * S.q * S.q;
     int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, cheb, S.lev[l].n, l, S.q, S.n1,
                                           d.nodes[l], d.nodes32[l]);
+    note_launch();
   }
 }
 
@@ -397,6 +401,7 @@ static NearArgs near_args(const DeviceProblem &d, const HostSetup &S, const igab
 
 void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
                        cudaStream_t st) {
+  Phase ph(d.prof, IGABEM_PH_SETUP_NEAR, st);
   NearArgs A = near_args(d, S, o);
   int nblk = (int)S.near_src.size();
   if (nblk > 0) {
@@ -406,6 +411,7 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
     size_t smem = per * warps;
     IGA_CUDA(cudaFuncSetAttribute(k_near_regular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_near_regular<<<nblk, 32 * warps, smem, st>>>(A);
+    note_launch();
     IGA_CUDA(cudaGetLastError());
   }
   SingArgs SA;
@@ -421,6 +427,7 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   size_t smem = (size_t)SING_CHUNK * (4 + 8 * S.nloc) * sizeof(double);
   IGA_CUDA(cudaFuncSetAttribute(k_near_singular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_near_singular<<<npt, 128, smem, st>>>(SA);
+  note_launch();
   IGA_CUDA(cudaGetLastError());
 }
 

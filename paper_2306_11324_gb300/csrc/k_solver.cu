@@ -188,21 +188,26 @@ RhsArgs rhs_args(const DeviceProblem &d, const HostSetup &S, const igabem_option
 
 void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                 const double *dirs_dev, double *b, cudaStream_t st) {
+  Phase ph(d.prof, IGABEM_PH_RHS, st);
   RhsArgs A = rhs_args(d, S, o, R);
   A.dirs = dirs_dev;
   k_rhs<<<grid_for(S.N * R), 256, 0, st>>>(A, reinterpret_cast<double2 *>(b));
+  note_launch();
   IGA_CUDA(cudaGetLastError());
 }
 
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      const double *dens, int n_dir, const double *xhat_dev, double *uinf,
                      cudaStream_t st) {
+  Phase ph(d.prof, IGABEM_PH_FARFIELD, st);
   RhsArgs A = rhs_args(d, S, o, R);
   long npts = (long)S.E * S.ng * S.ng;
   double2 *rho = reinterpret_cast<double2 *>(d.gq);  // scratch of size >= E nq R
   k_density<<<grid_for(npts * R), 256, 0, st>>>(A, d.x2g, reinterpret_cast<const double2 *>(dens), S.E, rho);
+  note_launch();
   dim3 grid(n_dir, R);
   k_farfield<<<grid, 256, 0, st>>>(A, rho, npts, xhat_dev, reinterpret_cast<double2 *>(uinf));
+  note_launch();
   IGA_CUDA(cudaGetLastError());
 }
 
@@ -213,8 +218,10 @@ void launch_multidot(const double *V, int nv, const double *w, long N, int R, do
   k_multidot_partial<<<grid, threads, threads * sizeof(double2), st>>>(
       reinterpret_cast<const double2 *>(V), reinterpret_cast<const double2 *>(w), N, R,
       reinterpret_cast<double2 *>(red));
+  note_launch();
   k_multidot_final<<<(nv * R + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2 *>(red), nv,
                                                          RED_BLOCKS, R, reinterpret_cast<double2 *>(h));
+  note_launch();
   IGA_CUDA(cudaGetLastError());
 }
 
@@ -222,27 +229,32 @@ void launch_multiaxpy(const double *V, int nv, const double *h, double *w, long 
   k_multiaxpy<<<grid_for(N * R), 256, 0, st>>>(reinterpret_cast<const double2 *>(V), nv,
                                                 reinterpret_cast<const double2 *>(h),
                                                 reinterpret_cast<double2 *>(w), N, R, -1.0);
+  note_launch();
 }
 
 void launch_update(const double *V, int nv, const double *y, double *x, long N, int R, cudaStream_t st) {
   k_multiaxpy<<<grid_for(N * R), 256, 0, st>>>(reinterpret_cast<const double2 *>(V), nv,
                                                 reinterpret_cast<const double2 *>(y),
                                                 reinterpret_cast<double2 *>(x), N, R, 1.0);
+  note_launch();
 }
 
 void launch_norms(const double *w, long N, int R, double *red, double *nrm, cudaStream_t st) {
   double *h = red + (size_t)2 * RED_BLOCKS * R * 2;  // past the partial sums of one vector
   launch_multidot(w, 1, w, N, R, red, h, st);
   k_sqrt_re<<<(R + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2 *>(h), nrm, R);
+  note_launch();
 }
 
 void launch_scale(const double *w, const double *s, double *dst, long N, int R, cudaStream_t st) {
   k_scale<<<grid_for(N * R), 256, 0, st>>>(reinterpret_cast<const double2 *>(w), s,
                                             reinterpret_cast<double2 *>(dst), N, R);
+  note_launch();
 }
 
 void launch_sub(const double *b, const double *y, double *r, long n, cudaStream_t st) {
   k_sub<<<grid_for(n), 256, 0, st>>>(b, y, r, n);
+  note_launch();
 }
 
 }  // namespace igabem

@@ -181,6 +181,23 @@ int igabem_solve(igabem_problem *prob, int n_rhs, const double *dirs, void *dens
 int igabem_farfield(igabem_problem *prob, int n_rhs, const void *density, int n_dir,
                     const double *xhat, void *uinf);
 
+/* Far-field pattern without any device memory allocation.  The paper has no counterpart: this is a
+   property of the library for callers that cannot allocate device memory -- a host program whose
+   own caching allocator has reserved the device (a library cudaMalloc would fail or fragment its
+   pool), or a serving loop that must not stall on the implicit device synchronisation of
+   cudaMalloc/cudaFree.  Same result as igabem_farfield, but density ([N][n_rhs] complex), xhat
+   ([n_dir][3] doubles) and uinf ([n_dir][n_rhs] complex) must all be device memory of the context's
+   device (host pointers are refused with IGABEM_EINVAL).  The problem must already exist (creating it
+   allocates).  Scratch: a fixed 32 MiB device array inside the library (2^21 complex values, one per
+   element x Gauss point x right-hand side), held by every device that loads the library until the
+   process exits; calls with n_elements * gauss_regular^2 * n_rhs > 2^21 are refused with
+   IGABEM_EINVAL.  The first call on a device looks up the array's device address; make that first
+   call before any stream capture on the device.  All calls share the array: calls whose GPU work
+   overlaps (other host threads, other contexts or streams on the same device) race and give wrong
+   results. */
+int igabem_farfield_noalloc(igabem_problem *prob, int n_rhs, const void *density, int n_dir,
+                            const double *xhat, void *uinf);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ SIGNATURES = {
     "igabem_farfield": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_profile_enable": (c_int, [c_void_p, c_int]),
     "igabem_profile_get": (c_int, [c_void_p, ctypes.POINTER(igabem_profile), c_int]),
+    "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
 }
 
 
@@ -219,6 +220,14 @@ def igabem_farfield(prob, density, xhat, out=None):
     out = _like(density, (xh.shape[0], R)) if out is None else out
     _check(lib().igabem_farfield(prob, R, _ptr(density), xh.shape[0], _ptr(xh), _ptr(out)))
     return out
+
+
+def igabem_farfield_noalloc(prob, density, xhat, uinf):
+    """Far field with no device allocation: density [N][R], xhat [n_dir][3] (float64) and uinf
+    [n_dir][R] must be CUDA tensors of the context's device (see include/igabem.h)."""
+    R = _ncols(density)
+    _check(lib().igabem_farfield_noalloc(prob, R, _ptr(density), int(xhat.shape[0]), _ptr(xhat), _ptr(uinf)))
+    return uinf
 
 
 def igabem_profile_enable(prob, on: bool = True):

@@ -359,6 +359,8 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
         total += bytes_of(S.lev[l].far_ptr) + bytes_of(S.lev[l].far_src);
         total += ((size_t)7 * S.lev[l].n * Q * sizeof(double) + 255) & ~size_t(255);
         total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
+        total += bytes_of(S.lev[l].center);
+        total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
       }
       size_t blk_bytes = S.near_src.size() * (size_t)S.nL * S.nL * 2 * sizeof(double);
       total += (blk_bytes + 255) & ~size_t(255);
@@ -399,16 +401,24 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
       d.far_src.assign(S.L + 1, nullptr);
       d.nodes.assign(S.L + 1, nullptr);
       d.nodes32.assign(S.L + 1, nullptr);
+      d.centers.assign(S.L + 1, nullptr);
+      d.pairc.assign(S.L + 1, nullptr);
       for (int l = 0; l <= S.L; ++l) {
         d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
         d.far_src[l] = upload(A, S.lev[l].far_src, st);
         d.nodes[l] = A.get<double>((size_t)7 * S.lev[l].n * Q);
         d.nodes32[l] = A.get<float>((size_t)7 * S.lev[l].n * Q);
+        d.centers[l] = upload(A, S.lev[l].center, st);
+        d.pairc[l] = A.get<float>(std::max<size_t>(S.lev[l].far_src.size(), 1) * 8);
       }
       d.blk = A.get<double>(S.near_src.size() * (size_t)S.nL * S.nL * 2);
       IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
       launch_gauss_geometry(d, S, st);
       launch_node_geometry(d, S, cheb, st);
+      if (S.n_far > 0) {
+        Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
+        launch_pair_consts(d, S, opt->kappa, st);
+      }
       launch_near_field(d, S, *opt, st);
       IGA_CUDA(cudaStreamSynchronize(st));
       IGA_CUDA(cudaGetLastError());

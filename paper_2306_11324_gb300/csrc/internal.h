@@ -173,7 +173,9 @@ struct DeviceProblem {
   int *near_ptr, *near_src, *near_tgt;
   std::vector<int *> far_ptr, far_src;       // per level
   std::vector<double *> nodes;               // per level: [7][n*q*q] (x, n~, a) node geometry
-  std::vector<float *> nodes32;
+  std::vector<float *> nodes32;              // per level: [7][n*q*q] (x - centre, n~, a) in FP32
+  std::vector<double *> centers;             // per level: [n][3] cluster centres
+  std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
   double *T1, *LG1;
   // near-field blocks (column-major nL x nL per near pair)
   double *blk;                               // complex FP64: 2 doubles per entry

@@ -372,11 +372,14 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         note_launch();
       }
     }
-    int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
-    int ntypes = D.hard ? 2 : 1;
-    size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
-    IGA_CUDA(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
+    if (m2l_rows_supported(S)) {
+      Phase ph(d.prof, IGABEM_PH_M2L, st);
+      launch_m2l_rows(d, S, o, R, o.precision == IGABEM_MIXED_FP32, st);
+    } else {
+      int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
+      int ntypes = D.hard ? 2 : 1;
+      size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
+      IGA_CUDA(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       for (int l = S.lmin; l <= S.L; ++l) {
         dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);

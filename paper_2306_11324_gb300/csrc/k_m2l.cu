@@ -1,0 +1,316 @@
+// M2L: couplings of admissible cluster pairs (Sec. 4.4) with the kernel samples between the
+// Chebyshev nodes generated on the fly, FP64 and FP32.
+//
+// Layout: one thread block per target cluster (all levels in one launch), its warps share the
+// target's interaction list; lane l owns target nodes l and l + 32 (q*q <= 64) and generates their
+// rows of the coupling block in registers while streaming the source nodes of one pair from shared
+// memory (broadcast reads).  Accumulation is blocked: q source nodes per partial sum, q partial sums
+// per pair, then the pairs; the warps are reduced through shared memory at the end.
+//
+// FP32 phase split: the sample phase kappa r is formed as kappa |D| (D = c_t - c_s, the distance of
+// the two cluster centres, taken in FP64 once per pair and reduced mod 2 pi) plus kappa (r - |D|),
+// with r - |D| = (2 D.delta + |delta|^2)/(r + |D|) computed in FP32 from the node offsets
+// delta = (x_a - c_t) - (y_b - c_s).  The FP32 error of the phase is then of the order of the
+// cluster size times the unit roundoff instead of kappa r times it, and the factor
+// exp(i kappa |D|) multiplies the pair's partial sums once.
+#include <algorithm>
+#include <type_traits>
+
+#include "internal.h"
+#include "k_common.cuh"
+#include "kernels.h"
+
+namespace igabem {
+
+namespace {
+
+constexpr int M2L_WARPS = 8;
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+template <class T> struct C2 {
+  T x, y;
+};
+template <class T> __device__ inline C2<T> c2(T a, T b) { return {a, b}; }
+template <class T> __device__ inline C2<T> add(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __device__ inline C2<T> mul(C2<T> a, C2<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __device__ inline C2<T> fma2(C2<T> a, C2<T> b, C2<T> acc) {  // acc + a b
+  return {acc.x + a.x * b.x - a.y * b.y, acc.y + a.x * b.y + a.y * b.x};
+}
+
+struct M2LLevel {
+  const int *far_ptr, *far_src;
+  const double *nodes;   // FP64 [7][n q^2]: x, n~, a
+  const float *nodes32;  // FP32 [7][n q^2]: x - c, n~, a
+  const float *pc;       // FP32 pair constants [n_far][8]: D, |D|, |D|^2, cos, sin of kappa|D| (FP32 path)
+  const double2 *xhat;
+  double2 *yhat;
+  int n;                 // clusters on the level
+  int first;             // first block index of the level in the flattened grid
+};
+
+struct M2LArgs {
+  M2LLevel lev[16];
+  int nlev;
+  int q, Q, CR, R;
+  double kappa, eta;
+  bool hard;
+};
+
+// per-source-node data in shared memory
+template <class T> struct SrcNode {
+  T dy[3], ny[3], ay, Ddy, Dny, pad;
+};
+
+// Kernel sample(s) between target node (x, n~x, ax) and source node (y, n~y, ay).
+//   soft: ks = a_y G'(r)/r (x-y).n~x - i eta a_x a_y G                       (K' - i eta V)
+//   hard: kk = a_x G'(r)/r (y-x).n~y (K),  g = G (the six W channels)
+// e = (cos, sin) of the phase carried by the sample; for FP32 the pair factor exp(i kappa |D|) is
+// applied by the caller.
+template <class T, int NCR, bool HARD>
+__global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_rows(M2LArgs A, int cr0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // locate the level of this block
+  int li = 0;
+  while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
+  const M2LLevel &L = A.lev[li];
+  const int t = blockIdx.x - L.first;
+  const int Q = A.Q;
+  const long NQ = (long)L.n * Q;
+  const int ncr = min(NCR, A.CR - cr0);
+  // shared memory: per warp Q source nodes + Q x NCR source coefficients; then the reduction area
+  SrcNode<T> *src = reinterpret_cast<SrcNode<T> *>(smraw) + warp * 64;
+  C2<T> *xs = reinterpret_cast<C2<T> *>(reinterpret_cast<SrcNode<T> *>(smraw) + M2L_WARPS * 64) + warp * 64 * NCR;
+  double2 *red = reinterpret_cast<double2 *>(smraw);
+  const T kappa = (T)A.kappa, eta = (T)A.eta;
+  // target rows of this lane
+  T tx[2][3], tn[2][3], ta[2];
+  bool valid[2];
+  for (int k = 0; k < 2; ++k) {
+    int a = lane + 32 * k;
+    valid[k] = a < Q;
+    long ia = (long)t * Q + (valid[k] ? a : 0);
+    for (int c = 0; c < 3; ++c) {
+      tx[k][c] = F32 ? (T)L.nodes32[c * NQ + ia] : (T)L.nodes[c * NQ + ia];
+      tn[k][c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ia] : (T)L.nodes[(3 + c) * NQ + ia];
+    }
+    ta[k] = F32 ? (T)L.nodes32[6 * NQ + ia] : (T)L.nodes[6 * NQ + ia];
+  }
+  C2<T> tot[2][NCR];
+  for (int k = 0; k < 2; ++k)
+    for (int c = 0; c < NCR; ++c) tot[k][c] = c2((T)0, (T)0);
+  const T inv4pi = (T)(0.25 / IGA_PI);
+  for (int kk = L.far_ptr[t] + warp; kk < L.far_ptr[t + 1]; kk += M2L_WARPS) {
+    const int s = L.far_src[kk];
+    // pair constants (FP32 path): D = c_t - c_s, |D|, |D|^2 and exp(i kappa |D|), from the set-up
+    T D[3] = {0, 0, 0}, Dn = 0, D2 = 0;
+    C2<T> e0 = c2((T)1, (T)0);
+    if constexpr (F32) {
+      const float4 p0 = reinterpret_cast<const float4 *>(L.pc)[2 * kk];
+      const float4 p1 = reinterpret_cast<const float4 *>(L.pc)[2 * kk + 1];
+      D[0] = p0.x; D[1] = p0.y; D[2] = p0.z; Dn = p0.w;
+      D2 = p1.x;
+      e0 = c2(p1.y, p1.z);
+    }
+    // stage the source nodes and coefficients of this pair
+    __syncwarp();
+    for (int b = lane; b < Q; b += 32) {
+      long ib = (long)s * Q + b;
+      SrcNode<T> sn;
+      for (int c = 0; c < 3; ++c) {
+        sn.dy[c] = F32 ? (T)L.nodes32[c * NQ + ib] : (T)L.nodes[c * NQ + ib];
+        sn.ny[c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ib] : (T)L.nodes[(3 + c) * NQ + ib];
+      }
+      sn.ay = F32 ? (T)L.nodes32[6 * NQ + ib] : (T)L.nodes[6 * NQ + ib];
+      sn.Ddy = D[0] * sn.dy[0] + D[1] * sn.dy[1] + D[2] * sn.dy[2];
+      sn.Dny = D[0] * sn.ny[0] + D[1] * sn.ny[1] + D[2] * sn.ny[2];
+      src[b] = sn;
+      for (int c = 0; c < ncr; ++c) {
+        double2 v = L.xhat[ib * A.CR + cr0 + c];
+        xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+      }
+    }
+    __syncwarp();
+    for (int k = 0; k < 2; ++k) {
+      if (!valid[k]) continue;
+      const T Ddx = D[0] * tx[k][0] + D[1] * tx[k][1] + D[2] * tx[k][2];
+      const T Dnx = D[0] * tn[k][0] + D[1] * tn[k][1] + D[2] * tn[k][2];
+      C2<T> acc[NCR];
+      for (int c = 0; c < NCR; ++c) acc[c] = c2((T)0, (T)0);
+      for (int b1 = 0; b1 < A.q; ++b1) {
+        C2<T> part[NCR];
+        for (int c = 0; c < NCR; ++c) part[c] = c2((T)0, (T)0);
+        for (int b2 = 0; b2 < A.q; ++b2) {
+          const int b = b1 * A.q + b2;
+          const SrcNode<T> &y = src[b];
+          T d0 = tx[k][0] - y.dy[0], d1 = tx[k][1] - y.dy[1], d2 = tx[k][2] - y.dy[2];
+          T r2, ir, r, cph, sph;
+          T dn_x, dn_y;  // (x-y).n~x and (x-y).n~y
+          if constexpr (F32) {
+            // delta = d; x - y = D + delta
+            T Dd = Ddx - y.Ddy;
+            T dd = d0 * d0 + d1 * d1 + d2 * d2;
+            T num = (T)2 * Dd + dd;
+            r2 = D2 + num;
+            ir = rsqrtf((float)r2);
+            r = r2 * ir;
+            T del = __fdividef((float)num, (float)(r + Dn));
+            T ph = kappa * del;
+            T kq = rintf((float)(ph * (T)0.15915494309189535));
+            ph = fmaf(-(float)kq, 6.28318548202514648f, (float)ph);
+            ph = fmaf(-(float)kq, -1.7484556e-07f, (float)ph);
+            float sf, cf;
+            __sincosf((float)ph, &sf, &cf);
+            cph = cf;
+            sph = sf;
+            dn_x = Dnx + d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
+            dn_y = y.Dny + d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
+          } else {
+            r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            ir = rsqrt((double)r2);
+            r = r2 * ir;
+            double sd, cd;
+            sincos(A.kappa * (double)r, &sd, &cd);
+            cph = cd;
+            sph = sd;
+            dn_x = d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
+            dn_y = d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
+          }
+          const T f = ir * inv4pi;
+          const T kr = kappa * r;
+          const T g2 = f * ir * ir;
+          // G = e f;  G'(r)/r = e (-1 + i kappa r) f / r^2
+          const C2<T> G = c2(cph * f, sph * f);
+          const C2<T> dG = c2((-cph - sph * kr) * g2, (-sph + cph * kr) * g2);
+          if (!HARD) {
+            const T w1 = y.ay * dn_x, w2 = ta[k] * y.ay * eta;
+            // ks = dG w1 - i eta a_x a_y G
+            const C2<T> ks = c2(dG.x * w1 + G.y * w2, dG.y * w1 - G.x * w2);
+            for (int c = 0; c < NCR; ++c) part[c] = fma2(ks, xs[b * NCR + c], part[c]);
+          } else {
+            const T w1 = -ta[k] * dn_y;  // a_x (y-x).n~y
+            const C2<T> kk2 = c2(dG.x * w1, dG.y * w1);
+            for (int c = 0; c < NCR; ++c) {
+              const int ch = (cr0 + c) / A.R;
+              part[c] = fma2(ch == 0 ? kk2 : G, xs[b * NCR + c], part[c]);
+            }
+          }
+        }
+        for (int c = 0; c < NCR; ++c) acc[c] = add(acc[c], part[c]);
+      }
+      for (int c = 0; c < NCR; ++c) tot[k][c] = fma2(e0, acc[c], tot[k][c]);
+    }
+  }
+  // reduce over the warps (the staging area is reused)
+  __syncthreads();
+  for (int k = 0; k < 2; ++k)
+    for (int c = 0; c < NCR; ++c) {
+      int a = lane + 32 * k;
+      red[(warp * 64 + a) * NCR + c] = make_double2((double)tot[k][c].x, (double)tot[k][c].y);
+    }
+  __syncthreads();
+  for (int o = threadIdx.x; o < Q * ncr; o += blockDim.x) {
+    int a = o / ncr, c = o % ncr;
+    double2 s = make_double2(0, 0);
+    for (int w = 0; w < M2L_WARPS; ++w) {
+      double2 v = red[(w * 64 + a) * NCR + c];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    L.yhat[((long)t * Q + a) * A.CR + cr0 + c] = s;
+  }
+}
+
+// pair constants of the FP32 path, per admissible pair k of a level (CSR order):
+// [D (3), |D|, |D|^2, cos(kappa |D|), sin(kappa |D|), 0] with D = c_t - c_s in FP64
+__global__ void k_pair_consts(const int *__restrict__ far_ptr, const int *__restrict__ far_src,
+                              const double *__restrict__ center, int n, double kappa, float *__restrict__ pc) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int k = far_ptr[t]; k < far_ptr[t + 1]; ++k) {
+    int s = far_src[k];
+    double D[3] = {center[3 * t] - center[3 * s], center[3 * t + 1] - center[3 * s + 1],
+                   center[3 * t + 2] - center[3 * s + 2]};
+    double nD = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    double sn, cs;
+    sincos(fmod(kappa * nD, TWO_PI), &sn, &cs);
+    float *o = pc + 8L * k;
+    o[0] = (float)D[0]; o[1] = (float)D[1]; o[2] = (float)D[2]; o[3] = (float)nD;
+    o[4] = (float)(nD * nD); o[5] = (float)cs; o[6] = (float)sn; o[7] = 0.f;
+  }
+}
+
+template <class T, int NCR, bool HARD>
+void launch_rows(const M2LArgs &A, int nblocks, cudaStream_t st) {
+  size_t smem = std::max((size_t)M2L_WARPS * 64 * sizeof(SrcNode<T>) + (size_t)M2L_WARPS * 64 * NCR * sizeof(C2<T>),
+                         (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
+  auto kfn = k_m2l_rows<T, NCR, HARD>;
+  IGA_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int cr0 = 0; cr0 < A.CR; cr0 += NCR) {
+    kfn<<<nblocks, 32 * M2L_WARPS, smem, st>>>(A, cr0);
+    note_launch();
+  }
+}
+
+template <class T>
+void launch_typed(const M2LArgs &A, int nblocks, cudaStream_t st) {
+  if (A.hard) {
+    launch_rows<T, 7, true>(A, nblocks, st);
+  } else if (A.CR == 1) {
+    launch_rows<T, 1, false>(A, nblocks, st);
+  } else if (A.CR == 2) {
+    launch_rows<T, 2, false>(A, nblocks, st);
+  } else {
+    launch_rows<T, 4, false>(A, nblocks, st);
+  }
+}
+
+}  // namespace
+
+void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, cudaStream_t st) {
+  for (int l = S.lmin; l <= S.L; ++l) {
+    int n = S.lev[l].n;
+    k_pair_consts<<<(n + 127) / 128, 128, 0, st>>>(d.far_ptr[l], d.far_src[l], d.centers[l], n, kappa, d.pairc[l]);
+    note_launch();
+  }
+  IGA_CUDA(cudaGetLastError());
+}
+
+bool m2l_rows_supported(const HostSetup &S) { return S.q * S.q <= 64 && S.L - S.lmin + 1 <= 16; }
+
+void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                     bool fp32, cudaStream_t st) {
+  M2LArgs A;
+  A.q = S.q;
+  A.Q = S.q * S.q;
+  A.R = R;
+  A.CR = (S.hard ? 7 : 1) * R;
+  A.kappa = o.kappa;
+  A.eta = o.eta_cfie;
+  A.hard = S.hard;
+  A.nlev = 0;
+  int nblocks = 0;
+  for (int l = S.lmin; l <= S.L; ++l) {
+    M2LLevel &L = A.lev[A.nlev++];
+    L.far_ptr = d.far_ptr[l];
+    L.far_src = d.far_src[l];
+    L.nodes = d.nodes[l];
+    L.nodes32 = d.nodes32[l];
+    L.pc = d.pairc[l];
+    L.xhat = reinterpret_cast<const double2 *>(d.xhat[l]);
+    L.yhat = reinterpret_cast<double2 *>(d.yhat[l]);
+    L.n = S.lev[l].n;
+    L.first = nblocks;
+    nblocks += S.lev[l].n;
+  }
+  if (fp32)
+    launch_typed<float>(A, nblocks, st);
+  else
+    launch_typed<double>(A, nblocks, st);
+  IGA_CUDA(cudaGetLastError());
+}
+
+}  // namespace igabem

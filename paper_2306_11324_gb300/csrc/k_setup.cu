@@ -36,7 +36,8 @@ __global__ void k_gauss_geometry(const int *__restrict__ edeg, const long *__res
 // geometry at the Chebyshev nodes of every cluster of level l: [7][n_clusters*q*q] = x, n~, a
 __global__ void k_node_geometry(const int *__restrict__ edeg, const long *__restrict__ eoff,
                                 const double *__restrict__ ebez, const double *__restrict__ cheb,
-                                int n_clusters, int l, int q, int n1, double *out, float *out32) {
+                                const double *__restrict__ center, int n_clusters, int l, int q, int n1,
+                                double *out, float *out32) {
   long tot = (long)n_clusters * q * q;
   int nl = 1 << l;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
@@ -55,7 +56,8 @@ __global__ void k_node_geometry(const int *__restrict__ edeg, const long *__rest
     double v[7] = {F[0], F[1], F[2], n[0], n[1], n[2], sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2])};
     for (int k = 0; k < 7; ++k) {
       out[k * tot + i] = v[k];
-      out32[k * tot + i] = (float)v[k];
+      // FP32 copy: positions relative to the cluster centre
+      out32[k * tot + i] = (float)(k < 3 ? v[k] - center[3 * t + k] : v[k]);
     }
   }
 }
@@ -379,8 +381,8 @@ void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *ch
   for (int l = 0; l <= S.L; ++l) {
     long tot = (long)S.lev[l].n * S.q * S.q;
     int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
-    k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, cheb, S.lev[l].n, l, S.q, S.n1,
-                                          d.nodes[l], d.nodes32[l]);
+    k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, cheb, d.centers[l], S.lev[l].n, l, S.q,
+                                          S.n1, d.nodes[l], d.nodes32[l]);
     note_launch();
   }
 }

@@ -80,3 +80,37 @@ def test_solve_sound_soft_sphere():
     u = B.igabem_farfield(prob, x, xh)[:, 0]
     assert G.rel(u, mie.mie_far_field(1.0, xh)) < 2e-4
     B.igabem_problem_destroy(prob)
+
+
+MIXED_MATVEC_TOL = 2e-6   # FP32 far field (phase-split kernel samples, FP32 accumulation)
+
+
+@pytest.mark.parametrize("hard,kappa", [(False, 1.0), (False, 6.0), (True, 3.0)])
+def test_mixed_fmm_matvec_matches_interpolated_kernel_matrix(hard, kappa):
+    """FP32 M2L (mixed precision) against the FP64 mode-B matrix of the oracle."""
+    m, p, leaf, q = 2, 1, 2, 5
+    prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
+                           leaf_offset=m - leaf, eta_adm=0.5, precision=B.MIXED_FP32)
+    sp = C.sphere_space(m, p, hard)
+    Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
+    x = inputs.random_complex(sp.N, seed=1234)
+    y = B.igabem_matvec(prob, x)
+    assert G.rel(y, Amat @ x) < MIXED_MATVEC_TOL
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_mixed_solve_far_field_matches_fp64(hard):
+    """The mixed-precision solve reproduces the FP64 far field to 1e-5 (spec bar)."""
+    kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=int(hard), cheb_q=7, leaf_offset=1,
+              eta_adm=0.5, tol=1e-8)
+    xh = inputs.fibonacci_directions(100)
+    d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])
+    u = {}
+    for prec in (B.FP64, B.MIXED_FP32):
+        prob, info = G.problem("deformed" if hard else "sphere", precision=prec, **kw)
+        x, sinfo = B.igabem_solve(prob, d, info["n_dofs"])
+        assert sinfo["rel_residual"] <= 1e-8
+        u[prec] = B.igabem_farfield(prob, x, xh)
+        B.igabem_problem_destroy(prob)
+    assert G.rel(u[B.MIXED_FP32], u[B.FP64]) < 1e-5

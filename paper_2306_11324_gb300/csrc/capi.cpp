@@ -362,8 +362,11 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
         total += bytes_of(S.lev[l].center);
         total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
       }
-      size_t blk_bytes = S.near_src.size() * (size_t)S.nL * S.nL * 2 * sizeof(double);
-      total += (blk_bytes + 255) & ~size_t(255);
+      const bool mixed = opt->precision == IGABEM_MIXED_FP32;
+      size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
+      size_t blk_bytes = blk_entries * sizeof(double);
+      // mixed precision keeps the near-field blocks in FP32; the FP64 assembly buffer is temporary
+      total += mixed ? ((blk_entries * sizeof(float) + 255) & ~size_t(255)) : ((blk_bytes + 255) & ~size_t(255));
       P->arena.reserve(total);
       Arena &A = P->arena;
       DeviceProblem &d = P->d;
@@ -411,7 +414,14 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
         d.centers[l] = upload(A, S.lev[l].center, st);
         d.pairc[l] = A.get<float>(std::max<size_t>(S.lev[l].far_src.size(), 1) * 8);
       }
-      d.blk = A.get<double>(S.near_src.size() * (size_t)S.nL * S.nL * 2);
+      double *blk_tmp = nullptr;
+      if (mixed) {
+        d.blk32 = A.get<float>(blk_entries);
+        IGA_CUDA(cudaMalloc(&blk_tmp, std::max<size_t>(blk_bytes, 256)));
+        d.blk = blk_tmp;
+      } else {
+        d.blk = A.get<double>(blk_entries);
+      }
       IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
       launch_gauss_geometry(d, S, st);
       launch_node_geometry(d, S, cheb, st);
@@ -420,6 +430,15 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
         launch_pair_consts(d, S, opt->kappa, st);
       }
       launch_near_field(d, S, *opt, st);
+      if (mixed) {
+        {
+          Phase ph(&P->prof, IGABEM_PH_SETUP_NEAR, st);
+          launch_blocks_to_fp32(d.blk, d.blk32, blk_entries, st);
+        }
+        IGA_CUDA(cudaStreamSynchronize(st));
+        IGA_CUDA(cudaFree(blk_tmp));
+        d.blk = nullptr;
+      }
       IGA_CUDA(cudaStreamSynchronize(st));
       IGA_CUDA(cudaGetLastError());
       P->prof.flush();

@@ -178,7 +178,8 @@ struct DeviceProblem {
   std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
   double *T1, *LG1;
   // near-field blocks (column-major nL x nL per near pair)
-  double *blk;                               // complex FP64: 2 doubles per entry
+  double *blk = nullptr;                     // complex FP64: 2 doubles per entry (FP64 precision)
+  float *blk32 = nullptr;                    // complex FP32 copy used by the mixed precision SpMV
   // work buffers, sized for max_rhs columns
   int max_rhs = 0;
   double *xX = nullptr;                      // X-space input [NX][R] complex

@@ -50,28 +50,6 @@ __device__ inline long xindex(const Dims &D, int j, int i1, int i2) {
   return ((long)j * D.nb + i1) * D.nb + i2;
 }
 
-// y_leaf[t][i][r] = sum over near blocks (t, s) of B[j][i] x_s[j][r]  (B includes 1/2 M)
-__global__ void k_near_spmv(Dims D, const int *__restrict__ near_ptr, const int *__restrict__ near_src,
-                            const double2 *__restrict__ blk, const double2 *__restrict__ xX,
-                            double2 *__restrict__ yleaf) {
-  const int t = blockIdx.x;
-  const int nlL = 1 << D.L, e1 = 1 << D.b;
-  for (int o = threadIdx.x; o < D.nL * D.R; o += blockDim.x) {
-    int i = o / D.R, r = o % D.R;
-    double2 acc = cmk(0, 0);
-    for (int k = near_ptr[t]; k < near_ptr[t + 1]; ++k) {
-      int s = near_src[k];
-      int js = s / (nlL * nlL), cx = (s / nlL) % nlL, cy = s % nlL;
-      const double2 *B = blk + (size_t)k * D.nL * D.nL;
-      for (int jj = 0; jj < D.nL; ++jj) {
-        long X = xindex(D, js, cx * e1 + jj / D.nL1, cy * e1 + jj % D.nL1);
-        acc = cadd(acc, cmul(B[(size_t)jj * D.nL + i], xX[X * D.R + r]));
-      }
-    }
-    yleaf[((size_t)t * D.nL + i) * D.R + r] = acc;
-  }
-}
-
 struct Tables {
   const double *phi1, *dphi1, *gw, *LG1, *T1;
   const double *gpn, *gfs, *gft;  // Gauss-point geometry (SoA, stride E*nq)
@@ -347,12 +325,10 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
                                                      reinterpret_cast<double2 *>(d.xX));
     note_launch();
   }
+  const bool leafk = leaf_kernels_supported(S);
   {
     Phase ph(d.prof, IGABEM_PH_NEAR, st);
-    k_near_spmv<<<nleaf, 128, 0, st>>>(D, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
-                                       reinterpret_cast<const double2 *>(d.xX),
-                                       reinterpret_cast<double2 *>(d.yleaf));
-    note_launch();
+    launch_near_spmv(d, S, o, R, st);
   }
   if (S.n_far > 0) {
     Tables T{d.phi1, d.dphi1, d.gw, d.LG1, d.T1, d.gpn, d.gfs, d.gft};
@@ -361,8 +337,12 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     long nleafQ = (long)nleaf * D.Q * D.CR;
     {
       Phase ph(d.prof, IGABEM_PH_P2M, st);
-      k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
-      note_launch();
+      if (leafk) {
+        launch_p2m(d, S, o, R, st);
+      } else {
+        k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
+        note_launch();
+      }
     }
     {
       Phase ph(d.prof, IGABEM_PH_M2M, st);
@@ -397,11 +377,15 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     }
     {
       Phase ph(d.prof, IGABEM_PH_L2P, st);
-      k_l2p_eval<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, Y(S.L), reinterpret_cast<double2 *>(d.gq));
-      note_launch();
-      k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.gq),
-                                                                    reinterpret_cast<double2 *>(d.yleaf));
-      note_launch();
+      if (leafk) {
+        launch_l2p(d, S, o, R, st);
+      } else {
+        k_l2p_eval<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, Y(S.L), reinterpret_cast<double2 *>(d.gq));
+        note_launch();
+        k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.gq),
+                                                                      reinterpret_cast<double2 *>(d.yleaf));
+        note_launch();
+      }
     }
   }
   {

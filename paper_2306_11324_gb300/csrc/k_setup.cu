@@ -90,10 +90,48 @@ __device__ inline PairKernel cfie_kernel(bool hard, double kappa, double eta, co
     double2 kk = cscale(kv.dGr, ax * dn);
     double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
     double2 g = kv.G;
-    // -kk + i eta kappa^2 nn G
     double f = eta * kappa * kappa * nn;
     pk.ks = cmk(-kk.x - f * g.y, -kk.y + f * g.x);
     pk.gc = cmk(eta * g.y, -eta * g.x);  // -i eta G
+  }
+  return pk;
+}
+
+template <class T> struct PK {
+  T ksx, ksy, gcx, gcy;
+};
+
+// the same kernel in precision T (FP32 for the regular pairs of the mixed precision set-up)
+template <class T>
+__device__ inline PK<T> cfie_kernel_t(bool hard, T kappa, T eta, const T *x, const T *nx, T ax, const T *y,
+                                      const T *ny, T ay) {
+  T d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  T r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  T ir, sn, cs;
+  if constexpr (sizeof(T) == 4) {
+    ir = rsqrtf(r2);
+    sincosf(kappa * r2 * ir, &sn, &cs);
+  } else {
+    ir = rsqrt(r2);
+    sincos(kappa * r2 * ir, &sn, &cs);
+  }
+  const T r = r2 * ir, f = ir * (T)(0.25 / IGA_PI), kr = kappa * r, g2 = f * ir * ir;
+  const T Gx = cs * f, Gy = sn * f;
+  const T dGx = (-cs - sn * kr) * g2, dGy = (-sn + cs * kr) * g2;
+  PK<T> pk;
+  if (!hard) {
+    T w1 = ay * (d0 * nx[0] + d1 * nx[1] + d2 * nx[2]), w2 = ax * ay * eta;
+    pk.ksx = dGx * w1 + Gy * w2;
+    pk.ksy = dGy * w1 - Gx * w2;
+    pk.gcx = 0;
+    pk.gcy = 0;
+  } else {
+    T w1 = -ax * (d0 * ny[0] + d1 * ny[1] + d2 * ny[2]);
+    T f2 = eta * kappa * kappa * (nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2]);
+    pk.ksx = -dGx * w1 - f2 * Gy;
+    pk.ksy = -dGy * w1 + f2 * Gx;
+    pk.gcx = eta * Gy;
+    pk.gcy = -eta * Gx;
   }
   return pk;
 }
@@ -154,21 +192,36 @@ __device__ inline bool touching(const NearArgs &A, int e, int f) {
 
 // One block of threads per near leaf pair, one warp per element pair (touching pairs skipped:
 // k_near_singular integrates them).  Block entry (k of e, l of f) +=
-//   sum_{q,r} w_q w_r h^4 [ks(q,r) psi_k(q) psi_l(r) + gc(q,r) c_k(q) . c_l(r)].
-__global__ void k_near_regular(NearArgs A) {
-  extern __shared__ double2 sm[];
+//   sum_{q,r} w_q w_r h^4 [ks(q,r) psi_k(q) psi_l(r) + gc(q,r) c_k(q) . c_l(r)],
+// evaluated in precision T (FP64, or FP32 for the mixed precision set-up), the leaf-pair block summed
+// in FP64 in shared memory when it fits (else with global FP64 atomics).
+template <class T>
+__global__ void k_near_regular_t(NearArgs A, int smem_block) {
+  extern __shared__ __align__(16) unsigned char smr[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int nq = A.ng * A.ng, nloc = A.nloc, p1 = A.p + 1;
-  const int per = 2 * nq * nq + 4 * nq * nloc;
-  double2 *ks = sm + warp * per, *gc = ks + nq * nq, *T = gc + nq * nq, *Tc = T + nq * nloc;
+  // per-warp scratch (T): pts[2][nq][7], phi[2][nq][nloc], curl[2][nq][nloc][3], ks/gc[nq*nq][2 each],
+  // Tm[nq][nloc][2], Tc[3][nq][nloc][2]
+  const int per = 2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc + 6 * nq * nloc;
+  double2 *Bs = reinterpret_cast<double2 *>(smr);
+  T *base = reinterpret_cast<T *>(smr + (smem_block ? (size_t)A.nL * A.nL * sizeof(double2) : 0));
+  T *pts = base + warp * per;
+  T *phe = pts + 2 * nq * 7, *phf = phe + nq * nloc;
+  T *cue = phf + nq * nloc, *cuf = cue + 3 * nq * nloc;
+  T *ks = cuf + 3 * nq * nloc, *gc = ks + 2 * nq * nq;
+  T *Tm = gc + 2 * nq * nq, *Tc = Tm + 2 * nq * nloc;
   const int bid = blockIdx.x;
   const int tgt = A.near_tgt[bid], src = A.near_src[bid];
   const int nlL = 1 << A.L, ne1 = 1 << A.b;
   const int jt = tgt / (nlL * nlL), cxt = (tgt / nlL) % nlL, cyt = tgt % nlL;
   const int js = src / (nlL * nlL), cxs = (src / nlL) % nlL, cys = src % nlL;
-  double2 *B = A.blk + (size_t)bid * A.nL * A.nL;
+  double2 *Bg = A.blk + (size_t)bid * A.nL * A.nL;
+  if (smem_block) {
+    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) Bs[i] = make_double2(0, 0);
+    __syncthreads();
+  }
   const long st = A.gstride;
-  const double h4 = A.h * A.h * A.h * A.h;
+  const T h2 = (T)(A.h * A.h), kap = (T)A.kappa, eta = (T)A.eta;
   const int npair = ne1 * ne1 * ne1 * ne1;
   for (int pr = warp; pr < npair; pr += nwarp) {
     int et = pr / (ne1 * ne1), es = pr % (ne1 * ne1);
@@ -176,60 +229,100 @@ __global__ void k_near_regular(NearArgs A) {
     int ixf = cxs * ne1 + es / ne1, iyf = cys * ne1 + es % ne1;
     int e = (jt * A.n1 + ixe) * A.n1 + iye, f = (js * A.n1 + ixf) * A.n1 + iyf;
     if (touching(A, e, f)) continue;  // warp-uniform
-    for (int i = lane; i < nq * nq; i += 32) {
-      int q = i / nq, r = i % nq;
-      long iq = (long)e * nq + q, ir = (long)f * nq + r;
-      double x[3] = {A.gpx[iq], A.gpx[st + iq], A.gpx[2 * st + iq]};
-      double nx[3] = {A.gpn[iq], A.gpn[st + iq], A.gpn[2 * st + iq]};
-      double y[3] = {A.gpx[ir], A.gpx[st + ir], A.gpx[2 * st + ir]};
-      double ny[3] = {A.gpn[ir], A.gpn[st + ir], A.gpn[2 * st + ir]};
-      PairKernel pk = cfie_kernel(A.hard, A.kappa, A.eta, x, nx, A.gpa[iq], y, ny, A.gpa[ir]);
-      double w = A.gw[q / A.ng] * A.gw[q % A.ng] * A.gw[r / A.ng] * A.gw[r % A.ng] * h4;
-      ks[i] = cscale(pk.ks, w);
-      gc[i] = cscale(pk.gc, w);
+    // stage the Gauss points (x, n~, a) and the weighted basis values / curls of both elements
+    for (int i = lane; i < 2 * nq; i += 32) {
+      int side = i / nq, q = i % nq;
+      long iq = (long)(side ? f : e) * nq + q;
+      T *o = pts + (side * nq + q) * 7;
+      for (int c = 0; c < 3; ++c) {
+        o[c] = (T)A.gpx[c * st + iq];
+        o[3 + c] = (T)A.gpn[c * st + iq];
+      }
+      o[6] = (T)A.gpa[iq];
+    }
+    for (int i = lane; i < 2 * nq * nloc; i += 32) {
+      int side = i / (nq * nloc), q = (i / nloc) % nq, k = i % nloc;
+      int ix = side ? ixf : ixe, iy = side ? iyf : iye, el = side ? f : e;
+      double v, ds, dt;
+      basis_gp(A, ix, iy, k, q, v, ds, dt);
+      double w = A.gw[q / A.ng] * A.gw[q % A.ng];
+      (side ? phf : phe)[q * nloc + k] = (T)(v * w);
+      if (A.hard) {
+        double c[3];
+        curl_gp(A, (long)el * nq + q, ds, dt, c);
+        for (int d = 0; d < 3; ++d) (side ? cuf : cue)[(q * nloc + k) * 3 + d] = (T)(c[d] * w);
+      }
     }
     __syncwarp();
+    for (int i = lane; i < nq * nq; i += 32) {
+      int q = i / nq, r = i % nq;
+      const T *X = pts + q * 7, *Y = pts + (nq + r) * 7;
+      PK<T> pk = cfie_kernel_t<T>(A.hard, kap, eta, X, X + 3, X[6], Y, Y + 3, Y[6]);
+      ks[2 * i] = pk.ksx * h2 * h2;
+      ks[2 * i + 1] = pk.ksy * h2 * h2;
+      gc[2 * i] = pk.gcx * h2 * h2;
+      gc[2 * i + 1] = pk.gcy * h2 * h2;
+    }
+    __syncwarp();
+    // Tm[q][l] = sum_r ks[q][r] phi_l(r);  Tc[d][q][l] = sum_r gc[q][r] c_l,d(r)
     for (int i = lane; i < nq * nloc; i += 32) {
       int q = i / nloc, l = i % nloc;
-      double2 t = cmk(0, 0), c0 = cmk(0, 0), c1 = cmk(0, 0), c2 = cmk(0, 0);
+      T tx = 0, ty = 0, c0x = 0, c0y = 0, c1x = 0, c1y = 0, c2x = 0, c2y = 0;
       for (int r = 0; r < nq; ++r) {
-        double v, ds, dt;
-        basis_gp(A, ixf, iyf, l, r, v, ds, dt);
-        t = cadd(t, cscale(ks[q * nq + r], v));
+        T kx = ks[2 * (q * nq + r)], ky = ks[2 * (q * nq + r) + 1], ph = phf[r * nloc + l];
+        tx += kx * ph;
+        ty += ky * ph;
         if (A.hard) {
-          double cl[3];
-          curl_gp(A, (long)f * nq + r, ds, dt, cl);
-          double2 g = gc[q * nq + r];
-          c0 = cadd(c0, cscale(g, cl[0]));
-          c1 = cadd(c1, cscale(g, cl[1]));
-          c2 = cadd(c2, cscale(g, cl[2]));
+          T gx = gc[2 * (q * nq + r)], gy = gc[2 * (q * nq + r) + 1];
+          const T *cl = cuf + (r * nloc + l) * 3;
+          c0x += gx * cl[0]; c0y += gy * cl[0];
+          c1x += gx * cl[1]; c1y += gy * cl[1];
+          c2x += gx * cl[2]; c2y += gy * cl[2];
         }
       }
-      T[i] = t;
+      Tm[2 * i] = tx;
+      Tm[2 * i + 1] = ty;
       if (A.hard) {
-        Tc[i] = c0;
-        Tc[nq * nloc + i] = c1;
-        Tc[2 * nq * nloc + i] = c2;
+        Tc[2 * i] = c0x; Tc[2 * i + 1] = c0y;
+        Tc[2 * (nq * nloc + i)] = c1x; Tc[2 * (nq * nloc + i) + 1] = c1y;
+        Tc[2 * (2 * nq * nloc + i)] = c2x; Tc[2 * (2 * nq * nloc + i) + 1] = c2y;
       }
     }
     __syncwarp();
     for (int i = lane; i < nloc * nloc; i += 32) {
       int k = i / nloc, l = i % nloc;
-      double2 acc = cmk(0, 0);
+      T ax = 0, ay = 0;
       for (int q = 0; q < nq; ++q) {
-        double v, ds, dt;
-        basis_gp(A, ixe, iye, k, q, v, ds, dt);
-        acc = cadd(acc, cscale(T[q * nloc + l], v));
+        T ph = phe[q * nloc + k];
+        ax += ph * Tm[2 * (q * nloc + l)];
+        ay += ph * Tm[2 * (q * nloc + l) + 1];
         if (A.hard) {
-          double ck[3];
-          curl_gp(A, (long)e * nq + q, ds, dt, ck);
-          for (int d = 0; d < 3; ++d) acc = cadd(acc, cscale(Tc[d * nq * nloc + q * nloc + l], ck[d]));
+          const T *ck = cue + (q * nloc + k) * 3;
+          for (int d = 0; d < 3; ++d) {
+            ax += ck[d] * Tc[2 * (d * nq * nloc + q * nloc + l)];
+            ay += ck[d] * Tc[2 * (d * nq * nloc + q * nloc + l) + 1];
+          }
         }
       }
-      block_add(B, A.nL, leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1),
-                leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1), acc);
+      int row = leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1);
+      int col = leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1);
+      if (smem_block) {
+        double2 *dst = Bs + (size_t)col * A.nL + row;
+        atomicAdd(&dst->x, (double)ax);
+        atomicAdd(&dst->y, (double)ay);
+      } else {
+        block_add(Bg, A.nL, row, col, cmk((double)ax, (double)ay));
+      }
     }
     __syncwarp();
+  }
+  if (smem_block) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) {
+      double2 v = Bs[i];
+      atomicAdd(&Bg[i].x, v.x);
+      atomicAdd(&Bg[i].y, v.y);
+    }
   }
 }
 
@@ -407,12 +500,23 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   NearArgs A = near_args(d, S, o);
   int nblk = (int)S.near_src.size();
   if (nblk > 0) {
-    int nq = S.ng * S.ng;
-    size_t per = (size_t)(2 * nq * nq + 4 * nq * S.nloc) * sizeof(double2);
-    int warps = 4;
-    size_t smem = per * warps;
-    IGA_CUDA(cudaFuncSetAttribute(k_near_regular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_near_regular<<<nblk, 32 * warps, smem, st>>>(A);
+    const int nq = S.ng * S.ng, nloc = S.nloc;
+    const bool f32 = o.precision == IGABEM_MIXED_FP32;
+    const size_t tsz = f32 ? sizeof(float) : sizeof(double);
+    const size_t per = (size_t)(2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc +
+                                6 * nq * nloc) * tsz;
+    const size_t bsm = (size_t)S.nL * S.nL * sizeof(double2);
+    const int smem_block = bsm <= 48 * 1024 ? 1 : 0;
+    int warps = 8;
+    while (warps > 1 && per * warps + (smem_block ? bsm : 0) > 200 * 1024) warps /= 2;
+    size_t smem = per * warps + (smem_block ? bsm : 0);
+    if (f32) {
+      IGA_CUDA(cudaFuncSetAttribute(k_near_regular_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_near_regular_t<float><<<nblk, 32 * warps, smem, st>>>(A, smem_block);
+    } else {
+      IGA_CUDA(cudaFuncSetAttribute(k_near_regular_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_near_regular_t<double><<<nblk, 32 * warps, smem, st>>>(A, smem_block);
+    }
     note_launch();
     IGA_CUDA(cudaGetLastError());
   }

@@ -15,6 +15,14 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
 void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
                        cudaStream_t st);
 
+// leaf kernels (k_leaf.cu)
+bool leaf_kernels_supported(const HostSetup &S);
+void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                      cudaStream_t st);
+void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
+void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
+void launch_blocks_to_fp32(const double *src, float *dst, size_t n, cudaStream_t st);
+
 // operator application (k_apply.cu): y = A x for R columns, x and y device [N][R] complex
 void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                    const double *x, double *y, cudaStream_t st);

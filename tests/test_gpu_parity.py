@@ -103,14 +103,16 @@ def test_mixed_fmm_matvec_matches_interpolated_kernel_matrix(hard, kappa):
 def test_mixed_solve_far_field_matches_fp64(hard):
     """The mixed-precision solve reproduces the FP64 far field to 1e-5 (spec bar)."""
     kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=int(hard), cheb_q=7, leaf_offset=1,
-              eta_adm=0.5, tol=1e-8)
+              eta_adm=0.5)
     xh = inputs.fibonacci_directions(100)
     d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])
     u = {}
-    for prec in (B.FP64, B.MIXED_FP32):
-        prob, info = G.problem("deformed" if hard else "sphere", precision=prec, **kw)
+    # FP64 to 1e-8; the mixed operator carries FP32 rounding (~1e-7 of ||A x||), so its GMRES stops
+    # at 1e-6
+    for prec, tol in ((B.FP64, 1e-8), (B.MIXED_FP32, 1e-6)):
+        prob, info = G.problem("deformed" if hard else "sphere", precision=prec, tol=tol, **kw)
         x, sinfo = B.igabem_solve(prob, d, info["n_dofs"])
-        assert sinfo["rel_residual"] <= 1e-8
+        assert sinfo["rel_residual"] <= tol
         u[prec] = B.igabem_farfield(prob, x, xh)
         B.igabem_problem_destroy(prob)
     assert G.rel(u[B.MIXED_FP32], u[B.FP64]) < 1e-5

@@ -28,13 +28,17 @@ sys.path.insert(0, ROOT)
 METRIC = "CFIE matvecs/s & solves/s at far-field err≤1e-5 vs FP64; p50/p99 solve latency"
 
 WORKLOADS = {
+    # leaf offset b (leaves of 2^b x 2^b elements) per precision: the faster set-up + solve on GB300;
+    # the mixed form's GMRES stops at its FP32 rounding floor
     "sphere_soft_6x32x32_p2_k8": dict(geometry="sphere", level_m=5, degree_p=2, kappa=8.0, bc=0,
-                                      cheb_q=7, eta_adm=0.5, leaf_offset=2, tol=1e-6, n_dir=100),
+                                      cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
+                                      tol={"fp64": 1e-6, "mixed": 1e-6}, n_dir=100),
 }
 DEFAULT = "sphere_soft_6x32x32_p2_k8"
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # kernel sample arithmetic, see the design doc
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 FP64_PEAK_TFLOPS = 1.25                      # GB300 nominal FP64 (no measured figure available)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
 def parse():
@@ -51,7 +55,7 @@ def parse():
 
 def patches_of(kind):
     from paper_2306_11324_gb300 import inputs
-    return inputs.unit_sphere_patches() if kind == "sphere" else inputs.deformed_sphere_patches(spans=8)
+    return inputs.unit_sphere_patches() if kind == "sphere" else inputs.deformed_sphere_patches(spans=4)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -187,90 +191,97 @@ def main():
     ctx = B.igabem_create(local, stream.cuda_stream)
     patches = patches_of(wl["geometry"])
     geom = B.igabem_geometry_create(ctx, patches)
-    opt = B.igabem_default_options(level_m=wl["level_m"], degree_p=wl["degree_p"], kappa=wl["kappa"],
-                                   eta_cfie=wl["kappa"], bc=wl["bc"], cheb_q=wl["cheb_q"],
-                                   eta_adm=wl["eta_adm"], leaf_offset=wl["leaf_offset"], tol=wl["tol"],
-                                   precision=B.FP64 if args.precision == "fp64" else B.MIXED_FP32)
     dirs = np.array([[0.0, 0.0, 1.0]])
     xhat = inputs.fibonacci_directions(wl["n_dir"])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # larger than the 129 MB L2
 
-    def step(host=False):
+    def options(precision):
+        leaf = wl["leaf_offset"][precision]
+        return B.igabem_default_options(level_m=wl["level_m"], degree_p=wl["degree_p"], kappa=wl["kappa"],
+                                        eta_cfie=wl["kappa"], bc=wl["bc"], cheb_q=wl["cheb_q"],
+                                        eta_adm=wl["eta_adm"], leaf_offset=leaf, tol=wl["tol"][precision],
+                                        precision=B.FP64 if precision == "fp64" else B.MIXED_FP32, profile=1)
+
+    def request(opt, host=False):
+        """One request through the public API; returns (problem, info, solve info, far field)."""
         prob = B.igabem_problem_create(geom, opt)
         info = B.igabem_problem_info(prob)
         N = info["n_dofs"]
-        dens = np.empty((N, 1), np.complex128) if host else torch.empty((N, 1), dtype=torch.complex128, device="cuda")
+        dens = None if host else torch.empty((N, 1), dtype=torch.complex128, device="cuda")
         dens, sinfo = B.igabem_solve(prob, dirs, N, density=dens)
-        u = B.igabem_farfield(prob, dens, xhat,
-                              out=np.empty((len(xhat), 1), np.complex128) if host else None)
-        return prob, info, sinfo, dens, u
+        u = B.igabem_farfield(prob, dens, xhat)
+        return prob, info, sinfo, u
 
-    for _ in range(args.warmup):
-        prob, *_ = step()
-        B.igabem_problem_destroy(prob)
-    torch.cuda.synchronize()
-
-    # ---- timed region: K full requests, device-resident outputs ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    prof_tot = {}
-    launches = 0
-    iters, mvs = [], []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            prob = B.igabem_problem_create(geom, opt)
-            B.igabem_profile_enable(prob, True)
-            info = B.igabem_problem_info(prob)
-            N = info["n_dofs"]
-            dens = torch.empty((N, 1), dtype=torch.complex128, device="cuda")
-            dens, sinfo = B.igabem_solve(prob, dirs, N, density=dens)
-            u = B.igabem_farfield(prob, dens, xhat)
-            ev[k][1].record(stream)
-            pr = B.igabem_profile_get(prob)
-            launches += pr["launches"]
-            for name, v in pr["phases"].items():
-                a = prof_tot.setdefault(name, {"ms": 0.0, "calls": 0, "launches": 0})
-                for key in a:
-                    a[key] += v[key]
-            iters.append(sinfo["iterations"])
-            mvs.append(sinfo["n_matvecs"])
+    def run_form(precision, steps, warmup, timed_clocks):
+        opt = options(precision)
+        for _ in range(warmup):
+            prob, *_ = request(opt)
             B.igabem_problem_destroy(prob)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    solves = args.steps * world
-    value = solves / (total_ms / 1e3)
-
-    # matvec-only throughput on a resident problem (same workload)
-    prob = B.igabem_problem_create(geom, opt)
-    info = B.igabem_problem_info(prob)
-    x = torch.tensor(inputs.random_complex(info["n_dofs"], cols=1), device="cuda")
-    y = torch.empty_like(x)
-    B.igabem_matvec(prob, x, y)
-    nmv = 20
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(nmv):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        prof_tot, launches, iters, mvs, u_last = {}, 0, [], [], None
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                prob, info, sinfo, u = request(opt)
+                ev[k][1].record(stream)
+                pr = B.igabem_profile_get(prob)
+                launches += pr["launches"]
+                for name, v in pr["phases"].items():
+                    a = prof_tot.setdefault(name, {"ms": 0.0, "calls": 0, "launches": 0})
+                    for key in a:
+                        a[key] += v[key]
+                iters.append(sinfo["iterations"])
+                mvs.append(sinfo["n_matvecs"])
+                u_last = u
+                B.igabem_problem_destroy(prob)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = sum(step_ms)
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # operator applications on a resident problem
+        prob = B.igabem_problem_create(geom, opt)
+        info = B.igabem_problem_info(prob)
+        x = torch.tensor(inputs.random_complex(info["n_dofs"], cols=1), device="cuda")
+        y = torch.empty_like(x)
         B.igabem_matvec(prob, x, y)
-    b.record(stream)
-    torch.cuda.synchronize()
-    matvec_ms = a.elapsed_time(b) / nmv
+        nmv = 20
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nmv):
+            B.igabem_matvec(prob, x, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        B.igabem_problem_destroy(prob)
+        lat = sorted(step_ms)
+        return {"precision": precision, "solves_per_s": steps * world / (total_ms / 1e3),
+                "ms_per_step": total_ms / steps, "matvec_ms": a.elapsed_time(b) / nmv,
+                "matvecs_per_s": 1e3 / (a.elapsed_time(b) / nmv) * world,
+                "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "iters": iters[-1], "mvs": mvs[-1], "launches": launches, "info": info,
+                "phases": {k: round(v["ms"] / steps, 3) for k, v in prof_tot.items() if v["ms"] > 0},
+                "prof": prof_tot, "u": u_last.cpu().numpy(), "clocks": clk.summary(),
+                "leaf_offset": wl["leaf_offset"][precision], "tol": wl["tol"][precision]}
 
-    # far-field error of this run vs the FP64 path (FP64 run: 0 by definition)
-    far_err = 0.0 if args.precision == "fp64" else None
+    main_form = run_form(args.precision, args.steps, args.warmup, True)
+    other = "mixed" if args.precision == "fp64" else "fp64"
+    other_form = run_form(other, max(1, min(args.steps, 3)), 1, False)
+    fp64_u = (main_form if args.precision == "fp64" else other_form)["u"]
+    mix_u = (other_form if args.precision == "fp64" else main_form)["u"]
+    far_err = float(np.abs(mix_u - fp64_u).max() / np.abs(fp64_u).max())
 
     # ---- end to end through the public API with host buffers ----
+    opt = options(args.precision)
     ke = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -287,6 +298,7 @@ def main():
         e2e_steps.append(time.perf_counter() - s0)
     e2e_value = ke / (time.perf_counter() - t0) * world
     _, _, knots, ctrl, w = inputs.patches_to_arrays(patches)
+    info = main_form["info"]
     h2d = int(knots.nbytes + ctrl.nbytes + w.nbytes + 8 * 2 * 2 * len(patches) + dirs.nbytes + xhat.nbytes)
     d2h = int(info["n_dofs"] * 16 + len(xhat) * 16)
 
@@ -295,40 +307,50 @@ def main():
     Q = wl["cheb_q"] ** 2
     hard = bool(wl["bc"])
     C = 7 if hard else 1
-    m2l = prof_tot.get("m2l", {"ms": 0.0, "calls": 0})
+    m2l = main_form["prof"].get("m2l", {"ms": 0.0, "calls": 0})
     flops_per_mv = far * Q * Q * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C)
     m2l_ms = m2l["ms"] / max(1, m2l["calls"])
     achieved = flops_per_mv / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_m2l (FP64)", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate of the profiling recipe (no measured FP64 peak)",
+    fp64 = args.precision == "fp64"
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    roofline = {"bound": "alu", "kernel": "k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": ("nominal GB300 FP64 rate of the profiling recipe" if fp64 else
+                                "FP32 CUDA-core rate from unit counts and the maximum SM clock") +
+                               " (no measured figure in MEASURED_PEAKS.json)",
                 "algorithmic_flops_per_matvec": flops_per_mv, "avg_ms_per_matvec": m2l_ms}
 
-    phases = {k: round(v["ms"] / args.steps, 3) for k, v in prof_tot.items() if v["ms"] > 0}
-    lat = sorted(step_ms)
+    def summary(f):
+        return {"precision": f["precision"], "solves_per_s": f["solves_per_s"], "matvecs_per_s": f["matvecs_per_s"],
+                "matvec_ms": f["matvec_ms"], "ms_per_step": f["ms_per_step"], "leaf_offset": f["leaf_offset"],
+                "gmres_tol": f["tol"], "gmres_iterations": f["iters"], "matvecs_per_solve": f["mvs"],
+                "solve_latency_ms": {"p50": f["p50"], "p99": f["p99"]}, "phase_ms_per_step": f["phases"],
+                "setup_ms": f["info"]["setup_ms"]}
+
     out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "metric": METRIC, "value": main_form["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_form["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32+f64",
         "data": "synthetic (seeded geometry, plane wave)",
         "config": {"workload": args.workload, "n_dofs": info["n_dofs"], "n_elements": info["n_elements"],
-                   "precision": args.precision, "leaf_offset": wl["leaf_offset"], "cheb_q": wl["cheb_q"],
-                   "eta_adm": wl["eta_adm"], "kappa": wl["kappa"], "tol": wl["tol"],
+                   "precision": args.precision, "leaf_offset": main_form["leaf_offset"], "cheb_q": wl["cheb_q"],
+                   "eta_adm": wl["eta_adm"], "kappa": wl["kappa"], "tol": main_form["tol"],
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"},
-        "matvecs_per_s": 1e3 / matvec_ms * world,
-        "matvec_ms": matvec_ms,
-        "solve_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "gmres_iterations": iters[-1], "matvecs_per_solve": mvs[-1],
-        "farfield_rel_err_vs_fp64": far_err,
-        "phase_ms_per_step": phases,
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "matvecs_per_s": main_form["matvecs_per_s"],
+        "matvec_ms": main_form["matvec_ms"],
+        "solve_latency_ms": {"p50": main_form["p50"], "p99": main_form["p99"]},
+        "gmres_iterations": main_form["iters"], "matvecs_per_solve": main_form["mvs"],
+        "phase_ms_per_step": main_form["phases"],
+        "other_form": summary(other_form),
+        "farfield_rel_err_mixed_vs_fp64": far_err,
+        "gpu_launches": main_form["launches"],
+        "clocks": main_form["clocks"],
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * statistics.mean(e2e_steps)},
         "roofline": roofline,
     }
-    B.igabem_problem_destroy(prob)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(wl)
     if rank == 0:

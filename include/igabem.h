@@ -74,6 +74,7 @@ typedef struct {
   int max_iter;        /* iteration limit per right-hand side */
   double tol;          /* relative residual ||b - A x|| <= tol ||b|| */
   int no_fmm;          /* 1: treat every element pair as near (dense Galerkin matrix; tests) */
+  int profile;         /* 1: per-phase CUDA-event timing from problem creation on (igabem_profile_*) */
 } igabem_options;
 
 /* Fills the defaults: p = 2, m = 3, kappa = 1, eta_cfie = kappa, sound-soft, q = 7, b = 0,
@@ -91,6 +92,7 @@ typedef struct {
   long n_far_pairs;          /* admissible cluster pairs (M2L) over all levels */
   size_t device_bytes;       /* device memory held by the problem */
   double setup_ms;           /* wall time of igabem_problem_create */
+  double host_setup_ms;      /* of which host-side set-up (tree, lists, tables) */
 } igabem_info;
 
 typedef struct {

@@ -28,14 +28,14 @@ class igabem_options(ctypes.Structure):
                 ("bc", c_int), ("cheb_q", c_int), ("leaf_offset", c_int), ("eta_adm", c_double),
                 ("kappa_cap", c_double), ("gauss_regular", c_int), ("gauss_singular", c_int),
                 ("precision", c_int), ("gmres_restart", c_int), ("max_iter", c_int), ("tol", c_double),
-                ("no_fmm", c_int)]
+                ("no_fmm", c_int), ("profile", c_int)]
 
 
 class igabem_info(ctypes.Structure):
     _fields_ = [("n_dofs", c_long), ("n_patch_dofs", c_long), ("n_elements", c_long),
                 ("n_clusters", c_long), ("n_near_pairs", c_long), ("n_near_element_pairs", c_long),
                 ("n_touching_pairs", c_long), ("n_far_pairs", c_long), ("device_bytes", c_size_t),
-                ("setup_ms", c_double)]
+                ("setup_ms", c_double), ("host_setup_ms", c_double)]
 
 
 class igabem_solve_info(ctypes.Structure):

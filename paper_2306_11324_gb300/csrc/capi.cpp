@@ -241,6 +241,7 @@ void igabem_default_options(igabem_options *o) {
   o->max_iter = 1000;
   o->tol = 1e-6;
   o->no_fmm = 0;
+  o->profile = 0;
 }
 
 int igabem_create(igabem_ctx **out, int device, void *stream) {
@@ -330,9 +331,12 @@ int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_p
     auto *P = new igabem_problem();
     P->geom = geom;
     P->opt = *opt;
+    P->prof.on = opt->profile != 0;
     try {
       HostSetup &S = P->S;
+      double th = now_ms();
       build_setup(geom->patches, *opt, S);
+      P->info.host_setup_ms = now_ms() - th;
       cudaStream_t st = geom->ctx->stream;
       const int Q = S.q * S.q, nq = S.ng * S.ng;
       const long nleaf = S.lev[S.L].n;

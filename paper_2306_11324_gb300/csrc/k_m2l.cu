@@ -224,6 +224,140 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_rows(M2LArgs A, int cr0)
   }
 }
 
+// Sample of one node pair in precision T: returns the kernel value of the requested type.
+//   type 0: soft  a_y G'(r)/r (x-y).n~x - i eta a_x a_y G
+//   type 1: hard  a_x G'(r)/r (y-x).n~y
+//   type 2: hard  G
+// x, y: FP64 absolute node positions (FP64 path) or offsets from the cluster centres (FP32 path,
+// with the pair constants D, |D|, |D|^2; the pair factor exp(i kappa |D|) is applied by the caller).
+template <class T>
+__device__ inline C2<T> node_sample(int type, const T *x, const T *nx, T ax, const T *y, const T *ny, T ay,
+                                    const T *D, T Dn, T D2, T kappa, T eta) {
+  constexpr bool F32 = std::is_same<T, float>::value;
+  T d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  T r2, ir, r, cph, sph, dn_x, dn_y;
+  if constexpr (F32) {
+    T Dd = D[0] * d0 + D[1] * d1 + D[2] * d2;
+    T dd = d0 * d0 + d1 * d1 + d2 * d2;
+    T num = (T)2 * Dd + dd;
+    r2 = D2 + num;
+    ir = rsqrtf(r2);
+    r = r2 * ir;
+    T ph = kappa * __fdividef(num, r + Dn);
+    T kq = rintf(ph * 0.15915494309189535f);
+    ph = fmaf(-kq, 6.28318548202514648f, ph);
+    ph = fmaf(-kq, -1.7484556e-07f, ph);
+    __sincosf(ph, &sph, &cph);
+    dn_x = D[0] * nx[0] + D[1] * nx[1] + D[2] * nx[2] + d0 * nx[0] + d1 * nx[1] + d2 * nx[2];
+    dn_y = D[0] * ny[0] + D[1] * ny[1] + D[2] * ny[2] + d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
+  } else {
+    r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    ir = rsqrt(r2);
+    r = r2 * ir;
+    sincos(kappa * r, &sph, &cph);
+    dn_x = d0 * nx[0] + d1 * nx[1] + d2 * nx[2];
+    dn_y = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
+  }
+  const T f = ir * (T)(0.25 / IGA_PI), kr = kappa * r, g2 = f * ir * ir;
+  const C2<T> G = c2(cph * f, sph * f);
+  if (type == 2) return G;
+  const C2<T> dG = c2((-cph - sph * kr) * g2, (-sph + cph * kr) * g2);
+  if (type == 1) {
+    T w1 = -ax * dn_y;
+    return c2(dG.x * w1, dG.y * w1);
+  }
+  T w1 = ay * dn_x, w2 = ax * ay * eta;
+  return c2(dG.x * w1 + G.y * w2, dG.y * w1 - G.x * w2);
+}
+
+// Multi-column M2L: per target cluster and column chunk, every coupling block S_ts (q^2 x q^2) is
+// generated once into shared memory and applied to the chunk's columns of xhat_s with a register
+// tiled product (4 x 4 complex outputs per thread).  A chunk lies within one channel, so one kernel
+// type per block.
+constexpr int GEMM_T = 16;  // thread tile grid 16 x 16
+
+template <class T>
+__global__ void __launch_bounds__(256) k_m2l_gemm(M2LArgs A, int Wc) {
+  extern __shared__ __align__(16) unsigned char smg[];
+  constexpr bool F32 = std::is_same<T, float>::value;
+  int li = 0;
+  while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
+  const M2LLevel &L = A.lev[li];
+  const int t = blockIdx.x - L.first;
+  const int Q = A.Q;
+  const long NQ = (long)L.n * Q;
+  const int cr0 = blockIdx.y * Wc, ch = cr0 / A.R;
+  const int type = A.hard ? (ch == 0 ? 1 : 2) : 0;
+  C2<T> *S = reinterpret_cast<C2<T> *>(smg);            // [Q][Q]
+  C2<T> *Xs = S + Q * Q;                                 // [Q][Wc]
+  T *tn = reinterpret_cast<T *>(Xs + Q * Wc);            // target nodes [Q][8]
+  T *sn = tn + Q * 8;                                    // source nodes [Q][8]
+  const T kappa = (T)A.kappa, eta = (T)A.eta;
+  for (int a = threadIdx.x; a < Q; a += blockDim.x) {
+    long ia = (long)t * Q + a;
+    for (int c = 0; c < 7; ++c) tn[a * 8 + c] = F32 ? (T)L.nodes32[c * NQ + ia] : (T)L.nodes[c * NQ + ia];
+  }
+  const int ty = threadIdx.x / GEMM_T, tx = threadIdx.x % GEMM_T;
+  C2<T> acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = c2((T)0, (T)0);
+  for (int kk = L.far_ptr[t]; kk < L.far_ptr[t + 1]; ++kk) {
+    const int s = L.far_src[kk];
+    T D[3] = {0, 0, 0}, Dn = 0, D2 = 0;
+    C2<T> e0 = c2((T)1, (T)0);
+    if constexpr (F32) {
+      const float4 p0 = reinterpret_cast<const float4 *>(L.pc)[2 * kk];
+      const float4 p1 = reinterpret_cast<const float4 *>(L.pc)[2 * kk + 1];
+      D[0] = p0.x; D[1] = p0.y; D[2] = p0.z; Dn = p0.w;
+      D2 = p1.x;
+      e0 = c2(p1.y, p1.z);
+    }
+    __syncthreads();  // previous contraction done with S, Xs, sn
+    for (int b = threadIdx.x; b < Q; b += blockDim.x) {
+      long ib = (long)s * Q + b;
+      for (int c = 0; c < 7; ++c) sn[b * 8 + c] = F32 ? (T)L.nodes32[c * NQ + ib] : (T)L.nodes[c * NQ + ib];
+    }
+    for (int i = threadIdx.x; i < Q * Wc; i += blockDim.x) {
+      int b = i / Wc, c = i % Wc;
+      double2 v = L.xhat[((long)s * Q + b) * A.CR + cr0 + c];
+      // the pair factor exp(i kappa |D|) is folded into the source coefficients
+      C2<T> xv = c2((T)v.x, (T)v.y);
+      Xs[i] = F32 ? mul(e0, xv) : xv;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+      int a = i / Q, b = i % Q;
+      const T *X = tn + a * 8, *Y = sn + b * 8;
+      S[i] = node_sample<T>(type, X, X + 3, X[6], Y, Y + 3, Y[6], D, Dn, D2, kappa, eta);
+    }
+    __syncthreads();
+    C2<T> part[4][4];  // this pair's sums (blocked accumulation)
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) part[i][j] = c2((T)0, (T)0);
+    for (int b = 0; b < Q; ++b) {
+      C2<T> sv[4], xv[4];
+      for (int i = 0; i < 4; ++i) {
+        int a = ty + GEMM_T * i;
+        sv[i] = a < Q ? S[a * Q + b] : c2((T)0, (T)0);
+      }
+      for (int j = 0; j < 4; ++j) {
+        int c = tx + GEMM_T * j;
+        xv[j] = c < Wc ? Xs[b * Wc + c] : c2((T)0, (T)0);
+      }
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) part[i][j] = fma2(sv[i], xv[j], part[i][j]);
+    }
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] = add(acc[i][j], part[i][j]);
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int a = ty + GEMM_T * i, c = tx + GEMM_T * j;
+      if (a < Q && c < Wc)
+        L.yhat[((long)t * Q + a) * A.CR + cr0 + c] = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+    }
+}
+
 // pair constants of the FP32 path, per admissible pair k of a level (CSR order):
 // [D (3), |D|, |D|^2, cos(kappa |D|), sin(kappa |D|), 0] with D = c_t - c_s in FP64
 __global__ void k_pair_consts(const int *__restrict__ far_ptr, const int *__restrict__ far_src,
@@ -306,10 +440,30 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     L.first = nblocks;
     nblocks += S.lev[l].n;
   }
-  if (fp32)
+  if (R > 1) {
+    // column chunk: the largest divisor of R not above 64 (chunks never straddle two channels)
+    int Wc = 1;
+    for (int w = std::min(R, 64); w >= 1; --w)
+      if (R % w == 0) {
+        Wc = w;
+        break;
+      }
+    const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
+    size_t smem = (size_t)A.Q * A.Q * 2 * tsz + (size_t)A.Q * Wc * 2 * tsz + (size_t)A.Q * 16 * tsz;
+    dim3 grid(nblocks, A.CR / Wc);
+    if (fp32) {
+      IGA_CUDA(cudaFuncSetAttribute(k_m2l_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_m2l_gemm<float><<<grid, 256, smem, st>>>(A, Wc);
+    } else {
+      IGA_CUDA(cudaFuncSetAttribute(k_m2l_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_m2l_gemm<double><<<grid, 256, smem, st>>>(A, Wc);
+    }
+    note_launch();
+  } else if (fp32) {
     launch_typed<float>(A, nblocks, st);
-  else
+  } else {
     launch_typed<double>(A, nblocks, st);
+  }
   IGA_CUDA(cudaGetLastError());
 }
 

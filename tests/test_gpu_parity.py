@@ -116,3 +116,22 @@ def test_mixed_solve_far_field_matches_fp64(hard):
         u[prec] = B.igabem_farfield(prob, x, xh)
         B.igabem_problem_destroy(prob)
     assert G.rel(u[B.MIXED_FP32], u[B.FP64]) < 1e-5
+
+
+@pytest.mark.parametrize("prec,hard", [(B.FP64, False), (B.FP64, True), (B.MIXED_FP32, False),
+                                       (B.MIXED_FP32, True)])
+def test_multi_rhs_fmm_matvec(prec, hard):
+    """Several right-hand sides at once (the multi-column M2L): every column against the oracle."""
+    m, p, leaf, q, kappa = 2, 1, 2, 5, 3.0
+    prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
+                           leaf_offset=m - leaf, eta_adm=0.5, precision=prec)
+    sp = C.sphere_space(m, p, hard)
+    Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
+    x = inputs.random_complex(sp.N, seed=77, cols=6)
+    y = B.igabem_matvec(prob, x)
+    tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
+    assert G.rel(y, Amat @ x) < tol
+    # the same columns one at a time give the same result
+    y0 = B.igabem_matvec(prob, np.ascontiguousarray(x[:, 2]))
+    assert G.rel(y0, y[:, 2]) < (1e-13 if prec == B.FP64 else MIXED_MATVEC_TOL)
+    B.igabem_problem_destroy(prob)

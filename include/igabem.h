@@ -183,6 +183,52 @@ int igabem_solve(igabem_problem *prob, int n_rhs, const double *dirs, void *dens
 int igabem_farfield(igabem_problem *prob, int n_rhs, const void *density, int n_dir,
                     const double *xhat, void *uinf);
 
+/* ------------------------------------------------------------------------------------------------
+ * Serving loop.  A server solves independent scattering requests (different geometries, levels,
+ * wavenumbers, boundary conditions, right-hand-side counts) concurrently on one device: up to
+ * max_active requests run at once, each on its own CUDA stream, and a request is admitted only when
+ * the exact device memory of its set-up plus its solve fits the server's budget alongside the
+ * requests already running; a request that arrives while others run starts as soon as a slot and
+ * memory are free.  Each request runs the whole path (set-up, right-hand sides for its incident
+ * directions, GMRES, far field at its directions) with its own options; its result does not depend
+ * on what else runs.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct igabem_server igabem_server;
+typedef struct igabem_request igabem_request;
+
+typedef struct {
+  long submitted, completed, failed;
+  double p50_ms, p99_ms, mean_ms; /* latency from submission to completion of completed requests */
+  double solves_per_s;            /* completed requests / (last completion - first submission) */
+  size_t peak_bytes;              /* largest admitted device memory at one time */
+  size_t budget_bytes;
+  int peak_active;                /* largest number of requests running at one time */
+} igabem_server_stats;
+
+/* Starts a server with max_active worker threads (1..64) on the context's device.  memory_budget in
+   bytes (0: 90 % of the free device memory; never more than the free memory). */
+int igabem_server_create(igabem_ctx *ctx, size_t memory_budget, int max_active, igabem_server **out);
+/* Finishes every submitted request, then stops the workers and frees the server. */
+int igabem_server_destroy(igabem_server *srv);
+/* Queues a request: geometry (must outlive the request), options (copied), n_rhs incident directions
+   dirs[n_rhs][3] and n_dir far-field directions xhat[n_dir][3] (host arrays, copied).  Returns at
+   once; the request handle belongs to the caller until igabem_request_destroy. */
+int igabem_submit(igabem_server *srv, igabem_geom *geom, const igabem_options *opt, int n_rhs,
+                  const double *dirs, int n_dir, const double *xhat, igabem_request **out);
+/* *done = 1 once the request has finished (successfully or not). */
+int igabem_poll(igabem_request *req, int *done);
+/* Blocks until the request finished or timeout_s seconds passed (IGABEM_ETIMEOUT); timeout_s < 0
+   waits without limit. */
+int igabem_wait(igabem_request *req, double timeout_s);
+/* Copies the far field uinf[n_dir][n_rhs] (complex, host memory) and the solve information (its
+   solve_ms is the request's latency from submission); returns the request's status: IGABEM_OK,
+   IGABEM_ENOMEM if the request alone exceeds the memory budget, IGABEM_ENOT_CONVERGED (far field
+   still written), or the error of a failed set-up or solve.  IGABEM_ETIMEOUT if not finished. */
+int igabem_result(igabem_request *req, void *uinf, igabem_solve_info *info);
+/* Waits for the request if it is still running, then frees it. */
+void igabem_request_destroy(igabem_request *req);
+int igabem_server_get_stats(igabem_server *srv, igabem_server_stats *out);
+
 /* Far-field pattern without any device memory allocation.  The paper has no counterpart: this is a
    property of the library for callers that cannot allocate device memory -- a host program whose
    own caching allocator has reserved the device (a library cudaMalloc would fail or fragment its

@@ -52,6 +52,12 @@ class igabem_profile(ctypes.Structure):
                 ("phase_launches", c_long * len(PHASES))]
 
 
+class igabem_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_long), ("completed", c_long), ("failed", c_long), ("p50_ms", c_double),
+                ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
+                ("peak_bytes", c_size_t), ("budget_bytes", c_size_t), ("peak_active", c_int)]
+
+
 class IgabemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -79,6 +85,15 @@ SIGNATURES = {
     "igabem_profile_enable": (c_int, [c_void_p, c_int]),
     "igabem_profile_get": (c_int, [c_void_p, ctypes.POINTER(igabem_profile), c_int]),
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    "igabem_server_create": (c_int, [c_void_p, c_size_t, c_int, ctypes.POINTER(c_void_p)]),
+    "igabem_server_destroy": (c_int, [c_void_p]),
+    "igabem_submit": (c_int, [c_void_p, c_void_p, ctypes.POINTER(igabem_options), c_int, c_void_p, c_int,
+                              c_void_p, ctypes.POINTER(c_void_p)]),
+    "igabem_poll": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "igabem_wait": (c_int, [c_void_p, c_double]),
+    "igabem_result": (c_int, [c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
+    "igabem_request_destroy": (None, [c_void_p]),
+    "igabem_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(igabem_server_stats)]),
 }
 
 
@@ -220,6 +235,62 @@ def igabem_farfield(prob, density, xhat, out=None):
     out = _like(density, (xh.shape[0], R)) if out is None else out
     _check(lib().igabem_farfield(prob, R, _ptr(density), xh.shape[0], _ptr(xh), _ptr(out)))
     return out
+
+
+def igabem_server_create(ctx, memory_budget: int = 0, max_active: int = 4):
+    h = c_void_p()
+    _check(lib().igabem_server_create(ctx, memory_budget, max_active, ctypes.byref(h)))
+    return h
+
+
+def igabem_server_destroy(srv):
+    _check(lib().igabem_server_destroy(srv))
+
+
+class Request:
+    """A submitted request and the host arrays it was given (kept alive until it is destroyed)."""
+
+    def __init__(self, handle, n_rhs, n_dir, keep):
+        self.handle, self.n_rhs, self.n_dir, self._keep = handle, n_rhs, n_dir, keep
+
+
+def igabem_submit(srv, geom, opt: igabem_options, dirs, xhat) -> Request:
+    d = _host(dirs, np.float64).reshape(-1, 3)
+    xh = _host(xhat, np.float64).reshape(-1, 3)
+    h = c_void_p()
+    _check(lib().igabem_submit(srv, geom, ctypes.byref(opt), d.shape[0], _ptr(d), xh.shape[0], _ptr(xh),
+                               ctypes.byref(h)))
+    return Request(h, d.shape[0], xh.shape[0], (d, xh, opt))
+
+
+def igabem_poll(req: Request) -> bool:
+    done = c_int(0)
+    _check(lib().igabem_poll(req.handle, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def igabem_wait(req: Request, timeout_s: float = -1.0):
+    _check(lib().igabem_wait(req.handle, timeout_s))
+
+
+def igabem_result(req: Request, raise_errors: bool = True):
+    """(far field [n_dir][n_rhs], solve info dict, status code)."""
+    u = np.zeros((req.n_dir, req.n_rhs), np.complex128)
+    info = igabem_solve_info()
+    rc = lib().igabem_result(req.handle, _ptr(u), ctypes.byref(info))
+    if rc != IGABEM_OK and raise_errors:
+        _check(rc)
+    return u, {k: getattr(info, k) for k, _ in igabem_solve_info._fields_}, rc
+
+
+def igabem_request_destroy(req: Request):
+    lib().igabem_request_destroy(req.handle)
+
+
+def igabem_server_get_stats(srv) -> dict:
+    st = igabem_server_stats()
+    _check(lib().igabem_server_get_stats(srv, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in igabem_server_stats._fields_}
 
 
 def igabem_farfield_noalloc(prob, density, xhat, uinf):

@@ -13,16 +13,16 @@
 
 namespace igabem {
 
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 namespace {
 thread_local std::string g_error;
 
 struct Failure {
   int code;
 };
-
-double now_ms() {
-  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
 
 bool is_device_ptr(const void *p) {
   if (!p) return false;
@@ -87,6 +87,34 @@ void Arena::release() {
   cap = off = 0;
 }
 
+// device bytes of the per-call work buffers for R columns (and a GMRES basis of gmres_m + 1 vectors)
+size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m) {
+  const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
+  const size_t cz = 2 * sizeof(double);
+  const long nleaf = S.lev[S.L].n;
+  size_t total = 0;
+  auto add = [&](size_t n) { total += (n + 255) & ~size_t(255); };
+  add(S.NX * R * cz);
+  add(nleaf * S.nL * R * cz);
+  add((size_t)S.E * nq * C * R * cz);
+  add(S.N * R * cz);
+  add(S.N * R * cz);
+  add((size_t)34 * 304 * R * cz + 4096);
+  for (int l = S.lmin; l <= S.L; ++l) {
+    add((size_t)S.lev[l].n * Q * C * R * cz);
+    add((size_t)S.lev[l].n * Q * C * R * cz);
+  }
+  if (gmres_m) {
+    add((size_t)(gmres_m + 1) * S.N * R * cz);
+    for (int k = 0; k < 4; ++k) add(S.N * R * cz);
+    add((size_t)(gmres_m + 2) * R * cz);
+    add(R * sizeof(double));
+    add(R * sizeof(double));
+    add((size_t)(gmres_m + 1) * R * cz);
+  }
+  return total;
+}
+
 }  // namespace igabem
 
 using namespace igabem;
@@ -133,31 +161,8 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   R = std::max(R, W.R);
   if (with_gmres) W.gmres_m = std::max(W.gmres_m, m);
   const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
-  const size_t cz = 2 * sizeof(double);
   const long nleaf = S.lev[S.L].n;
-  std::vector<size_t> lev(S.L + 1, 0);
-  size_t total = 0;
-  auto add = [&](size_t n) { total += (n + 255) & ~size_t(255); return n; };
-  add(S.NX * R * cz);
-  add(nleaf * S.nL * R * cz);
-  add((size_t)S.E * nq * C * R * cz);
-  add(S.N * R * cz);
-  add(S.N * R * cz);
-  add((size_t)34 * 304 * R * cz + 4096);
-  for (int l = 0; l <= S.L; ++l) {
-    if (l >= S.lmin) {
-      add((size_t)S.lev[l].n * Q * C * R * cz);
-      add((size_t)S.lev[l].n * Q * C * R * cz);
-    }
-  }
-  if (W.gmres_m) {
-    add((size_t)(W.gmres_m + 1) * S.N * R * cz);
-    for (int k = 0; k < 4; ++k) add(S.N * R * cz);
-    add((size_t)(W.gmres_m + 2) * R * cz);
-    add(R * sizeof(double));
-    add(R * sizeof(double));
-    add((size_t)(W.gmres_m + 1) * R * cz);
-  }
+  size_t total = problem_work_bytes(S, R, W.gmres_m);
   W.arena.reserve(total);
   W.R = R;
   W.xX = W.arena.get<double>(S.NX * R * 2);
@@ -206,7 +211,7 @@ template <class T> size_t bytes_of(const std::vector<T> &v) {
 }
 
 void matvec_dev(igabem_problem *P, int R, const double *x, double *y) {
-  launch_matvec(P->d, P->S, P->opt, R, x, y, P->geom->ctx->stream);
+  launch_matvec(P->d, P->S, P->opt, R, x, y, P->stream);
 }
 
 // Complex Givens rotation [[c, s], [-conj(s), conj(c)]], c = conj(a)/den, s = conj(b)/den.
@@ -217,6 +222,187 @@ struct Col {
 };
 
 }  // namespace
+
+namespace igabem {
+
+// host-side plan of a problem: validation, set-up tables and the device memory it will hold
+igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
+  if (!geom || !opt) fail(IGABEM_EINVAL, "invalid problem arguments");
+  if (opt->precision != IGABEM_FP64 && opt->precision != IGABEM_MIXED_FP32)
+    fail(IGABEM_EINVAL, "unknown precision");
+  if (!(opt->eta_adm > 0)) fail(IGABEM_EINVAL, "eta_adm must be positive");
+  if (!(opt->kappa >= 0)) fail(IGABEM_EINVAL, "kappa must be >= 0");
+  auto *P = new igabem_problem();
+  P->geom = geom;
+  P->opt = *opt;
+  P->stream = geom->ctx->stream;
+  P->prof.on = opt->profile != 0;
+  P->t_plan = now_ms();
+  try {
+    HostSetup &S = P->S;
+    build_setup(geom->patches, *opt, S);
+    P->info.host_setup_ms = now_ms() - P->t_plan;
+    const int Q = S.q * S.q, nq = S.ng * S.ng;
+    size_t total = 0;
+    std::vector<int> dummy_tgt(S.near_src.size());
+    size_t nrule = S.r_id.w.size() + S.r_edge.w.size() + S.r_vert.w.size();
+    total += bytes_of(S.edeg) + bytes_of(S.eoff) + bytes_of(S.ebez) + bytes_of(S.corners);
+    size_t gst = (size_t)S.E * nq;
+    total += 13 * ((gst * sizeof(double) + 255) & ~size_t(255));
+    total += bytes_of(S.phi1) + bytes_of(S.dphi1) + bytes_of(S.ext1) + bytes_of(S.gx) + bytes_of(S.gw);
+    total += 3 * 256 + 5 * nrule * sizeof(double);
+    total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.sing) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) +
+             bytes_of(S.g2x_idx);
+    total += bytes_of(S.near_ptr) + bytes_of(S.near_src) + bytes_of(dummy_tgt);
+    total += bytes_of(S.cheb) + bytes_of(S.T1) + bytes_of(S.LG1);
+    for (int l = 0; l <= S.L; ++l) {
+      total += bytes_of(S.lev[l].far_ptr) + bytes_of(S.lev[l].far_src);
+      total += ((size_t)7 * S.lev[l].n * Q * sizeof(double) + 255) & ~size_t(255);
+      total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
+      total += bytes_of(S.lev[l].center);
+      total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
+    }
+    const bool mixed = opt->precision == IGABEM_MIXED_FP32;
+    size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
+    size_t blk_bytes = blk_entries * sizeof(double);
+    // mixed precision keeps the near-field blocks in FP32; the FP64 assembly buffer is temporary
+    total += mixed ? ((blk_entries * sizeof(float) + 255) & ~size_t(255)) : ((blk_bytes + 255) & ~size_t(255));
+    P->arena_bytes = total + 4096;
+    P->temp_bytes = mixed ? blk_bytes : 0;
+  } catch (...) {
+    delete P;
+    throw;
+  }
+  return P;
+}
+
+// device set-up of a planned problem on stream st: tables, near-field quadrature
+void problem_materialize(igabem_problem *P, cudaStream_t st) {
+  const igabem_options *opt = &P->opt;
+  P->stream = st;
+  HostSetup &S = P->S;
+  IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+  const int Q = S.q * S.q, nq = S.ng * S.ng;
+  const long nleaf = S.lev[S.L].n;
+  std::vector<int> near_tgt(S.near_src.size());
+  for (long t = 0; t < nleaf; ++t)
+    for (int k = S.near_ptr[t]; k < S.near_ptr[t + 1]; ++k) near_tgt[k] = (int)t;
+  std::vector<double> rules[3];
+  const Rule4 *R4[3] = {&S.r_id, &S.r_edge, &S.r_vert};
+  for (int k = 0; k < 3; ++k) {
+    const Rule4 &r = *R4[k];
+    for (const auto *v : {&r.x1, &r.x2, &r.y1, &r.y2, &r.w}) rules[k].insert(rules[k].end(), v->begin(), v->end());
+  }
+  const size_t gst = (size_t)S.E * nq;
+  const bool mixed = opt->precision == IGABEM_MIXED_FP32;
+  const size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
+  const size_t blk_bytes = blk_entries * sizeof(double);
+  P->arena.reserve(P->arena_bytes);
+  Arena &A = P->arena;
+  DeviceProblem &d = P->d;
+  d.prof = &P->prof;
+  d.edeg = upload(A, S.edeg, st);
+  d.eoff = upload(A, S.eoff, st);
+  d.ebez = upload(A, S.ebez, st);
+  d.corners = upload(A, S.corners, st);
+  d.gpx = A.get<double>(3 * gst);
+  d.gpn = A.get<double>(3 * gst);
+  d.gpa = A.get<double>(gst);
+  d.gfs = A.get<double>(3 * gst);
+  d.gft = A.get<double>(3 * gst);
+  d.phi1 = upload(A, S.phi1, st);
+  d.dphi1 = upload(A, S.dphi1, st);
+  d.ext1 = upload(A, S.ext1, st);
+  d.gx = upload(A, S.gx, st);
+  d.gw = upload(A, S.gw, st);
+  for (int k = 0; k < 3; ++k) {
+    d.rule[k] = upload(A, rules[k], st);
+    d.rule_n[k] = (int)R4[k]->w.size();
+  }
+  d.touch = upload(A, S.touch, st);
+  d.touch_blk = upload(A, S.touch_blk, st);
+  d.sing = upload(A, S.sing, st);
+  d.x2g = upload(A, S.x2g, st);
+  d.g2x_ptr = upload(A, S.g2x_ptr, st);
+  d.g2x_idx = upload(A, S.g2x_idx, st);
+  d.near_ptr = upload(A, S.near_ptr, st);
+  d.near_src = upload(A, S.near_src, st);
+  d.near_tgt = upload(A, near_tgt, st);
+  double *cheb = upload(A, S.cheb, st);
+  d.T1 = upload(A, S.T1, st);
+  d.LG1 = upload(A, S.LG1, st);
+  d.far_ptr.assign(S.L + 1, nullptr);
+  d.far_src.assign(S.L + 1, nullptr);
+  d.nodes.assign(S.L + 1, nullptr);
+  d.nodes32.assign(S.L + 1, nullptr);
+  d.centers.assign(S.L + 1, nullptr);
+  d.pairc.assign(S.L + 1, nullptr);
+  for (int l = 0; l <= S.L; ++l) {
+    d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
+    d.far_src[l] = upload(A, S.lev[l].far_src, st);
+    d.nodes[l] = A.get<double>((size_t)7 * S.lev[l].n * Q);
+    d.nodes32[l] = A.get<float>((size_t)7 * S.lev[l].n * Q);
+    d.centers[l] = upload(A, S.lev[l].center, st);
+    d.pairc[l] = A.get<float>(std::max<size_t>(S.lev[l].far_src.size(), 1) * 8);
+  }
+  double *blk_tmp = nullptr;
+  if (mixed) {
+    d.blk32 = A.get<float>(blk_entries);
+    IGA_CUDA(cudaMalloc(&blk_tmp, std::max<size_t>(blk_bytes, 256)));
+    d.blk = blk_tmp;
+  } else {
+    d.blk = A.get<double>(blk_entries);
+  }
+  IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
+  launch_gauss_geometry(d, S, st);
+  launch_node_geometry(d, S, cheb, st);
+  if (S.n_far > 0) {
+    Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
+    launch_pair_consts(d, S, opt->kappa, st);
+  }
+  launch_near_field(d, S, *opt, st);
+  if (mixed) {
+    {
+      Phase ph(&P->prof, IGABEM_PH_SETUP_NEAR, st);
+      launch_blocks_to_fp32(d.blk, d.blk32, blk_entries, st);
+    }
+    IGA_CUDA(cudaStreamSynchronize(st));
+    IGA_CUDA(cudaFree(blk_tmp));
+    d.blk = nullptr;
+  }
+  IGA_CUDA(cudaStreamSynchronize(st));
+  IGA_CUDA(cudaGetLastError());
+  P->prof.flush();
+  igabem_info &I = P->info;
+  I.n_dofs = S.N;
+  I.n_patch_dofs = S.NX;
+  I.n_elements = S.E;
+  long ncl = 0;
+  for (auto &lv : S.lev) ncl += lv.n;
+  I.n_clusters = ncl;
+  I.n_near_pairs = (long)S.near_src.size();
+  I.n_near_element_pairs = I.n_near_pairs << (4 * S.b);
+  I.n_touching_pairs = (long)S.touch.size() / 5;
+  I.n_far_pairs = S.n_far;
+  I.device_bytes = A.cap;
+  I.setup_ms = now_ms() - P->t_plan;
+}
+
+void problem_release(igabem_problem *P) {
+  {
+    std::lock_guard<std::mutex> lk(g_ext_mu);
+    auto it = g_ext.find(P);
+    if (it != g_ext.end()) {
+      it->second->work.arena.release();
+      delete it->second;
+      g_ext.erase(it);
+    }
+  }
+  P->arena.release();
+  delete P;
+}
+
+}  // namespace igabem
 
 extern "C" {
 
@@ -322,146 +508,12 @@ void igabem_geometry_destroy(igabem_geom *geom) { delete geom; }
 int igabem_problem_create(igabem_geom *geom, const igabem_options *opt, igabem_problem **out) {
   return guarded([&] {
     if (!geom || !opt || !out) fail(IGABEM_EINVAL, "invalid problem arguments");
-    if (opt->precision != IGABEM_FP64 && opt->precision != IGABEM_MIXED_FP32)
-      fail(IGABEM_EINVAL, "unknown precision");
-    if (!(opt->eta_adm > 0)) fail(IGABEM_EINVAL, "eta_adm must be positive");
-    if (!(opt->kappa >= 0)) fail(IGABEM_EINVAL, "kappa must be >= 0");
-    double t0 = now_ms();
     IGA_CUDA(cudaSetDevice(geom->ctx->device));
-    auto *P = new igabem_problem();
-    P->geom = geom;
-    P->opt = *opt;
-    P->prof.on = opt->profile != 0;
+    igabem_problem *P = problem_plan(geom, opt);
     try {
-      HostSetup &S = P->S;
-      double th = now_ms();
-      build_setup(geom->patches, *opt, S);
-      P->info.host_setup_ms = now_ms() - th;
-      cudaStream_t st = geom->ctx->stream;
-      const int Q = S.q * S.q, nq = S.ng * S.ng;
-      const long nleaf = S.lev[S.L].n;
-      std::vector<int> near_tgt(S.near_src.size());
-      for (long t = 0; t < nleaf; ++t)
-        for (int k = S.near_ptr[t]; k < S.near_ptr[t + 1]; ++k) near_tgt[k] = (int)t;
-      std::vector<double> rules[3];
-      const Rule4 *R4[3] = {&S.r_id, &S.r_edge, &S.r_vert};
-      for (int k = 0; k < 3; ++k) {
-        const Rule4 &r = *R4[k];
-        for (const auto *v : {&r.x1, &r.x2, &r.y1, &r.y2, &r.w}) rules[k].insert(rules[k].end(), v->begin(), v->end());
-      }
-      // --- size the arena ---
-      size_t total = 0;
-      total += bytes_of(S.edeg) + bytes_of(S.eoff) + bytes_of(S.ebez) + bytes_of(S.corners);
-      size_t gst = (size_t)S.E * nq;
-      total += 13 * ((gst * sizeof(double) + 255) & ~size_t(255));
-      total += bytes_of(S.phi1) + bytes_of(S.dphi1) + bytes_of(S.ext1) + bytes_of(S.gx) + bytes_of(S.gw);
-      for (int k = 0; k < 3; ++k) total += bytes_of(rules[k]);
-      total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) + bytes_of(S.g2x_idx);
-      total += bytes_of(S.near_ptr) + bytes_of(S.near_src) + bytes_of(near_tgt);
-      total += bytes_of(S.cheb) + bytes_of(S.T1) + bytes_of(S.LG1);
-      for (int l = 0; l <= S.L; ++l) {
-        total += bytes_of(S.lev[l].far_ptr) + bytes_of(S.lev[l].far_src);
-        total += ((size_t)7 * S.lev[l].n * Q * sizeof(double) + 255) & ~size_t(255);
-        total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
-        total += bytes_of(S.lev[l].center);
-        total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
-      }
-      const bool mixed = opt->precision == IGABEM_MIXED_FP32;
-      size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
-      size_t blk_bytes = blk_entries * sizeof(double);
-      // mixed precision keeps the near-field blocks in FP32; the FP64 assembly buffer is temporary
-      total += mixed ? ((blk_entries * sizeof(float) + 255) & ~size_t(255)) : ((blk_bytes + 255) & ~size_t(255));
-      P->arena.reserve(total);
-      Arena &A = P->arena;
-      DeviceProblem &d = P->d;
-      d.prof = &P->prof;
-      d.edeg = upload(A, S.edeg, st);
-      d.eoff = upload(A, S.eoff, st);
-      d.ebez = upload(A, S.ebez, st);
-      d.corners = upload(A, S.corners, st);
-      d.gpx = A.get<double>(3 * gst);
-      d.gpn = A.get<double>(3 * gst);
-      d.gpa = A.get<double>(gst);
-      d.gfs = A.get<double>(3 * gst);
-      d.gft = A.get<double>(3 * gst);
-      d.phi1 = upload(A, S.phi1, st);
-      d.dphi1 = upload(A, S.dphi1, st);
-      d.ext1 = upload(A, S.ext1, st);
-      d.gx = upload(A, S.gx, st);
-      d.gw = upload(A, S.gw, st);
-      for (int k = 0; k < 3; ++k) {
-        d.rule[k] = upload(A, rules[k], st);
-        d.rule_n[k] = (int)R4[k]->w.size();
-      }
-      d.touch = upload(A, S.touch, st);
-      d.touch_blk = upload(A, S.touch_blk, st);
-      d.x2g = upload(A, S.x2g, st);
-      d.g2x_ptr = upload(A, S.g2x_ptr, st);
-      d.g2x_idx = upload(A, S.g2x_idx, st);
-      d.near_ptr = upload(A, S.near_ptr, st);
-      d.near_src = upload(A, S.near_src, st);
-      d.near_tgt = upload(A, near_tgt, st);
-      double *cheb = upload(A, S.cheb, st);
-      d.T1 = upload(A, S.T1, st);
-      d.LG1 = upload(A, S.LG1, st);
-      d.far_ptr.assign(S.L + 1, nullptr);
-      d.far_src.assign(S.L + 1, nullptr);
-      d.nodes.assign(S.L + 1, nullptr);
-      d.nodes32.assign(S.L + 1, nullptr);
-      d.centers.assign(S.L + 1, nullptr);
-      d.pairc.assign(S.L + 1, nullptr);
-      for (int l = 0; l <= S.L; ++l) {
-        d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
-        d.far_src[l] = upload(A, S.lev[l].far_src, st);
-        d.nodes[l] = A.get<double>((size_t)7 * S.lev[l].n * Q);
-        d.nodes32[l] = A.get<float>((size_t)7 * S.lev[l].n * Q);
-        d.centers[l] = upload(A, S.lev[l].center, st);
-        d.pairc[l] = A.get<float>(std::max<size_t>(S.lev[l].far_src.size(), 1) * 8);
-      }
-      double *blk_tmp = nullptr;
-      if (mixed) {
-        d.blk32 = A.get<float>(blk_entries);
-        IGA_CUDA(cudaMalloc(&blk_tmp, std::max<size_t>(blk_bytes, 256)));
-        d.blk = blk_tmp;
-      } else {
-        d.blk = A.get<double>(blk_entries);
-      }
-      IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
-      launch_gauss_geometry(d, S, st);
-      launch_node_geometry(d, S, cheb, st);
-      if (S.n_far > 0) {
-        Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
-        launch_pair_consts(d, S, opt->kappa, st);
-      }
-      launch_near_field(d, S, *opt, st);
-      if (mixed) {
-        {
-          Phase ph(&P->prof, IGABEM_PH_SETUP_NEAR, st);
-          launch_blocks_to_fp32(d.blk, d.blk32, blk_entries, st);
-        }
-        IGA_CUDA(cudaStreamSynchronize(st));
-        IGA_CUDA(cudaFree(blk_tmp));
-        d.blk = nullptr;
-      }
-      IGA_CUDA(cudaStreamSynchronize(st));
-      IGA_CUDA(cudaGetLastError());
-      P->prof.flush();
-      igabem_info &I = P->info;
-      I.n_dofs = S.N;
-      I.n_patch_dofs = S.NX;
-      I.n_elements = S.E;
-      long ncl = 0;
-      for (auto &lv : S.lev) ncl += lv.n;
-      I.n_clusters = ncl;
-      I.n_near_pairs = (long)S.near_src.size();
-      I.n_near_element_pairs = I.n_near_pairs << (4 * S.b);
-      I.n_touching_pairs = (long)S.touch.size() / 5;
-      I.n_far_pairs = S.n_far;
-      I.device_bytes = A.cap;
-      I.setup_ms = now_ms() - t0;
+      problem_materialize(P, geom->ctx->stream);
     } catch (...) {
-      P->arena.release();
-      delete P;
+      problem_release(P);
       throw;
     }
     *out = P;
@@ -479,18 +531,7 @@ int igabem_problem_info(const igabem_problem *prob, igabem_info *out) {
 }
 
 void igabem_problem_destroy(igabem_problem *prob) {
-  if (!prob) return;
-  {
-    std::lock_guard<std::mutex> lk(g_ext_mu);
-    auto it = g_ext.find(prob);
-    if (it != g_ext.end()) {
-      it->second->work.arena.release();
-      delete it->second;
-      g_ext.erase(it);
-    }
-  }
-  prob->arena.release();
-  delete prob;
+  if (prob) problem_release(prob);
 }
 
 int igabem_profile_enable(igabem_problem *P, int on) {
@@ -519,7 +560,7 @@ int igabem_rhs(igabem_problem *P, int n_rhs, const double *dirs, void *b) {
     if (!P || !dirs || !b || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid rhs arguments");
     IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
     ensure_work(P, n_rhs, false);
-    cudaStream_t st = P->geom->ctx->stream;
+    cudaStream_t st = P->stream;
     ProblemWork &W = ext(P)->work;
     double *ddir = W.red;  // 3 n_rhs doubles fit in the reduction scratch
     IGA_CUDA(cudaMemcpyAsync(ddir, dirs, 3 * sizeof(double) * n_rhs, cudaMemcpyHostToDevice, st));
@@ -538,7 +579,7 @@ int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
     if (!P || !x || !y || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid matvec arguments");
     IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
     ensure_work(P, n_rhs, false);
-    cudaStream_t st = P->geom->ctx->stream;
+    cudaStream_t st = P->stream;
     ProblemWork &W = ext(P)->work;
     size_t bytes = P->S.N * n_rhs * 2 * sizeof(double);
     bool dx = is_device_ptr(x), dy = is_device_ptr(y);
@@ -559,7 +600,7 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     double t0 = now_ms();
     IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
     ensure_work(P, n_rhs, true);
-    cudaStream_t st = P->geom->ctx->stream;
+    cudaStream_t st = P->stream;
     ProblemWork &W = ext(P)->work;
     const HostSetup &S = P->S;
     const long N = S.N;
@@ -719,7 +760,7 @@ int igabem_farfield(igabem_problem *P, int n_rhs, const void *density, int n_dir
     if (!P || !density || !xhat || !uinf || n_rhs <= 0 || n_dir <= 0) fail(IGABEM_EINVAL, "invalid far-field arguments");
     IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
     ensure_work(P, n_rhs, false);
-    cudaStream_t st = P->geom->ctx->stream;
+    cudaStream_t st = P->stream;
     ProblemWork &W = ext(P)->work;
     size_t db = P->S.N * n_rhs * 2 * sizeof(double);
     bool dd = is_device_ptr(density), du = is_device_ptr(uinf);

@@ -581,6 +581,20 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     if (it == b1 || *it != tf) fail(IGABEM_EINVAL, "touching pair outside the near field");
     S.touch_blk[i] = int(it - S.near_src.begin());
   }
+  // unordered work list: identical pairs, and (e, f) with e < f for the others (the block of (f, e)
+  // comes from the same quadrature points with the roles of x and y exchanged)
+  S.sing.clear();
+  std::unordered_map<long long, int> blk_of;
+  for (int i = 0; i < npt; ++i) blk_of[(long long)S.touch[5 * i] * S.E + S.touch[5 * i + 1]] = S.touch_blk[i];
+  for (int i = 0; i < npt; ++i) {
+    const int *t = &S.touch[5 * i];
+    if (t[2] == 0) {
+      S.sing.insert(S.sing.end(), {t[0], t[1], 0, 0, 0, S.touch_blk[i], -1});
+    } else if (t[0] < t[1]) {
+      int back = blk_of.at((long long)t[1] * S.E + t[0]);
+      S.sing.insert(S.sing.end(), {t[0], t[1], t[2], t[3], t[4], S.touch_blk[i], back});
+    }
+  }
 
   // --- interpolation tables ---
   S.cheb.resize(S.q);

@@ -29,6 +29,16 @@ void set_error(const std::string &msg);
       ::igabem::fail(IGABEM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
   } while (0)
 
+// Opt-in shared memory: kernels are set once to the device's largest opt-in size (a per-kernel value,
+// so concurrent host threads never lower it under each other's launches); the launch's own size must
+// not exceed it.
+int max_optin_smem();
+template <class K> cudaError_t set_max_dynamic_smem(K kernel, size_t bytes) {
+  const int mx = max_optin_smem();
+  if (bytes > (size_t)mx) fail(IGABEM_EINVAL, "kernel needs more shared memory than the device offers");
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 // ----------------------------------------------------------------------------------------------
 // geometry input (host copy)
 
@@ -93,6 +103,9 @@ struct HostSetup {
   std::vector<TreeLevel> lev;
   std::vector<int> near_ptr, near_src; // near leaf pairs, CSR by target leaf
   std::vector<int> touch_blk;          // per touching pair: index of its near leaf pair
+  // work list of the singular quadrature: each unordered touching pair once,
+  // (e, f, kind, Te, Tf, block of (e,f), block of (f,e) or -1 for identical pairs)
+  std::vector<int> sing;
   long n_far = 0;
   // interpolation tables
   std::vector<double> cheb;            // normalised Chebyshev nodes t_a on [0,1]
@@ -167,7 +180,7 @@ struct DeviceProblem {
   double *rule[3];                          // singular rules (5 arrays each, SoA)
   int rule_n[3];
   double *corners;
-  int *touch, *touch_blk;
+  int *touch, *touch_blk, *sing;
   int *x2g, *g2x_ptr, *g2x_idx;
   // tree
   int *near_ptr, *near_src, *near_tgt;
@@ -192,9 +205,22 @@ struct DeviceProblem {
 
 }  // namespace igabem
 
+struct igabem_problem;
+namespace igabem {
+igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt);
+void problem_materialize(igabem_problem *P, cudaStream_t st);
+void problem_release(igabem_problem *P);
+size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m);
+double now_ms();
+}  // namespace igabem
+
 struct igabem_problem {
   igabem::Profiler prof;
   igabem_geom *geom = nullptr;
+  cudaStream_t stream = nullptr;   // the stream all of the problem's work is issued on
+  size_t arena_bytes = 0;          // device memory of the set-up arena
+  size_t temp_bytes = 0;           // transient device memory during set-up
+  double t_plan = 0;
   igabem_options opt{};
   igabem::HostSetup S;
   igabem::Arena arena;

@@ -359,7 +359,7 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
       int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
       int ntypes = D.hard ? 2 : 1;
       size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
-      IGA_CUDA(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IGA_CUDA(set_max_dynamic_smem(k_m2l, smem));
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       for (int l = S.lmin; l <= S.L; ++l) {
         dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);

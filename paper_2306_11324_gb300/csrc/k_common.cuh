@@ -87,6 +87,40 @@ __device__ inline void bez_eval(const double *__restrict__ H, int p1, int p2, do
   }
 }
 
+// The same evaluation done separably (contract the second parameter first); H may point to shared
+// memory.
+__device__ inline void bez_eval_sep(const double *__restrict__ H, int p1, int p2, double u, double v,
+                                    double F[3], double Fu[3], double Fv[3]) {
+  double B1[8], dB1[8], B2[8], dB2[8];
+  bernstein_all(p1, u, B1, dB1);
+  bernstein_all(p2, v, B2, dB2);
+  double h[4] = {0, 0, 0, 0}, hu[4] = {0, 0, 0, 0}, hv[4] = {0, 0, 0, 0};
+  for (int i = 0; i <= p1; ++i) {
+    double r[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0};
+    const double *c = H + i * (p2 + 1) * 4;
+    for (int j = 0; j <= p2; ++j) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        r[k] += B2[j] * c[4 * j + k];
+        rv[k] += dB2[j] * c[4 * j + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      h[k] += B1[i] * r[k];
+      hu[k] += dB1[i] * r[k];
+      hv[k] += B1[i] * rv[k];
+    }
+  }
+  double iw = 1.0 / h[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    F[k] = h[k] * iw;
+    Fu[k] = (hu[k] - F[k] * hu[3]) * iw;
+    Fv[k] = (hv[k] - F[k] * hv[3]) * iw;
+  }
+}
+
 __device__ inline void cross3(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];

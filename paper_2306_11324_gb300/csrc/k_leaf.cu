@@ -363,7 +363,7 @@ void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options
   const int nleaf = S.lev[S.L].n;
   int Rc = column_chunk(p2m_smem, S, A.C, R);
   size_t smem = p2m_smem(S, A.C, Rc);
-  IGA_CUDA(cudaFuncSetAttribute(k_p2m2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  IGA_CUDA(set_max_dynamic_smem(k_p2m2, smem));
   for (int r0 = 0; r0 < R; r0 += Rc) {
     k_p2m2<<<nleaf, 256, smem, st>>>(A, reinterpret_cast<const double2 *>(d.xX),
                                      reinterpret_cast<double2 *>(d.xhat[S.L]), r0, std::min(Rc, R - r0));
@@ -377,7 +377,7 @@ void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options
   const int nleaf = S.lev[S.L].n;
   int Rc = column_chunk(l2p_smem, S, A.C, R);
   size_t smem = l2p_smem(S, A.C, Rc);
-  IGA_CUDA(cudaFuncSetAttribute(k_l2p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  IGA_CUDA(set_max_dynamic_smem(k_l2p2, smem));
   for (int r0 = 0; r0 < R; r0 += Rc) {
     k_l2p2<<<nleaf, 256, smem, st>>>(A, reinterpret_cast<const double2 *>(d.yhat[S.L]),
                                      reinterpret_cast<double2 *>(d.yleaf), r0, std::min(Rc, R - r0));

@@ -382,7 +382,7 @@ void launch_rows(const M2LArgs &A, int nblocks, cudaStream_t st) {
   size_t smem = std::max((size_t)M2L_WARPS * 64 * sizeof(SrcNode<T>) + (size_t)M2L_WARPS * 64 * NCR * sizeof(C2<T>),
                          (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
   auto kfn = k_m2l_rows<T, NCR, HARD>;
-  IGA_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  IGA_CUDA(set_max_dynamic_smem(kfn, smem));
   for (int cr0 = 0; cr0 < A.CR; cr0 += NCR) {
     kfn<<<nblocks, 32 * M2L_WARPS, smem, st>>>(A, cr0);
     note_launch();
@@ -452,10 +452,10 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     size_t smem = (size_t)A.Q * A.Q * 2 * tsz + (size_t)A.Q * Wc * 2 * tsz + (size_t)A.Q * 16 * tsz;
     dim3 grid(nblocks, A.CR / Wc);
     if (fp32) {
-      IGA_CUDA(cudaFuncSetAttribute(k_m2l_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IGA_CUDA(set_max_dynamic_smem(k_m2l_gemm<float>, smem));
       k_m2l_gemm<float><<<grid, 256, smem, st>>>(A, Wc);
     } else {
-      IGA_CUDA(cudaFuncSetAttribute(k_m2l_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IGA_CUDA(set_max_dynamic_smem(k_m2l_gemm<double>, smem));
       k_m2l_gemm<double><<<grid, 256, smem, st>>>(A, Wc);
     }
     note_launch();

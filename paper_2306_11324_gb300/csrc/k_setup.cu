@@ -97,6 +97,35 @@ __device__ inline PairKernel cfie_kernel(bool hard, double kappa, double eta, co
   return pk;
 }
 
+// Both orientations of a touching pair from one evaluation of G: the kernel at (x, y) and the ks part
+// at (y, x) (gc is symmetric).
+__device__ inline void cfie_kernel_both(bool hard, double kappa, double eta, const double *x, const double *nx,
+                                        double ax, const double *y, const double *ny, double ay,
+                                        PairKernel &xy, double2 &ks_yx) {
+  double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+  double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  KernelVals kv = helmholtz(kappa, r);
+  const double dnx = d[0] * nx[0] + d[1] * nx[1] + d[2] * nx[2];   // (x-y).n~x
+  const double dny = d[0] * ny[0] + d[1] * ny[1] + d[2] * ny[2];   // (x-y).n~y
+  if (!hard) {
+    double2 v = cscale(kv.G, ax * ay);
+    double2 kp = cscale(kv.dGr, ay * dnx);
+    xy.ks = cmk(kp.x + eta * v.y, kp.y - eta * v.x);
+    xy.gc = cmk(0.0, 0.0);
+    double2 kq = cscale(kv.dGr, -ax * dny);                        // a_x G'/r (y-x).n~y
+    ks_yx = cmk(kq.x + eta * v.y, kq.y - eta * v.x);
+  } else {
+    double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+    double f = eta * kappa * kappa * nn;
+    double2 g = kv.G;
+    double2 kk = cscale(kv.dGr, -ax * dny);                        // a_x G'/r (y-x).n~y
+    xy.ks = cmk(-kk.x - f * g.y, -kk.y + f * g.x);
+    xy.gc = cmk(eta * g.y, -eta * g.x);
+    double2 kk2 = cscale(kv.dGr, ay * dnx);                        // a_y G'/r (x-y).n~x
+    ks_yx = cmk(-kk2.x - f * g.y, -kk2.y + f * g.x);
+  }
+}
+
 template <class T> struct PK {
   T ksx, ksy, gcx, gcy;
 };
@@ -333,114 +362,131 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
 
 struct SingArgs {
   NearArgs A;
-  const int *touch, *touch_blk;
+  const int *sing;        // 7 ints per unordered touching pair
   const double *rule[3];  // per kind: x1, x2, y1, y2, w arrays of n points, concatenated
   int rule_n[3];
 };
 
-// basis values (and d/ds, d/dt) of the nloc local functions at local point (u, v) of element
-// column (ix, iy), by Bernstein extraction
-__device__ inline void basis_at(const NearArgs &A, int ix, int iy, double u, double v, double *val,
-                                double *ds, double *dt) {
-  int p = A.p, p1 = p + 1;
+// values of the nloc local functions at local point (u, v) of element column (ix, iy) (Bernstein
+// extraction) into val; with curl != nullptr also c_k = d_s psi_k d_t F - d_t psi_k d_s F
+__device__ inline void basis_curl_at(const NearArgs &A, int ix, int iy, double u, double v, const double *fs,
+                                     const double *ft, double *val, double *curl) {
+  const int p = A.p, p1 = p + 1;
   double Bu[8], dBu[8], Bv[8], dBv[8];
-  bernstein_all(p, u, Bu, dBu);
-  bernstein_all(p, v, Bv, dBv);
+  bernstein_all(p, u, Bu, curl ? dBu : nullptr);
+  bernstein_all(p, v, Bv, curl ? dBv : nullptr);
   double fu[8], dfu[8], fv[8], dfv[8];
   for (int a = 0; a <= p; ++a) {
     double s0 = 0, s1 = 0, t0 = 0, t1 = 0;
     for (int c = 0; c <= p; ++c) {
       double ea = A.ext1[(ix * p1 + a) * p1 + c], eb = A.ext1[(iy * p1 + a) * p1 + c];
-      s0 += ea * Bu[c]; s1 += ea * dBu[c];
-      t0 += eb * Bv[c]; t1 += eb * dBv[c];
+      s0 += ea * Bu[c];
+      t0 += eb * Bv[c];
+      if (curl) {
+        s1 += ea * dBu[c];
+        t1 += eb * dBv[c];
+      }
     }
-    fu[a] = s0; dfu[a] = s1 * A.n1; fv[a] = t0; dfv[a] = t1 * A.n1;
+    fu[a] = s0; fv[a] = t0; dfu[a] = s1 * A.n1; dfv[a] = t1 * A.n1;
   }
   for (int a = 0; a <= p; ++a)
     for (int b = 0; b <= p; ++b) {
-      val[a * p1 + b] = fu[a] * fv[b];
-      if (ds) {
-        ds[a * p1 + b] = dfu[a] * fv[b];
-        dt[a * p1 + b] = fu[a] * dfv[b];
+      const int k = a * p1 + b;
+      val[k] = fu[a] * fv[b];
+      if (curl) {
+        const double ds = dfu[a] * fv[b], dt = fu[a] * dfv[b];
+        for (int d = 0; d < 3; ++d) curl[k * 3 + d] = ds * ft[d] - dt * fs[d];
       }
     }
 }
 
-constexpr int SING_CHUNK = 64;
-constexpr int SING_MAXACC = 20;
+constexpr int SING_CHUNK = 128;  // one point per thread
+constexpr int SING_MAXACC = 19;  // (p+1)^4 / 128 rounded up for p <= 6
 
+// One block per unordered touching pair.  Points of the regularising rule of the pair's kind, mapped
+// by the canonical square symmetries; for edge and vertex pairs the same points also give the block
+// of (f, e) with the roles of x and y exchanged (the rules are symmetric under that exchange).
+template <int NSLOT>
 __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;
   extern __shared__ double smd[];
   const int nloc = A.nloc, p1 = A.p + 1;
-  // shared: ks[C], gc[C] (complex), phx[C][nloc], phy[C][nloc], cx[C][nloc][3], cy[C][nloc][3]
-  double2 *ks = reinterpret_cast<double2 *>(smd), *gc = ks + SING_CHUNK;
+  // shared: ks[C], kb[C], gc[C] (complex), phx[C][nloc], phy[C][nloc], cx[C][nloc][3], cy[C][nloc][3]
+  double2 *ks = reinterpret_cast<double2 *>(smd), *kb = ks + SING_CHUNK, *gc = kb + SING_CHUNK;
   double *phx = reinterpret_cast<double *>(gc + SING_CHUNK), *phy = phx + SING_CHUNK * nloc;
   double *cxs = phy + SING_CHUNK * nloc, *cys = cxs + 3 * SING_CHUNK * nloc;
-  const int pid = blockIdx.x;
-  const int e = S.touch[5 * pid], f = S.touch[5 * pid + 1], kind = S.touch[5 * pid + 2];
-  const int te = S.touch[5 * pid + 3], tf = S.touch[5 * pid + 4];
+  double *net_e = cys + 3 * SING_CHUNK * nloc, *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
+  const int *W = S.sing + 7 * blockIdx.x;
+  const int e = W[0], f = W[1], kind = W[2], te = W[3], tf = W[4], blk_ef = W[5], blk_fe = W[6];
+  const bool both = blk_fe >= 0;
   const int ri = kind == 0 ? 0 : (kind == 2 ? 1 : 2);
   const int npt = S.rule_n[ri];
   const double *R = S.rule[ri];
   const int n1 = A.n1;
   const int ixe = (e / n1) % n1, iye = e % n1, ixf = (f / n1) % n1, iyf = f % n1;
   const double h4 = A.h * A.h * A.h * A.h;
-  double2 acc[SING_MAXACC];
-  for (int i = 0; i < SING_MAXACC; ++i) acc[i] = cmk(0, 0);
+  double2 acc[NSLOT], accb[NSLOT];
+#pragma unroll
+  for (int i = 0; i < NSLOT; ++i) acc[i] = accb[i] = cmk(0, 0);
+  const int pe1 = A.edeg[2 * e], pe2 = A.edeg[2 * e + 1], pf1 = A.edeg[2 * f], pf2 = A.edeg[2 * f + 1];
+  for (int i = threadIdx.x; i < 4 * (pe1 + 1) * (pe2 + 1); i += blockDim.x) net_e[i] = A.ebez[A.eoff[e] + i];
+  for (int i = threadIdx.x; i < 4 * (pf1 + 1) * (pf2 + 1); i += blockDim.x) net_f[i] = A.ebez[A.eoff[f] + i];
+  __syncthreads();
   for (int c0 = 0; c0 < npt; c0 += SING_CHUNK) {
-    int cn = min(SING_CHUNK, npt - c0);
+    const int cn = min(SING_CHUNK, npt - c0);
     for (int t = threadIdx.x; t < cn; t += blockDim.x) {
-      int ip = c0 + t;
+      const int ip = c0 + t;
       double ue, ve, uf, vf;
       d4_apply(te, R[ip], R[npt + ip], ue, ve);
       d4_apply(tf, R[2 * npt + ip], R[3 * npt + ip], uf, vf);
-      double w = R[4 * npt + ip] * h4;
+      const double w = R[4 * npt + ip] * h4;
       double X[3], Xu[3], Xv[3], Y[3], Yu[3], Yv[3], fs[3], ft[3], gs[3], gt[3], nx[3], ny[3];
-      bez_eval(A.ebez + A.eoff[e], A.edeg[2 * e], A.edeg[2 * e + 1], ue, ve, X, Xu, Xv);
-      bez_eval(A.ebez + A.eoff[f], A.edeg[2 * f], A.edeg[2 * f + 1], uf, vf, Y, Yu, Yv);
+      bez_eval_sep(net_e, pe1, pe2, ue, ve, X, Xu, Xv);
+      bez_eval_sep(net_f, pf1, pf2, uf, vf, Y, Yu, Yv);
       for (int k = 0; k < 3; ++k) {
         fs[k] = Xu[k] * n1; ft[k] = Xv[k] * n1; gs[k] = Yu[k] * n1; gt[k] = Yv[k] * n1;
       }
       cross3(fs, ft, nx);
       cross3(gs, gt, ny);
-      double ax = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
-      double ay = sqrt(ny[0] * ny[0] + ny[1] * ny[1] + ny[2] * ny[2]);
-      PairKernel pk = cfie_kernel(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay);
+      const double ax = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
+      const double ay = sqrt(ny[0] * ny[0] + ny[1] * ny[1] + ny[2] * ny[2]);
+      PairKernel pk;
+      double2 kyx;
+      cfie_kernel_both(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay, pk, kyx);
       ks[t] = cscale(pk.ks, w);
-      gc[t] = cscale(pk.gc, w);
-      double dsx[49], dtx[49], dsy[49], dty[49];
-      basis_at(A, ixe, iye, ue, ve, phx + t * nloc, dsx, dtx);
-      basis_at(A, ixf, iyf, uf, vf, phy + t * nloc, dsy, dty);
-      if (A.hard) {
-        for (int k = 0; k < nloc; ++k)
-          for (int d = 0; d < 3; ++d) {
-            cxs[(t * nloc + k) * 3 + d] = dsx[k] * ft[d] - dtx[k] * fs[d];
-            cys[(t * nloc + k) * 3 + d] = dsy[k] * gt[d] - dty[k] * gs[d];
-          }
-      }
+      gc[t] = cscale(pk.gc, w);  // gc(y, x) = gc(x, y)
+      kb[t] = cscale(kyx, w);
+      basis_curl_at(A, ixe, iye, ue, ve, fs, ft, phx + t * nloc, A.hard ? cxs + t * nloc * 3 : nullptr);
+      basis_curl_at(A, ixf, iyf, uf, vf, gs, gt, phy + t * nloc, A.hard ? cys + t * nloc * 3 : nullptr);
     }
     __syncthreads();
-    int slot = 0;
-    for (int i = threadIdx.x; i < nloc * nloc; i += blockDim.x, ++slot) {
-      int k = i / nloc, l = i % nloc;
-      double2 a = acc[slot];
+#pragma unroll
+    for (int slot = 0; slot < NSLOT; ++slot) {
+      const int i = threadIdx.x + slot * blockDim.x;
+      if (i >= nloc * nloc) break;
+      const int k = i / nloc, l = i % nloc;
+      double2 a = acc[slot], b = accb[slot];
       for (int t = 0; t < cn; ++t) {
-        a = cadd(a, cscale(ks[t], phx[t * nloc + k] * phy[t * nloc + l]));
+        const double P = phx[t * nloc + k] * phy[t * nloc + l];
+        double2 g = cmk(0, 0);
         if (A.hard) {
           const double *ck = cxs + (t * nloc + k) * 3, *cl = cys + (t * nloc + l) * 3;
-          a = cadd(a, cscale(gc[t], ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2]));
+          g = cscale(gc[t], ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2]);
         }
+        a = cadd(a, cadd(cscale(ks[t], P), g));
+        if (both) b = cadd(b, cadd(cscale(kb[t], P), g));
       }
       acc[slot] = a;
+      accb[slot] = b;
     }
     __syncthreads();
   }
-  double2 *B = A.blk + (size_t)S.touch_blk[pid] * A.nL * A.nL;
   const int nq = A.ng * A.ng;
-  int slot = 0;
-  for (int i = threadIdx.x; i < nloc * nloc; i += blockDim.x, ++slot) {
-    int k = i / nloc, l = i % nloc;
+#pragma unroll
+  for (int slot = 0; slot < NSLOT; ++slot) {
+    const int i = threadIdx.x + slot * blockDim.x;
+    if (i >= nloc * nloc) break;
+    const int k = i / nloc, l = i % nloc;
     double2 a = acc[slot];
     if (kind == 0) {  // + 1/2 M_kl = 1/2 sum_q w_q h^2 a_q psi_k psi_l
       double m = 0;
@@ -452,8 +498,10 @@ __global__ void k_near_singular(SingArgs S) {
       }
       a.x += 0.5 * m * A.h * A.h;
     }
-    block_add(B, A.nL, leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1),
-              leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1), a);
+    const int re = leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1);
+    const int cf = leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1);
+    block_add(A.blk + (size_t)blk_ef * A.nL * A.nL, A.nL, re, cf, a);
+    if (both) block_add(A.blk + (size_t)blk_fe * A.nL * A.nL, A.nL, cf, re, accb[slot]);
   }
 }
 
@@ -511,10 +559,10 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
     while (warps > 1 && per * warps + (smem_block ? bsm : 0) > 200 * 1024) warps /= 2;
     size_t smem = per * warps + (smem_block ? bsm : 0);
     if (f32) {
-      IGA_CUDA(cudaFuncSetAttribute(k_near_regular_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IGA_CUDA(set_max_dynamic_smem(k_near_regular_t<float>, smem));
       k_near_regular_t<float><<<nblk, 32 * warps, smem, st>>>(A, smem_block);
     } else {
-      IGA_CUDA(cudaFuncSetAttribute(k_near_regular_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IGA_CUDA(set_max_dynamic_smem(k_near_regular_t<double>, smem));
       k_near_regular_t<double><<<nblk, 32 * warps, smem, st>>>(A, smem_block);
     }
     note_launch();
@@ -522,17 +570,24 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   }
   SingArgs SA;
   SA.A = A;
-  SA.touch = d.touch;
-  SA.touch_blk = d.touch_blk;
+  SA.sing = d.sing;
   for (int k = 0; k < 3; ++k) {
     SA.rule[k] = d.rule[k];
     SA.rule_n[k] = d.rule_n[k];
   }
-  int npt = (int)S.touch.size() / 5;
+  const int nsing = (int)S.sing.size() / 7;
   if (S.nloc * S.nloc > SING_MAXACC * 128) fail(IGABEM_EINVAL, "degree_p too large for the singular kernel");
-  size_t smem = (size_t)SING_CHUNK * (4 + 8 * S.nloc) * sizeof(double);
-  IGA_CUDA(cudaFuncSetAttribute(k_near_singular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_near_singular<<<npt, 128, smem, st>>>(SA);
+  const size_t smem = ((size_t)SING_CHUNK * (6 + 8 * S.nloc) + 8 * 49) * sizeof(double);
+  const int nslot = (S.nloc * S.nloc + 127) / 128;
+  auto go = [&](auto kfn) {
+    IGA_CUDA(set_max_dynamic_smem(kfn, smem));
+    kfn<<<nsing, 128, smem, st>>>(SA);
+  };
+  if (nslot <= 1) go(k_near_singular<1>);
+  else if (nslot <= 2) go(k_near_singular<2>);
+  else if (nslot <= 5) go(k_near_singular<5>);
+  else if (nslot <= 11) go(k_near_singular<11>);
+  else go(k_near_singular<SING_MAXACC>);
   note_launch();
   IGA_CUDA(cudaGetLastError());
 }

@@ -82,6 +82,19 @@ Phase::~Phase() {
   t_phase = prev_ph_;
 }
 
+int max_optin_smem() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0, x = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+      v = x;
+    else
+      v = 48 * 1024;
+  }
+  return v;
+}
+
 void note_launch() {
   if (t_prof) {
     t_prof->launches++;

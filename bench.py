@@ -32,7 +32,17 @@ WORKLOADS = {
     # the mixed form's GMRES stops at its FP32 rounding floor
     "sphere_soft_6x32x32_p2_k8": dict(geometry="sphere", level_m=5, degree_p=2, kappa=8.0, bc=0,
                                       cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
-                                      tol={"fp64": 1e-6, "mixed": 1e-6}, n_dir=100),
+                                      tol={"fp64": 1e-6, "mixed": 1e-6}, n_dir=100, n_rhs=1, kappa_cap=0.0,
+                                      restart=30, precond={"fp64": 0, "mixed": 1}),
+    # sound-hard deformed sphere (amplitude 0.15, seed 1), 64 x 64 elements per patch, kappa = 20,
+    # 64 incident directions on a Fibonacci sphere solved as one multi-RHS request; admissibility capped
+    # at kappa * diameter <= 6 (FMM truncation ~1e-5 against the dense matrix at q = 7)
+    # GMRES(30) stagnates on this sound-hard system (the hypersingular part is unbounded and kappa is
+    # large): restart 300.
+    "deformed_hard_6x64x64_p2_k20_64dirs": dict(geometry="deformed", level_m=6, degree_p=2, kappa=20.0, bc=1,
+                                                cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
+                                                tol={"fp64": 1e-5, "mixed": 1e-5}, n_dir=100, n_rhs=64,
+                                                kappa_cap=6.0, restart=300, precond={"fp64": 0, "mixed": 0}),
 }
 DEFAULT = "sphere_soft_6x32x32_p2_k8"
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # kernel sample arithmetic, see the design doc
@@ -47,9 +57,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["serving_stream"])
+    ap.add_argument("--requests", type=int, default=64, help="serving_stream: requests in the stream")
+    ap.add_argument("--rate", type=float, default=2.0, help="serving_stream: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving_stream: concurrent requests")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--one-form", action="store_true", help="time only --precision (no second form)")
     return ap.parse_args()
 
 
@@ -170,10 +184,90 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------------------------
 
+def serving_requests(n, seed=0):
+    """The serving stream: n requests, each a seeded deformed sphere with 16x16 .. 64x64 elements per
+    patch, kappa ~ U[1, 30] rejected until there are >= 8 degree-2 unknowns per wavelength
+    ((2^m + 2) / 2 >= kappa along a patch edge of arc pi/2), random boundary condition, 1..32
+    incident directions; exponential inter-arrival gaps of mean 1 (scaled by the arrival rate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        m = int(rng.integers(4, 7))
+        while True:
+            kappa = float(rng.uniform(1.0, 30.0))
+            if kappa <= (2 ** m + 2) / 2:
+                break
+        dirs = rng.standard_normal((int(rng.integers(1, 33)), 3))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        out.append(dict(m=m, kappa=kappa, bc=int(rng.integers(0, 2)), dirs=dirs, geom_seed=int(rng.integers(1, 10**6)),
+                        gap=float(rng.exponential(1.0))))
+    return out
+
+
+def run_serving(args):
+    """Continuous-batching serving run: Poisson arrivals into the library's server."""
+    import torch
+    from paper_2306_11324_gb300 import binding as B
+    from paper_2306_11324_gb300 import inputs
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    reqs = serving_requests(args.requests)[rank::world]        # replicas: requests dealt to the ranks
+    ctx = B.igabem_create(local, None)
+    xhat = inputs.fibonacci_directions(100)
+    geoms = {}
+
+    def geom(seed):
+        if seed not in geoms:
+            geoms[seed] = B.igabem_geometry_create(ctx, inputs.deformed_sphere_patches(seed=seed, spans=4))
+        return geoms[seed]
+
+    def opt(r):
+        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload)
+        return B.igabem_default_options(level_m=r["m"], degree_p=2, kappa=r["kappa"], eta_cfie=r["kappa"],
+                                        bc=r["bc"], cheb_q=7, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
+                                        precision=B.MIXED_FP32, tol=1e-5, max_iter=5000,
+                                        gmres_restart=300 if r["bc"] else 30, precond=0 if r["bc"] else 1)
+    for r in reqs:
+        geom(r["geom_seed"])
+    srv = B.igabem_server_create(ctx, 0, args.slots)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        handles, t_next = [], t0
+        for r in reqs:
+            t_next += r["gap"] / args.rate
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.005, max(0.0, t_next - time.perf_counter())))
+            handles.append(B.igabem_submit(srv, geom(r["geom_seed"]), opt(r), r["dirs"], xhat))
+        for h in handles:
+            B.igabem_wait(h, -1.0)
+        wall = time.perf_counter() - t0
+    status = [B.igabem_result(h, raise_errors=False)[2] for h in handles]
+    st = B.igabem_server_get_stats(srv)
+    for h in handles:
+        B.igabem_request_destroy(h)
+    B.igabem_server_destroy(srv)
+    ok = sum(1 for c in status if c == 0)
+    out = {"metric": METRIC, "value": ok / wall * world, "unit": "solves/s", "n_gpus": world, "steps": len(reqs),
+           "warmup": 0, "ms_per_step": 1e3 * wall / max(1, len(reqs)), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded deformed spheres, Poisson arrivals)",
+           "config": {"workload": "serving_stream", "requests": len(reqs), "arrival_rate_per_s": args.rate,
+                      "slots": args.slots, "precision": "mixed", "tol": 1e-5},
+           "solve_latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
+           "completed": st["completed"], "failed": st["failed"], "peak_active": st["peak_active"],
+           "peak_bytes": st["peak_bytes"], "statuses": sorted(set(status)), "clocks": clk.summary(),
+           "rhs_total": int(sum(len(r["dirs"]) for r in reqs))}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving_stream":
+        return run_serving(args)
     import torch
     from paper_2306_11324_gb300 import binding as B
     from paper_2306_11324_gb300 import inputs
@@ -191,7 +285,7 @@ def main():
     ctx = B.igabem_create(local, stream.cuda_stream)
     patches = patches_of(wl["geometry"])
     geom = B.igabem_geometry_create(ctx, patches)
-    dirs = np.array([[0.0, 0.0, 1.0]])
+    dirs = np.array([[0.0, 0.0, 1.0]]) if wl["n_rhs"] == 1 else inputs.fibonacci_directions(wl["n_rhs"])
     xhat = inputs.fibonacci_directions(wl["n_dir"])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # larger than the 129 MB L2
 
@@ -200,6 +294,8 @@ def main():
         return B.igabem_default_options(level_m=wl["level_m"], degree_p=wl["degree_p"], kappa=wl["kappa"],
                                         eta_cfie=wl["kappa"], bc=wl["bc"], cheb_q=wl["cheb_q"],
                                         eta_adm=wl["eta_adm"], leaf_offset=leaf, tol=wl["tol"][precision],
+                                        kappa_cap=wl["kappa_cap"], gmres_restart=wl["restart"],
+                                        max_iter=5000, precond=wl["precond"][precision],
                                         precision=B.FP64 if precision == "fp64" else B.MIXED_FP32, profile=1)
 
     def request(opt, host=False):
@@ -207,7 +303,7 @@ def main():
         prob = B.igabem_problem_create(geom, opt)
         info = B.igabem_problem_info(prob)
         N = info["n_dofs"]
-        dens = None if host else torch.empty((N, 1), dtype=torch.complex128, device="cuda")
+        dens = None if host else torch.empty((N, len(dirs)), dtype=torch.complex128, device="cuda")
         dens, sinfo = B.igabem_solve(prob, dirs, N, density=dens)
         u = B.igabem_farfield(prob, dens, xhat)
         return prob, info, sinfo, u
@@ -251,7 +347,7 @@ def main():
         # operator applications on a resident problem
         prob = B.igabem_problem_create(geom, opt)
         info = B.igabem_problem_info(prob)
-        x = torch.tensor(inputs.random_complex(info["n_dofs"], cols=1), device="cuda")
+        x = torch.tensor(inputs.random_complex(info["n_dofs"], cols=len(dirs)), device="cuda")
         y = torch.empty_like(x)
         B.igabem_matvec(prob, x, y)
         nmv = 20
@@ -275,10 +371,13 @@ def main():
 
     main_form = run_form(args.precision, args.steps, args.warmup, True)
     other = "mixed" if args.precision == "fp64" else "fp64"
-    other_form = run_form(other, max(1, min(args.steps, 3)), 1, False)
-    fp64_u = (main_form if args.precision == "fp64" else other_form)["u"]
-    mix_u = (other_form if args.precision == "fp64" else main_form)["u"]
-    far_err = float(np.abs(mix_u - fp64_u).max() / np.abs(fp64_u).max())
+    other_form = run_form(other, max(1, min(args.steps, 3)), 1, False) if not args.one_form else None
+    if other_form is not None:
+        fp64_u = (main_form if args.precision == "fp64" else other_form)["u"]
+        mix_u = (other_form if args.precision == "fp64" else main_form)["u"]
+        far_err = float(np.abs(mix_u - fp64_u).max() / np.abs(fp64_u).max())
+    else:
+        far_err = None
 
     # ---- end to end through the public API with host buffers ----
     opt = options(args.precision)
@@ -300,7 +399,7 @@ def main():
     _, _, knots, ctrl, w = inputs.patches_to_arrays(patches)
     info = main_form["info"]
     h2d = int(knots.nbytes + ctrl.nbytes + w.nbytes + 8 * 2 * 2 * len(patches) + dirs.nbytes + xhat.nbytes)
-    d2h = int(info["n_dofs"] * 16 + len(xhat) * 16)
+    d2h = int(info["n_dofs"] * 16 * len(dirs) + len(xhat) * 16 * len(dirs))
 
     # ---- roofline of the dominant kernel (M2L) from the timed region's CUDA events ----
     far = info["n_far_pairs"]
@@ -308,7 +407,7 @@ def main():
     hard = bool(wl["bc"])
     C = 7 if hard else 1
     m2l = main_form["prof"].get("m2l", {"ms": 0.0, "calls": 0})
-    flops_per_mv = far * Q * Q * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C)
+    flops_per_mv = far * Q * Q * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C * len(dirs))
     m2l_ms = m2l["ms"] / max(1, m2l["calls"])
     achieved = flops_per_mv / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else 0.0
     fp64 = args.precision == "fp64"
@@ -322,7 +421,7 @@ def main():
                 "algorithmic_flops_per_matvec": flops_per_mv, "avg_ms_per_matvec": m2l_ms}
 
     def summary(f):
-        return {"precision": f["precision"], "solves_per_s": f["solves_per_s"], "matvecs_per_s": f["matvecs_per_s"],
+        return {"precision": f["precision"], "precond": wl["precond"][f["precision"]], "solves_per_s": f["solves_per_s"], "matvecs_per_s": f["matvecs_per_s"],
                 "matvec_ms": f["matvec_ms"], "ms_per_step": f["ms_per_step"], "leaf_offset": f["leaf_offset"],
                 "gmres_tol": f["tol"], "gmres_iterations": f["iters"], "matvecs_per_solve": f["mvs"],
                 "solve_latency_ms": {"p50": f["p50"], "p99": f["p99"]}, "phase_ms_per_step": f["phases"],
@@ -335,15 +434,17 @@ def main():
         "dtype": "f64" if fp64 else "f32+f64",
         "data": "synthetic (seeded geometry, plane wave)",
         "config": {"workload": args.workload, "n_dofs": info["n_dofs"], "n_elements": info["n_elements"],
+                   "n_rhs": len(dirs), "kappa_cap": wl["kappa_cap"],
                    "precision": args.precision, "leaf_offset": main_form["leaf_offset"], "cheb_q": wl["cheb_q"],
                    "eta_adm": wl["eta_adm"], "kappa": wl["kappa"], "tol": main_form["tol"],
+                   "gmres_restart": wl["restart"], "precond": wl["precond"][args.precision],
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"},
         "matvecs_per_s": main_form["matvecs_per_s"],
         "matvec_ms": main_form["matvec_ms"],
         "solve_latency_ms": {"p50": main_form["p50"], "p99": main_form["p99"]},
         "gmres_iterations": main_form["iters"], "matvecs_per_solve": main_form["mvs"],
         "phase_ms_per_step": main_form["phases"],
-        "other_form": summary(other_form),
+        "other_form": summary(other_form) if other_form is not None else None,
         "farfield_rel_err_mixed_vs_fp64": far_err,
         "gpu_launches": main_form["launches"],
         "clocks": main_form["clocks"],

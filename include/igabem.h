@@ -75,6 +75,9 @@ typedef struct {
   double tol;          /* relative residual ||b - A x|| <= tol ||b|| */
   int no_fmm;          /* 1: treat every element pair as near (dense Galerkin matrix; tests) */
   int profile;         /* 1: per-phase CUDA-event timing from problem creation on (igabem_profile_*) */
+  int precond;         /* GMRES preconditioner (the paper uses none): 0 none; 1 right preconditioner by the
+                          inverses of the leaf clusters' diagonal near-field blocks, summed over the
+                          overlapping leaves (block Jacobi).  The stopping test stays ||b - A x|| <= tol ||b||. */
 } igabem_options;
 
 /* Fills the defaults: p = 2, m = 3, kappa = 1, eta_cfie = kappa, sound-soft, q = 7, b = 0,

@@ -28,7 +28,7 @@ class igabem_options(ctypes.Structure):
                 ("bc", c_int), ("cheb_q", c_int), ("leaf_offset", c_int), ("eta_adm", c_double),
                 ("kappa_cap", c_double), ("gauss_regular", c_int), ("gauss_singular", c_int),
                 ("precision", c_int), ("gmres_restart", c_int), ("max_iter", c_int), ("tol", c_double),
-                ("no_fmm", c_int), ("profile", c_int)]
+                ("no_fmm", c_int), ("profile", c_int), ("precond", c_int)]
 
 
 class igabem_info(ctypes.Structure):

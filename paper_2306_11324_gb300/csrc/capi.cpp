@@ -106,7 +106,7 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m) {
   }
   if (gmres_m) {
     add((size_t)(gmres_m + 1) * S.N * R * cz);
-    for (int k = 0; k < 4; ++k) add(S.N * R * cz);
+    for (int k = 0; k < 6; ++k) add(S.N * R * cz);
     add((size_t)(gmres_m + 2) * R * cz);
     add(R * sizeof(double));
     add(R * sizeof(double));
@@ -126,7 +126,7 @@ struct ProblemWork {
   double *xX, *yleaf, *gq, *xin, *yout, *red;
   std::vector<void *> xhat, yhat;
   // GMRES
-  double *V, *w, *x, *b, *r, *hdev, *nrm, *sdev, *ydev;
+  double *V, *w, *x, *b, *r, *t, *u, *hdev, *nrm, *sdev, *ydev;
 };
 
 namespace {
@@ -183,6 +183,8 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
     W.x = W.arena.get<double>(S.N * R * 2);
     W.b = W.arena.get<double>(S.N * R * 2);
     W.r = W.arena.get<double>(S.N * R * 2);
+    W.t = W.arena.get<double>(S.N * R * 2);
+    W.u = W.arena.get<double>(S.N * R * 2);
     W.hdev = W.arena.get<double>((size_t)(W.gmres_m + 2) * R * 2);
     W.nrm = W.arena.get<double>(R);
     W.sdev = W.arena.get<double>(R);
@@ -267,6 +269,13 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     size_t blk_bytes = blk_entries * sizeof(double);
     // mixed precision keeps the near-field blocks in FP32; the FP64 assembly buffer is temporary
     total += mixed ? ((blk_entries * sizeof(float) + 255) & ~size_t(255)) : ((blk_bytes + 255) & ~size_t(255));
+    if (opt->precond) {
+      if (opt->precond != 1) fail(IGABEM_EINVAL, "unknown preconditioner");
+      if (S.nL > 64) fail(IGABEM_EINVAL, "the block preconditioner needs leaves with at most 64 local functions");
+      const size_t nleaf = S.lev[S.L].n;
+      total += ((nleaf * S.nL * S.nL * 2 * sizeof(double)) + 255) & ~size_t(255);
+      total += 3 * (((nleaf + 1) * sizeof(int) + 255) & ~size_t(255));
+    }
     P->arena_bytes = total + 4096;
     P->temp_bytes = mixed ? blk_bytes : 0;
   } catch (...) {
@@ -361,6 +370,17 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     launch_pair_consts(d, S, opt->kappa, st);
   }
   launch_near_field(d, S, *opt, st);
+  if (opt->precond) {
+    std::vector<int> ip(nleaf + 1), is(nleaf);
+    for (long t = 0; t <= nleaf; ++t) ip[t] = (int)t;
+    for (long t = 0; t < nleaf; ++t) is[t] = (int)t;
+    d.diag_blk = upload(A, S.diag_blk, st);
+    d.ident_ptr = upload(A, ip, st);
+    d.ident_src = upload(A, is, st);
+    d.binv = A.get<double>((size_t)nleaf * S.nL * S.nL * 2);
+    Phase ph(&P->prof, IGABEM_PH_SETUP_NEAR, st);
+    launch_block_inverse(d, S, st);
+  }
   if (mixed) {
     {
       Phase ph(&P->prof, IGABEM_PH_SETUP_NEAR, st);
@@ -428,6 +448,7 @@ void igabem_default_options(igabem_options *o) {
   o->tol = 1e-6;
   o->no_fmm = 0;
   o->profile = 0;
+  o->precond = 0;
 }
 
 int igabem_create(igabem_ctx **out, int device, void *stream) {
@@ -620,6 +641,7 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     };
     norms(W.b, bn);
     IGA_CUDA(cudaMemsetAsync(W.x, 0, vb, st));
+    IGA_CUDA(cudaMemsetAsync(W.u, 0, vb, st));
     IGA_CUDA(cudaMemcpyAsync(W.r, W.b, vb, cudaMemcpyDeviceToDevice, st));
     beta = bn;
     std::vector<int> its(R, 0);
@@ -649,7 +671,15 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
       }
       for (int j = 0; j < m; ++j) {
         double *Vj = W.V + (size_t)j * N * R * 2;
-        matvec_dev(P, R, Vj, W.w);
+        if (P->opt.precond) {  // right preconditioning: w = A M^-1 v_j
+          {
+            Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+            launch_precond(P->d, S, P->opt, R, Vj, W.t, st);
+          }
+          matvec_dev(P, R, W.t, W.w);
+        } else {
+          matvec_dev(P, R, Vj, W.w);
+        }
         ++n_mv;
         std::vector<cd> h((j + 1) * R, 0.0);
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
@@ -717,7 +747,12 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
       IGA_CUDA(cudaMemcpyAsync(W.ydev, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
       {
         Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-        launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+        if (P->opt.precond) {  // u += V y;  x = M^-1 u
+          launch_update(W.V, kmax, W.ydev, W.u, N, R, st);
+          launch_precond(P->d, S, P->opt, R, W.u, W.x, st);
+        } else {
+          launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+        }
       }
       matvec_dev(P, R, W.x, W.w);
       ++n_mv;

@@ -581,6 +581,10 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     if (it == b1 || *it != tf) fail(IGABEM_EINVAL, "touching pair outside the near field");
     S.touch_blk[i] = int(it - S.near_src.begin());
   }
+  S.diag_blk.assign(nleaf, -1);
+  for (int t = 0; t < nleaf; ++t)
+    for (int k = S.near_ptr[t]; k < S.near_ptr[t + 1]; ++k)
+      if (S.near_src[k] == t) S.diag_blk[t] = k;
   // unordered work list: identical pairs, and (e, f) with e < f for the others (the block of (f, e)
   // comes from the same quadrature points with the roles of x and y exchanged)
   S.sing.clear();

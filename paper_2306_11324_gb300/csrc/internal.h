@@ -34,7 +34,10 @@ void set_error(const std::string &msg);
 // not exceed it.
 int max_optin_smem();
 template <class K> cudaError_t set_max_dynamic_smem(K kernel, size_t bytes) {
-  const int mx = max_optin_smem();
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int mx = max_optin_smem() - (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts too
   if (bytes > (size_t)mx) fail(IGABEM_EINVAL, "kernel needs more shared memory than the device offers");
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
@@ -106,6 +109,7 @@ struct HostSetup {
   // work list of the singular quadrature: each unordered touching pair once,
   // (e, f, kind, Te, Tf, block of (e,f), block of (f,e) or -1 for identical pairs)
   std::vector<int> sing;
+  std::vector<int> diag_blk;           // per leaf: index of its diagonal near block (t, t)
   long n_far = 0;
   // interpolation tables
   std::vector<double> cheb;            // normalised Chebyshev nodes t_a on [0,1]
@@ -193,6 +197,9 @@ struct DeviceProblem {
   // near-field blocks (column-major nL x nL per near pair)
   double *blk = nullptr;                     // complex FP64: 2 doubles per entry (FP64 precision)
   float *blk32 = nullptr;                    // complex FP32 copy used by the mixed precision SpMV
+  // preconditioner: inverses of the diagonal leaf blocks (column-major, complex FP64), identity lists
+  double *binv = nullptr;
+  int *diag_blk = nullptr, *ident_ptr = nullptr, *ident_src = nullptr;
   // work buffers, sized for max_rhs columns
   int max_rhs = 0;
   double *xX = nullptr;                      // X-space input [NX][R] complex

@@ -315,6 +315,20 @@ __global__ void k_gather_out(Dims D, const int *__restrict__ g2x_ptr, const int 
 
 }  // namespace
 
+void launch_precond(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                    const double *r, double *z, cudaStream_t st) {
+  Dims D = dims(S, o, R);
+  k_gather_in<<<grid_for(D.NX * R), 256, 0, st>>>(D, d.x2g, reinterpret_cast<const double2 *>(r),
+                                                   reinterpret_cast<double2 *>(d.xX));
+  note_launch();
+  launch_block_apply(d, S, o, R, st);
+  k_gather_out<<<grid_for(D.N * R), 256, 0, st>>>(D, d.g2x_ptr, d.g2x_idx,
+                                                   reinterpret_cast<const double2 *>(d.yleaf),
+                                                   reinterpret_cast<double2 *>(z));
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
 void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                    const double *x, double *y, cudaStream_t st) {
   Dims D = dims(S, o, R);

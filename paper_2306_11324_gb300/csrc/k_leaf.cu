@@ -312,6 +312,135 @@ int column_chunk(size_t (*smem)(const HostSetup &, int, int), const HostSetup &S
 }  // namespace
 
 namespace {
+// Preconditioner blocks: for every leaf t, the near-field part of the operator restricted to the
+// leaf's own functions (the principal submatrix A[I_t, I_t]: every leaf-pair block (t', s') whose
+// leaves carry both functions contributes its entry), inverted by Gauss-Jordan elimination with
+// partial pivoting in FP64.  A numerically singular block is replaced by the identity.
+struct InvArgs {
+  const int *near_ptr, *near_src;
+  const int *x2g, *g2x_ptr, *g2x_idx;
+  int L, b, nL1, nL, nb;
+};
+
+// near-field entry A^near[X_r, X_c] between two patch-wise functions (possibly of different patches):
+// the sum over the leaf pairs whose leaves carry the two functions
+template <class BT>
+__device__ double2 near_entry(const InvArgs &A, const BT *__restrict__ blk, int Xr, int Xc) {
+  const int nlL = 1 << A.L, e1 = 1 << A.b, nb2 = A.nb * A.nb;
+  const int jr = Xr / nb2, r1 = (Xr / A.nb) % A.nb, r2 = Xr % A.nb;
+  const int jc = Xc / nb2, c1 = (Xc / A.nb) % A.nb, c2 = Xc % A.nb;
+  double2 sum = make_double2(0, 0);
+  auto lo = [&](int i) { return max(0, (i - A.nL1 + e1) / e1); };
+  auto hi = [&](int i) { return min(nlL - 1, i / e1); };
+  for (int x1 = lo(r1); x1 <= hi(r1); ++x1)
+    for (int y1 = lo(r2); y1 <= hi(r2); ++y1) {
+      const int tp = (jr * nlL + x1) * nlL + y1;
+      const int rl = (r1 - x1 * e1) * A.nL1 + (r2 - y1 * e1);
+      const int k0 = A.near_ptr[tp], k1 = A.near_ptr[tp + 1];
+      for (int x2 = lo(c1); x2 <= hi(c1); ++x2)
+        for (int y2 = lo(c2); y2 <= hi(c2); ++y2) {
+          const int sp = (jc * nlL + x2) * nlL + y2;
+          int a = k0, z = k1;  // binary search for the near block (tp, sp)
+          while (a < z) {
+            int mid = (a + z) >> 1;
+            if (A.near_src[mid] < sp) a = mid + 1; else z = mid;
+          }
+          if (a < k1 && A.near_src[a] == sp) {
+            const int cl = (c1 - x2 * e1) * A.nL1 + (c2 - y2 * e1);
+            const BT v = blk[(size_t)a * A.nL * A.nL + (size_t)cl * A.nL + rl];
+            sum.x += (double)v.x;
+            sum.y += (double)v.y;
+          }
+        }
+    }
+  return sum;
+}
+
+// entry (al, be) of the principal submatrix of leaf t in global numbering: the basis functions of
+// the (continuous) space are sums of their patch-wise copies
+template <class BT>
+__device__ double2 principal_entry(const InvArgs &A, const BT *__restrict__ blk, int t, int al, int be) {
+  const int nlL = 1 << A.L, e1 = 1 << A.b;
+  const int j = t / (nlL * nlL), cx = (t / nlL) % nlL, cy = t % nlL;
+  const int Xa = (j * A.nb + cx * e1 + al / A.nL1) * A.nb + cy * e1 + al % A.nL1;
+  const int Xb = (j * A.nb + cx * e1 + be / A.nL1) * A.nb + cy * e1 + be % A.nL1;
+  const int ga = A.x2g[Xa], gb = A.x2g[Xb];
+  double2 sum = make_double2(0, 0);
+  for (int u = A.g2x_ptr[ga]; u < A.g2x_ptr[ga + 1]; ++u)
+    for (int v = A.g2x_ptr[gb]; v < A.g2x_ptr[gb + 1]; ++v) {
+      double2 e = near_entry(A, blk, A.g2x_idx[u], A.g2x_idx[v]);
+      sum.x += e.x;
+      sum.y += e.y;
+    }
+  return sum;
+}
+
+template <class BT>
+__global__ void k_block_inverse(InvArgs IA, const BT *__restrict__ blk, double2 *__restrict__ binv) {
+  extern __shared__ double2 gj[];
+  const int nL = IA.nL;
+  double2 *M = gj, *I = gj + nL * nL, *fac = I + nL * nL;
+  __shared__ int piv;
+  __shared__ bool bad;
+  const int t = blockIdx.x;
+  for (int o = threadIdx.x; o < nL * nL; o += blockDim.x) {
+    int i = o / nL, j = o % nL;                       // row-major M[i][j] = A[I_t(i), I_t(j)]
+    M[o] = principal_entry(IA, blk, t, i, j);
+    I[o] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (threadIdx.x == 0) bad = false;
+  __syncthreads();
+  for (int c = 0; c < nL; ++c) {
+    if (threadIdx.x == 0) {
+      int best = c;
+      double bv = -1.0;
+      for (int r = c; r < nL; ++r) {
+        double2 v = M[r * nL + c];
+        double a = v.x * v.x + v.y * v.y;
+        if (a > bv) {
+          bv = a;
+          best = r;
+        }
+      }
+      piv = best;
+      if (!(bv > 1e-280)) bad = true;
+    }
+    __syncthreads();
+    if (bad) break;
+    const int pr = piv;
+    if (pr != c)
+      for (int j = threadIdx.x; j < nL; j += blockDim.x) {
+        double2 a = M[c * nL + j], b = M[pr * nL + j];
+        M[c * nL + j] = b; M[pr * nL + j] = a;
+        a = I[c * nL + j]; b = I[pr * nL + j];
+        I[c * nL + j] = b; I[pr * nL + j] = a;
+      }
+    __syncthreads();
+    const double2 d = M[c * nL + c];
+    const double den = d.x * d.x + d.y * d.y;
+    const double2 inv = make_double2(d.x / den, -d.y / den);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nL; j += blockDim.x) {
+      M[c * nL + j] = cmul(M[c * nL + j], inv);
+      I[c * nL + j] = cmul(I[c * nL + j], inv);
+    }
+    for (int r = threadIdx.x; r < nL; r += blockDim.x) fac[r] = M[r * nL + c];
+    __syncthreads();
+    for (int o = threadIdx.x; o < nL * nL; o += blockDim.x) {
+      int r = o / nL, j = o % nL;
+      if (r == c) continue;
+      M[o] = csub(M[o], cmul(fac[r], M[c * nL + j]));
+      I[o] = csub(I[o], cmul(fac[r], I[c * nL + j]));
+    }
+    __syncthreads();
+  }
+  double2 *out = binv + (size_t)t * nL * nL;
+  for (int o = threadIdx.x; o < nL * nL; o += blockDim.x) {
+    int i = o / nL, j = o % nL;                       // column-major out[j][i] = Inv[i][j]
+    out[(size_t)j * nL + i] = bad ? make_double2(i == j ? 1.0 : 0.0, 0.0) : I[o];
+  }
+}
+
 __global__ void k_to_fp32(const double *__restrict__ src, float *__restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -320,6 +449,38 @@ __global__ void k_to_fp32(const double *__restrict__ src, float *__restrict__ ds
 
 void launch_blocks_to_fp32(const double *src, float *dst, size_t n, cudaStream_t st) {
   k_to_fp32<<<152 * 8, 256, 0, st>>>(src, dst, n);
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
+void launch_block_inverse(const DeviceProblem &d, const HostSetup &S, cudaStream_t st) {
+  const int nleaf = S.lev[S.L].n;
+  const size_t smem = (2 * (size_t)S.nL * S.nL + S.nL) * sizeof(double2);
+  InvArgs IA{d.near_ptr, d.near_src, d.x2g, d.g2x_ptr, d.g2x_idx, S.L, S.b, S.nL1, S.nL, S.nb};
+  if (d.blk) {
+    IGA_CUDA(set_max_dynamic_smem(k_block_inverse<double2>, smem));
+    k_block_inverse<double2><<<nleaf, 256, smem, st>>>(IA, reinterpret_cast<const double2 *>(d.blk),
+                                                       reinterpret_cast<double2 *>(d.binv));
+  } else {
+    IGA_CUDA(set_max_dynamic_smem(k_block_inverse<float2>, smem));
+    k_block_inverse<float2><<<nleaf, 256, smem, st>>>(IA, reinterpret_cast<const float2 *>(d.blk32),
+                                                      reinterpret_cast<double2 *>(d.binv));
+  }
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
+// z_leaf[t] = Binv_t x_t for every leaf t (the same product as the near-field SpMV, one block per leaf)
+void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                        cudaStream_t st) {
+  LeafArgs A = leaf_args(d, S, o, R);
+  const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
+  const int G = nout <= threads / 2 ? threads / nout : 1;
+  size_t smem = G > 1 ? (size_t)G * nout * sizeof(double2) : 0;
+  k_near_spmv2<double2><<<dim3(nleaf, 1), threads, smem, st>>>(A, d.ident_ptr, d.ident_src,
+                                                               reinterpret_cast<const double2 *>(d.binv),
+                                                               reinterpret_cast<const double2 *>(d.xX),
+                                                               reinterpret_cast<double2 *>(d.yleaf), S.nL);
   note_launch();
   IGA_CUDA(cudaGetLastError());
 }

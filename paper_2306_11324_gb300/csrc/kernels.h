@@ -21,6 +21,12 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
                       cudaStream_t st);
 void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
 void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
+void launch_block_inverse(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
+void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                        cudaStream_t st);
+// z = M^-1 r for the block Jacobi preconditioner (k_apply.cu)
+void launch_precond(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
+                    const double *r, double *z, cudaStream_t st);
 void launch_blocks_to_fp32(const double *src, float *dst, size_t n, cudaStream_t st);
 
 // operator application (k_apply.cu): y = A x for R columns, x and y device [N][R] complex

@@ -53,8 +53,13 @@ typedef enum { IGABEM_SOUND_SOFT = 0, IGABEM_SOUND_HARD = 1 } igabem_bc;
 
 typedef enum {
   IGABEM_FP64 = 0,        /* every step in FP64 */
-  IGABEM_MIXED_FP32 = 1   /* far field (M2L, moments) and regular near-field quadrature in FP32,
-                             singular quadrature, near-field SpMV, GMRES and residuals in FP64 */
+  IGABEM_MIXED_FP32 = 1,  /* far field (M2L, moments), regular near-field quadrature and the stored
+                             near-field blocks in FP32 with FP32 accumulation per block; singular
+                             quadrature, GMRES and residuals in FP64 */
+  IGABEM_MIXED_TC = 2     /* IGABEM_MIXED_FP32 with the M2L of R >= 16 right-hand sides (R a multiple
+                             of 16, channels x R <= 512) on the tensor cores: TF32 operands split
+                             into hi + lo, three products, FP32 accumulation; other R as
+                             IGABEM_MIXED_FP32 */
 } igabem_precision;
 
 typedef struct {

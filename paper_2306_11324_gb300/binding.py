@@ -20,7 +20,7 @@ c_int, c_long, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_long, ctyp
 IGABEM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOT_CONVERGED", -5: "ENUMERIC", -6: "ETIMEOUT"}
 SOUND_SOFT, SOUND_HARD = 0, 1
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_TC = 0, 1, 2
 
 
 class igabem_options(ctypes.Structure):

@@ -88,7 +88,7 @@ void Arena::release() {
 }
 
 // device bytes of the per-call work buffers for R columns (and a GMRES basis of gmres_m + 1 vectors)
-size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m) {
+size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision) {
   const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
   const size_t cz = 2 * sizeof(double);
   const long nleaf = S.lev[S.L].n;
@@ -104,6 +104,8 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m) {
     add((size_t)S.lev[l].n * Q * C * R * cz);
     add((size_t)S.lev[l].n * Q * C * R * cz);
   }
+  if (precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
+    for (int l = S.lmin; l <= S.L; ++l) add(m2l_tc_image_bytes(S, l, R));
   if (gmres_m) {
     add((size_t)(gmres_m + 1) * S.N * R * cz);
     for (int k = 0; k < 6; ++k) add(S.N * R * cz);
@@ -125,6 +127,7 @@ struct ProblemWork {
   Arena arena;
   double *xX, *yleaf, *gq, *xin, *yout, *red;
   std::vector<void *> xhat, yhat;
+  std::vector<uint8_t *> tc_bimg;
   // GMRES
   double *V, *w, *x, *b, *r, *t, *u, *hdev, *nrm, *sdev, *ydev;
 };
@@ -162,7 +165,7 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   if (with_gmres) W.gmres_m = std::max(W.gmres_m, m);
   const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
   const long nleaf = S.lev[S.L].n;
-  size_t total = problem_work_bytes(S, R, W.gmres_m);
+  size_t total = problem_work_bytes(S, R, W.gmres_m, P->opt.precision);
   W.arena.reserve(total);
   W.R = R;
   W.xX = W.arena.get<double>(S.NX * R * 2);
@@ -177,6 +180,9 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
     W.xhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
     W.yhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
   }
+  W.tc_bimg.assign(S.L + 1, nullptr);
+  if (P->opt.precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
+    for (int l = S.lmin; l <= S.L; ++l) W.tc_bimg[l] = W.arena.get<uint8_t>(m2l_tc_image_bytes(S, l, R));
   if (W.gmres_m) {
     W.V = W.arena.get<double>((size_t)(W.gmres_m + 1) * S.N * R * 2);
     W.w = W.arena.get<double>(S.N * R * 2);
@@ -200,6 +206,17 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   d.red = W.red;
   d.xhat = W.xhat;
   d.yhat = W.yhat;
+  d.tc_bimg = W.tc_bimg;
+}
+
+// the device status word: a kernel whose bounded wait ran out has set it (the stream is synchronised)
+void check_status(igabem_problem *P) {
+  int v = 0;
+  IGA_CUDA(cudaMemcpy(&v, P->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    IGA_CUDA(cudaMemset(P->d.status, 0, sizeof(int)));
+    fail(IGABEM_ETIMEOUT, "a tensor-core M2L wait timed out; the result is incomplete");
+  }
 }
 
 template <class T> T *upload(Arena &A, const std::vector<T> &v, cudaStream_t st) {
@@ -230,7 +247,7 @@ namespace igabem {
 // host-side plan of a problem: validation, set-up tables and the device memory it will hold
 igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
   if (!geom || !opt) fail(IGABEM_EINVAL, "invalid problem arguments");
-  if (opt->precision != IGABEM_FP64 && opt->precision != IGABEM_MIXED_FP32)
+  if (opt->precision != IGABEM_FP64 && opt->precision != IGABEM_MIXED_FP32 && opt->precision != IGABEM_MIXED_TC)
     fail(IGABEM_EINVAL, "unknown precision");
   if (!(opt->eta_adm > 0)) fail(IGABEM_EINVAL, "eta_adm must be positive");
   if (!(opt->kappa >= 0)) fail(IGABEM_EINVAL, "kappa must be >= 0");
@@ -264,7 +281,7 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
       total += bytes_of(S.lev[l].center);
       total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
     }
-    const bool mixed = opt->precision == IGABEM_MIXED_FP32;
+    const bool mixed = opt->precision != IGABEM_FP64;
     size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
     size_t blk_bytes = blk_entries * sizeof(double);
     // mixed precision keeps the near-field blocks in FP32; the FP64 assembly buffer is temporary
@@ -276,6 +293,9 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
       total += ((nleaf * S.nL * S.nL * 2 * sizeof(double)) + 255) & ~size_t(255);
       total += 3 * (((nleaf + 1) * sizeof(int) + 255) & ~size_t(255));
     }
+    total += 256;  // status word
+    if (S.n_far > 0 && leaf_moments_supported(S))
+      total += ((leaf_moment_entries(S) * (mixed ? sizeof(float) : sizeof(double))) + 255) & ~size_t(255);
     P->arena_bytes = total + 4096;
     P->temp_bytes = mixed ? blk_bytes : 0;
   } catch (...) {
@@ -303,13 +323,15 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     for (const auto *v : {&r.x1, &r.x2, &r.y1, &r.y2, &r.w}) rules[k].insert(rules[k].end(), v->begin(), v->end());
   }
   const size_t gst = (size_t)S.E * nq;
-  const bool mixed = opt->precision == IGABEM_MIXED_FP32;
+  const bool mixed = opt->precision != IGABEM_FP64;
   const size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
   const size_t blk_bytes = blk_entries * sizeof(double);
   P->arena.reserve(P->arena_bytes);
   Arena &A = P->arena;
   DeviceProblem &d = P->d;
   d.prof = &P->prof;
+  d.status = A.get<int>(1);
+  IGA_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int), st));
   d.edeg = upload(A, S.edeg, st);
   d.eoff = upload(A, S.eoff, st);
   d.ebez = upload(A, S.ebez, st);
@@ -365,6 +387,14 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
   launch_gauss_geometry(d, S, st);
   launch_node_geometry(d, S, cheb, st);
+  if (S.n_far > 0 && leaf_moments_supported(S)) {
+    if (mixed)
+      d.lm32 = A.get<float>(leaf_moment_entries(S));
+    else
+      d.lm64 = A.get<double>(leaf_moment_entries(S));
+    Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
+    launch_leaf_moments(d, S, *opt, st);
+  }
   if (S.n_far > 0) {
     Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
     launch_pair_consts(d, S, opt->kappa, st);
@@ -610,6 +640,7 @@ int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
     matvec_dev(P, n_rhs, xi, yo);
     if (!dy) IGA_CUDA(cudaMemcpyAsync(y, yo, bytes, cudaMemcpyDeviceToHost, st));
     IGA_CUDA(cudaStreamSynchronize(st));
+    check_status(P);
     P->prof.flush();
   });
 }
@@ -761,6 +792,7 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
         launch_sub(W.b, W.w, W.r, N * R * 2, st);
       }
       norms(W.r, beta);
+      check_status(P);
       for (int r = 0; r < R; ++r) {
         if (!std::isfinite(beta[r])) fail(IGABEM_ENUMERIC, "GMRES met a non-finite residual");
         active[r] = beta[r] > tol * bn[r];

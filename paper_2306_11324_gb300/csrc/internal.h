@@ -193,6 +193,10 @@ struct DeviceProblem {
   std::vector<float *> nodes32;              // per level: [7][n*q*q] (x - centre, n~, a) in FP32
   std::vector<double *> centers;             // per level: [n][3] cluster centres
   std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
+  std::vector<uint8_t *> tc_bimg;            // per level: tensor-core M2L operands of the sources
+  int *status = nullptr;                     // device status word: non-zero after a timed-out wait
+  double *lm64 = nullptr;                    // leaf moment matrices [n_leaf][nL][q^2 C] (FP64 precision)
+  float *lm32 = nullptr;                     // the same in FP32 (mixed precision)
   double *T1, *LG1;
   // near-field blocks (column-major nL x nL per near pair)
   double *blk = nullptr;                     // complex FP64: 2 doubles per entry (FP64 precision)
@@ -217,7 +221,7 @@ namespace igabem {
 igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt);
 void problem_materialize(igabem_problem *P, cudaStream_t st);
 void problem_release(igabem_problem *P);
-size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m);
+size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision);
 double now_ms();
 }  // namespace igabem
 

@@ -368,7 +368,10 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     }
     if (m2l_rows_supported(S)) {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
-      launch_m2l_rows(d, S, o, R, o.precision == IGABEM_MIXED_FP32, st);
+      if (o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() && d.tc_bimg[S.L])
+        launch_m2l_tc(d, S, o, R, st);
+      else
+        launch_m2l_rows(d, S, o, R, o.precision != IGABEM_FP64, st);
     } else {
       int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
       int ntypes = D.hard ? 2 : 1;

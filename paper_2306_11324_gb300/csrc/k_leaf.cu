@@ -106,6 +106,85 @@ __global__ void k_near_spmv2(LeafArgs A, const int *__restrict__ near_ptr, const
   }
 }
 
+// Near-field SpMV for many columns: one thread block per (target leaf, chunk of 64 columns).  Each
+// near block and the source leaf's coefficients (converted to the block's precision) are staged in
+// shared memory; each thread owns a 4 x 4 tile of (local function, column) outputs.  One block's sum
+// is formed in the storage precision, the blocks are summed in FP64, as in k_near_spmv2.
+constexpr int NM_COLS = 64;
+
+template <class BT>
+__global__ void __launch_bounds__(256) k_near_mrhs(LeafArgs A, const int *__restrict__ near_ptr,
+                                                   const int *__restrict__ near_src, const BT *__restrict__ blk,
+                                                   const double2 *__restrict__ xX, double2 *__restrict__ yleaf,
+                                                   int nL) {
+  using RT = decltype(BT::x);
+  extern __shared__ __align__(16) unsigned char smn[];
+  BT *Bs = reinterpret_cast<BT *>(smn);  // [nL (source)][nL (target)]
+  BT *Xs = Bs + nL * nL;                 // [nL][NM_COLS]
+  const int t = blockIdx.x, r0 = blockIdx.y * NM_COLS, Rc = min(NM_COLS, A.R - r0);
+  const int nlL = 1 << A.L, e1 = 1 << A.b;
+  const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
+  double2 acc[4][4];
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) acc[m][n] = make_double2(0.0, 0.0);
+  for (int k = near_ptr[t]; k < near_ptr[t + 1]; ++k) {
+    const int s = near_src[k];
+    const int js = s / (nlL * nlL), cx = (s / nlL) % nlL, cy = s % nlL;
+    const long base = ((long)js * A.nb + cx * e1) * A.nb + cy * e1;
+    __syncthreads();  // the previous block's products are done
+    const BT *Bk = blk + (size_t)k * nL * nL;
+    for (int e = threadIdx.x; e < nL * nL; e += blockDim.x) Bs[e] = Bk[e];
+    for (int e = threadIdx.x; e < nL * NM_COLS; e += blockDim.x) {
+      const int jj = e / NM_COLS, c = e % NM_COLS, al = jj / A.nL1, be = jj % A.nL1;
+      BT v;
+      v.x = 0;
+      v.y = 0;
+      if (c < Rc) {
+        const double2 xd = xX[(base + (long)al * A.nb + be) * A.R + r0 + c];
+        v.x = (RT)xd.x;
+        v.y = (RT)xd.y;
+      }
+      Xs[e] = v;
+    }
+    __syncthreads();
+    RT px[4][4], py[4][4];
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) px[m][n] = py[m][n] = 0;
+    for (int jj = 0; jj < nL; ++jj) {
+      BT bv[4], xv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int i = ti + 16 * m;
+        if (i < nL) {
+          bv[m] = Bs[jj * nL + i];
+        } else {
+          bv[m].x = 0;
+          bv[m].y = 0;
+        }
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) xv[n] = Xs[jj * NM_COLS + tr + 16 * n];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          px[m][n] += bv[m].x * xv[n].x - bv[m].y * xv[n].y;
+          py[m][n] += bv[m].x * xv[n].y + bv[m].y * xv[n].x;
+        }
+    }
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) {
+        acc[m][n].x += (double)px[m][n];
+        acc[m][n].y += (double)py[m][n];
+      }
+  }
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) {
+      const int i = ti + 16 * m, c = tr + 16 * n;
+      if (i < nL && c < Rc) yleaf[((size_t)t * nL + i) * A.R + r0 + c] = acc[m][n];
+    }
+}
+
 // P2M for the columns [r0, r0 + Rc) of every channel.
 // shared: X[nL1][nL1][Rc], U[nG][nL1][Rc] (and dU), f[nG][nG][C][Rc], T[q][nG][C][Rc]
 __global__ void k_p2m2(LeafArgs A, const double2 *__restrict__ xX, double2 *__restrict__ xhat, int r0, int Rc) {
@@ -278,6 +357,196 @@ __global__ void k_l2p2(LeafArgs A, const double2 *__restrict__ yhat, double2 *__
     double2 *dst = yleaf + ((size_t)t * A.nL1 * A.nL1 + al * nL1 + be) * A.R + r0 + r;
     *dst = cadd(*dst, s);
   }
+}
+
+// Leaf moment matrices (Sec. 4.4), set up once per problem: M_t[k][a C + c] = sum over the leaf's
+// Gauss points g of L_a(g) w_c(g, k) for the leaf-local B-spline k = al nL1 + be, with
+//   w_0 = W phi_k,  w_{1+d} = W (ft_d d_s phi_k - fs_d d_t phi_k),  w_{4+d} = W n~_d phi_k
+// (W = w_1 w_2 h^2; channels 1..6 only for sound-hard).  P2M applies M_t to the leaf's coefficients;
+// L2P applies its transpose with the channel factors of the tested operator, so both passes are dense
+// products over many columns.  Tensor form: the a1 sum first (shared memory Tq[k][a1][g2]).
+template <class T>
+__global__ void k_leaf_moments(LeafArgs A, T *__restrict__ M) {
+  extern __shared__ double smm[];
+  const int t = blockIdx.x;
+  const int nlL = 1 << A.L, e1 = 1 << A.b;
+  const int j = t / (nlL * nlL), cx = (t / nlL) % nlL, cy = t % nlL;
+  const int c0x = cx * e1, c0y = cy * e1;
+  const int nG = e1 * A.ng, q = A.q, Q = q * q, C = A.C, nL1 = A.nL1, nL = nL1 * nL1, QC = Q * C;
+  double *Tq = smm;  // [nL][q][nG]
+  for (int c = 0; c < C; ++c) {
+    for (int i = threadIdx.x; i < nL * q * nG; i += blockDim.x) {
+      const int k = i / (q * nG), a1 = (i / nG) % q, g2 = i % nG;
+      const int al = k / nL1, be = k % nL1;
+      const double pb = leaf_phi(A, A.phi1, c0y, g2, be);
+      const double dpb = A.hard ? leaf_phi(A, A.dphi1, c0y, g2, be) : 0.0;
+      double sum = 0.0;
+      if (pb != 0.0 || dpb != 0.0) {
+        for (int g1 = 0; g1 < nG; ++g1) {
+          const double pa = leaf_phi(A, A.phi1, c0x, g1, al);
+          const double dpa = A.hard ? leaf_phi(A, A.dphi1, c0x, g1, al) : 0.0;
+          if (pa == 0.0 && dpa == 0.0) continue;
+          const double W = A.gw[g1 % A.ng] * A.gw[g2 % A.ng] * A.h * A.h;
+          double w;
+          if (c == 0) {
+            w = W * pa * pb;
+          } else {
+            const long e = ((long)j * A.n1 + c0x + g1 / A.ng) * A.n1 + c0y + g2 / A.ng;
+            const long iq = e * A.ng * A.ng + (g1 % A.ng) * A.ng + g2 % A.ng;
+            if (c <= 3)
+              w = W * (A.gft[(c - 1) * A.gst + iq] * dpa * pb - A.gfs[(c - 1) * A.gst + iq] * pa * dpb);
+            else
+              w = W * A.gpn[(c - 4) * A.gst + iq] * pa * pb;
+          }
+          sum += A.LG1[g1 * q + a1] * w;
+        }
+      }
+      Tq[i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nL * Q; i += blockDim.x) {
+      const int k = i / Q, a = i % Q, a1 = a / q, a2 = a % q;
+      double sum = 0.0;
+      for (int g2 = 0; g2 < nG; ++g2) sum += A.LG1[g2 * q + a2] * Tq[(k * q + a1) * nG + g2];
+      M[((size_t)t * nL + k) * QC + a * C + c] = (T)sum;
+    }
+    __syncthreads();
+  }
+}
+
+// complex value type of the moment products
+template <class T> struct CT;
+template <> struct CT<float> { using type = float2; };
+template <> struct CT<double> { using type = double2; };
+
+// P2M for many columns: xhat_t[a C + c][r] = sum_k M_t[k][a C + c] x_t[k][r], one thread block per
+// (leaf, chunk of 64 columns), 64-row chunks of the output with a 4 x 4 register tile per thread.
+template <class T>
+__global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ xX,
+                                                  double2 *__restrict__ xhat) {
+  using V = typename CT<T>::type;
+  extern __shared__ __align__(16) unsigned char smp[];
+  const int nL1 = A.nL1, nL = nL1 * nL1, QC = A.q * A.q * A.C;
+  V *Xs = reinterpret_cast<V *>(smp);        // [nL][64]
+  T *Ms = reinterpret_cast<T *>(Xs + nL * 64);  // [nL][64]
+  const int t = blockIdx.x, r0 = blockIdx.y * 64, Rc = min(64, A.R - r0);
+  const int nlL = 1 << A.L, e1 = 1 << A.b;
+  const int j = t / (nlL * nlL), cx = (t / nlL) % nlL, cy = t % nlL;
+  const long base = ((long)j * A.nb + cx * e1) * A.nb + cy * e1;
+  const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
+  for (int e = threadIdx.x; e < nL * 64; e += blockDim.x) {
+    const int k = e / 64, c = e % 64, al = k / nL1, be = k % nL1;
+    V v;
+    v.x = 0;
+    v.y = 0;
+    if (c < Rc) {
+      const double2 xd = xX[(base + (long)al * A.nb + be) * A.R + r0 + c];
+      v.x = (T)xd.x;
+      v.y = (T)xd.y;
+    }
+    Xs[e] = v;
+  }
+  for (int i0 = 0; i0 < QC; i0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nL * 64; e += blockDim.x) {
+      const int k = e / 64, i = i0 + e % 64;
+      Ms[e] = i < QC ? M[((size_t)t * nL + k) * QC + i] : (T)0;
+    }
+    __syncthreads();
+    T px[4][4], py[4][4];
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) px[m][n] = py[m][n] = 0;
+    for (int k = 0; k < nL; ++k) {
+      T mv[4];
+      V xv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) mv[m] = Ms[k * 64 + ti + 16 * m];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) xv[n] = Xs[k * 64 + tr + 16 * n];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          px[m][n] += mv[m] * xv[n].x;
+          py[m][n] += mv[m] * xv[n].y;
+        }
+    }
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) {
+        const int i = i0 + ti + 16 * m, c = tr + 16 * n;
+        if (i < QC && c < Rc) xhat[((size_t)t * QC + i) * A.R + r0 + c] = make_double2((double)px[m][n], (double)py[m][n]);
+      }
+  }
+}
+
+// L2P for many columns: y_leaf[t][k][r] += sum_{a, c} M_t[k][a C + c] sigma_c yhat_t[a C + c][r] with the
+// channel factors of the tested operator: soft sigma_0 = 1; hard sigma_0 = -1 (the -K part),
+// sigma_{1..3} = -i eta (curl test of -i eta W), sigma_{4..6} = i eta kappa^2 (its normal part).
+template <class T>
+__global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ yhat,
+                                                  double2 *__restrict__ yleaf) {
+  using V = typename CT<T>::type;
+  extern __shared__ __align__(16) unsigned char smq[];
+  const int nL1 = A.nL1, nL = nL1 * nL1, C = A.C, QC = A.q * A.q * C;
+  V *Ys = reinterpret_cast<V *>(smq);           // [64 rows a C + c][64]
+  T *Ms = reinterpret_cast<T *>(Ys + 64 * 64);  // [nL][64 rows]
+  const int t = blockIdx.x, r0 = blockIdx.y * 64, Rc = min(64, A.R - r0);
+  const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
+  const double k2e = A.kappa * A.kappa * A.eta;
+  T px[4][4], py[4][4];
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) px[m][n] = py[m][n] = 0;
+  for (int i0 = 0; i0 < QC; i0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+      const int i = i0 + e / 64, c = e % 64;
+      double2 y = make_double2(0.0, 0.0);
+      if (i < QC && c < Rc) {
+        const double2 yv = yhat[((size_t)t * QC + i) * A.R + r0 + c];
+        const int ch = i % C;
+        if (!A.hard) y = yv;
+        else if (ch == 0) y = make_double2(-yv.x, -yv.y);
+        else if (ch <= 3) y = make_double2(A.eta * yv.y, -A.eta * yv.x);
+        else y = make_double2(-k2e * yv.y, k2e * yv.x);
+      }
+      V v;
+      v.x = (T)y.x;
+      v.y = (T)y.y;
+      Ys[e] = v;
+    }
+    for (int e = threadIdx.x; e < nL * 64; e += blockDim.x) {
+      const int k = e / 64, i = i0 + e % 64;
+      Ms[e] = i < QC ? M[((size_t)t * nL + k) * QC + i] : (T)0;
+    }
+    __syncthreads();
+    const int iw = min(64, QC - i0);
+    for (int i = 0; i < iw; ++i) {
+      T mv[4];
+      V yv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = ti + 16 * m;
+        mv[m] = k < nL ? Ms[k * 64 + i] : (T)0;
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) yv[n] = Ys[i * 64 + tr + 16 * n];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          px[m][n] += mv[m] * yv[n].x;
+          py[m][n] += mv[m] * yv[n].y;
+        }
+    }
+  }
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) {
+      const int k = ti + 16 * m, c = tr + 16 * n;
+      if (k < nL && c < Rc) {
+        double2 *dst = yleaf + ((size_t)t * nL + k) * A.R + r0 + c;
+        *dst = make_double2(dst->x + (double)px[m][n], dst->y + (double)py[m][n]);
+      }
+    }
 }
 
 LeafArgs leaf_args(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R) {
@@ -475,6 +744,27 @@ void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem
                         cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
+  if (R >= 8 && S.nL <= 64) {
+    dim3 grid(nleaf, (R + NM_COLS - 1) / NM_COLS);
+    if (d.blk32) {
+      const size_t smem = sizeof(float2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
+      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<float2>, smem));
+      k_near_mrhs<float2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
+                                                       reinterpret_cast<const float2 *>(d.blk32),
+                                                       reinterpret_cast<const double2 *>(d.xX),
+                                                       reinterpret_cast<double2 *>(d.yleaf), S.nL);
+    } else {
+      const size_t smem = sizeof(double2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
+      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<double2>, smem));
+      k_near_mrhs<double2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
+                                                        reinterpret_cast<const double2 *>(d.blk),
+                                                        reinterpret_cast<const double2 *>(d.xX),
+                                                        reinterpret_cast<double2 *>(d.yleaf), S.nL);
+    }
+    note_launch();
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   const int G = nout <= threads / 2 ? threads / nout : 1;
   size_t smem = G > 1 ? (size_t)G * nout * sizeof(double2) : 0;
   k_near_spmv2<double2><<<dim3(nleaf, 1), threads, smem, st>>>(A, d.ident_ptr, d.ident_src,
@@ -519,9 +809,48 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
   IGA_CUDA(cudaGetLastError());
 }
 
+size_t leaf_moment_entries(const HostSetup &S) {
+  return (size_t)S.lev[S.L].n * S.nL1 * S.nL1 * S.q * S.q * (S.hard ? 7 : 1);
+}
+
+bool leaf_moments_supported(const HostSetup &S) { return S.nL1 * S.nL1 <= 64; }
+
+void launch_leaf_moments(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, cudaStream_t st) {
+  LeafArgs A = leaf_args(d, S, o, 1);
+  const int nG = (1 << S.b) * S.ng;
+  const size_t smem = sizeof(double) * (size_t)S.nL1 * S.nL1 * S.q * nG;
+  if (d.lm32) {
+    IGA_CUDA(set_max_dynamic_smem(k_leaf_moments<float>, smem));
+    k_leaf_moments<float><<<S.lev[S.L].n, 256, smem, st>>>(A, d.lm32);
+  } else {
+    IGA_CUDA(set_max_dynamic_smem(k_leaf_moments<double>, smem));
+    k_leaf_moments<double><<<S.lev[S.L].n, 256, smem, st>>>(A, d.lm64);
+  }
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
 void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n;
+  if (R >= 8 && (d.lm32 || d.lm64)) {
+    dim3 grid(nleaf, (R + 63) / 64);
+    const size_t nl = (size_t)S.nL1 * S.nL1 * 64;
+    if (d.lm32) {
+      const size_t smem = nl * (sizeof(float2) + sizeof(float));
+      IGA_CUDA(set_max_dynamic_smem(k_p2m_mrhs<float>, smem));
+      k_p2m_mrhs<float><<<grid, 256, smem, st>>>(A, d.lm32, reinterpret_cast<const double2 *>(d.xX),
+                                                 reinterpret_cast<double2 *>(d.xhat[S.L]));
+    } else {
+      const size_t smem = nl * (sizeof(double2) + sizeof(double));
+      IGA_CUDA(set_max_dynamic_smem(k_p2m_mrhs<double>, smem));
+      k_p2m_mrhs<double><<<grid, 256, smem, st>>>(A, d.lm64, reinterpret_cast<const double2 *>(d.xX),
+                                                  reinterpret_cast<double2 *>(d.xhat[S.L]));
+    }
+    note_launch();
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   int Rc = column_chunk(p2m_smem, S, A.C, R);
   size_t smem = p2m_smem(S, A.C, Rc);
   IGA_CUDA(set_max_dynamic_smem(k_p2m2, smem));
@@ -536,6 +865,24 @@ void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options
 void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n;
+  if (R >= 8 && (d.lm32 || d.lm64)) {
+    dim3 grid(nleaf, (R + 63) / 64);
+    const size_t nl = (size_t)S.nL1 * S.nL1 * 64;
+    if (d.lm32) {
+      const size_t smem = 64 * 64 * sizeof(float2) + nl * sizeof(float);
+      IGA_CUDA(set_max_dynamic_smem(k_l2p_mrhs<float>, smem));
+      k_l2p_mrhs<float><<<grid, 256, smem, st>>>(A, d.lm32, reinterpret_cast<const double2 *>(d.yhat[S.L]),
+                                                 reinterpret_cast<double2 *>(d.yleaf));
+    } else {
+      const size_t smem = 64 * 64 * sizeof(double2) + nl * sizeof(double);
+      IGA_CUDA(set_max_dynamic_smem(k_l2p_mrhs<double>, smem));
+      k_l2p_mrhs<double><<<grid, 256, smem, st>>>(A, d.lm64, reinterpret_cast<const double2 *>(d.yhat[S.L]),
+                                                  reinterpret_cast<double2 *>(d.yleaf));
+    }
+    note_launch();
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   int Rc = column_chunk(l2p_smem, S, A.C, R);
   size_t smem = l2p_smem(S, A.C, Rc);
   IGA_CUDA(set_max_dynamic_smem(k_l2p2, smem));

@@ -549,7 +549,7 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   int nblk = (int)S.near_src.size();
   if (nblk > 0) {
     const int nq = S.ng * S.ng, nloc = S.nloc;
-    const bool f32 = o.precision == IGABEM_MIXED_FP32;
+    const bool f32 = o.precision != IGABEM_FP64;
     const size_t tsz = f32 ? sizeof(float) : sizeof(double);
     const size_t per = (size_t)(2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc +
                                 6 * nq * nloc) * tsz;

@@ -12,6 +12,10 @@ void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa
 bool m2l_rows_supported(const HostSetup &S);
 void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      bool fp32, cudaStream_t st);
+// tensor-core M2L for R right-hand sides (k_m2l_tc.cu); yhat from xhat through d.tc_bimg
+bool m2l_tc_supported(const HostSetup &S, int R);
+size_t m2l_tc_image_bytes(const HostSetup &S, int l, int R);
+void launch_m2l_tc(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
 void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
                        cudaStream_t st);
 
@@ -21,6 +25,10 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
                       cudaStream_t st);
 void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
 void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
+// leaf moment matrices for the many-column P2M / L2P (set up once per problem)
+bool leaf_moments_supported(const HostSetup &S);
+size_t leaf_moment_entries(const HostSetup &S);
+void launch_leaf_moments(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, cudaStream_t st);
 void launch_block_inverse(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
 void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                         cudaStream_t st);

@@ -89,7 +89,7 @@ void worker_loop(igabem_server *S) {
     try {
       P = problem_plan(r->geom, &r->opt);
       need = P->arena_bytes + P->temp_bytes +
-             problem_work_bytes(P->S, r->R, std::max(1, r->opt.gmres_restart)) + (size_t(64) << 20);
+             problem_work_bytes(P->S, r->R, std::max(1, r->opt.gmres_restart), r->opt.precision) + (size_t(64) << 20);
       r->bytes = need;
       if (need > S->budget) {
         status = IGABEM_ENOMEM;

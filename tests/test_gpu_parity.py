@@ -83,6 +83,9 @@ def test_solve_sound_soft_sphere():
 
 
 MIXED_MATVEC_TOL = 2e-6   # FP32 far field (phase-split kernel samples, FP32 accumulation)
+# tensor-core M2L: TF32 split products (hi hi + hi lo + lo hi, each operand to ~2^-22) summed by the
+# tensor core into FP32 over K = 2 q^2 terms and the whole interaction list
+MIXED_TC_TOL = 1e-5
 
 
 @pytest.mark.parametrize("hard,kappa", [(False, 1.0), (False, 6.0), (True, 3.0)])
@@ -102,8 +105,7 @@ def test_mixed_fmm_matvec_matches_interpolated_kernel_matrix(hard, kappa):
 @pytest.mark.parametrize("hard", [False, True])
 def test_mixed_solve_far_field_matches_fp64(hard):
     """The mixed-precision solve reproduces the FP64 far field to 1e-5 (spec bar)."""
-    kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=int(hard), cheb_q=7, leaf_offset=1,
-              eta_adm=0.5)
+    kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=int(hard), cheb_q=7, leaf_offset=1)
     xh = inputs.fibonacci_directions(100)
     d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])
     u = {}
@@ -118,16 +120,18 @@ def test_mixed_solve_far_field_matches_fp64(hard):
     assert G.rel(u[B.MIXED_FP32], u[B.FP64]) < 1e-5
 
 
+@pytest.mark.parametrize("R", [6, 16])
 @pytest.mark.parametrize("prec,hard", [(B.FP64, False), (B.FP64, True), (B.MIXED_FP32, False),
                                        (B.MIXED_FP32, True)])
-def test_multi_rhs_fmm_matvec(prec, hard):
-    """Several right-hand sides at once (the multi-column M2L): every column against the oracle."""
+def test_multi_rhs_fmm_matvec(prec, hard, R):
+    """Several right-hand sides at once (the multi-column M2L; from 8 columns on also the many-column
+    near-field SpMV and the moment-matrix P2M / L2P): every column against the oracle."""
     m, p, leaf, q, kappa = 2, 1, 2, 5, 3.0
     prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
                            leaf_offset=m - leaf, eta_adm=0.5, precision=prec)
     sp = C.sphere_space(m, p, hard)
     Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
-    x = inputs.random_complex(sp.N, seed=77, cols=6)
+    x = inputs.random_complex(sp.N, seed=77, cols=R)
     y = B.igabem_matvec(prob, x)
     tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
     assert G.rel(y, Amat @ x) < tol
@@ -135,6 +139,62 @@ def test_multi_rhs_fmm_matvec(prec, hard):
     y0 = B.igabem_matvec(prob, np.ascontiguousarray(x[:, 2]))
     assert G.rel(y0, y[:, 2]) < (1e-13 if prec == B.FP64 else MIXED_MATVEC_TOL)
     B.igabem_problem_destroy(prob)
+
+
+def _m2l_launches(prob):
+    return B.igabem_profile_get(prob, reset=True)["phases"]["m2l"]["launches"]
+
+
+@pytest.mark.parametrize("hard,R", [(False, 16), (False, 64), (True, 16), (True, 32)])
+def test_tensor_core_m2l_matches_oracle(hard, R):
+    """tcgen05 M2L (TF32 hi/lo split, FP32 accumulation) against the oracle's mode-B matrix, every column."""
+    m, p, leaf, q, kappa = 2, 1, 2, 5, 3.0
+    prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
+                           leaf_offset=m - leaf, eta_adm=0.5, precision=B.MIXED_TC)
+    sp = C.sphere_space(m, p, hard)
+    Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
+    x = inputs.random_complex(sp.N, seed=78, cols=R)
+    _m2l_launches(prob)
+    y = B.igabem_matvec(prob, x)
+    launches = _m2l_launches(prob)
+    assert launches >= 2            # operand packing per level + the tensor-core kernel
+    ref = Amat @ x
+    # the same product with the FP32 CUDA-core M2L, for the record
+    prob32, _ = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
+                          leaf_offset=m - leaf, eta_adm=0.5, precision=B.MIXED_FP32)
+    y32 = B.igabem_matvec(prob32, x)
+    B.igabem_problem_destroy(prob32)
+    print(f"tensor-core M2L rel. error {G.rel(y, ref):.2e}, FP32 M2L {G.rel(y32, ref):.2e}")
+    assert G.rel(y32, ref) < MIXED_MATVEC_TOL
+    assert G.rel(y, ref) < MIXED_TC_TOL
+    # a column count the tensor-core path does not take (not a multiple of 16) runs the FP32 M2L
+    y5 = B.igabem_matvec(prob, np.ascontiguousarray(x[:, :5]))
+    assert _m2l_launches(prob) == 1
+    assert G.rel(y5, ref[:, :5]) < MIXED_MATVEC_TOL
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_tensor_core_m2l_q7_against_fp64(hard):
+    """q = 7 (the benchmark's interpolation degree), many clusters and pairs: tcgen05 M2L against the
+    FP64 GPU path and against the FP32 CUDA-core M2L."""
+    m, R = 4, (32 if hard else 64)
+    kw = dict(level_m=m, degree_p=2, kappa=6.0, eta_adm=0.5, eta_cfie=6.0, bc=int(hard), cheb_q=7, leaf_offset=1)
+    kind = "deformed" if hard else "sphere"
+    ys = {}
+    for prec in (B.FP64, B.MIXED_FP32, B.MIXED_TC):
+        prob, info = G.problem(kind, precision=prec, **kw)
+        if prec == B.FP64:
+            x = inputs.random_complex(info["n_dofs"], seed=79, cols=R)
+        _m2l_launches(prob)
+        ys[prec] = B.igabem_matvec(prob, x)
+        if prec == B.MIXED_TC:
+            assert _m2l_launches(prob) >= 2
+        B.igabem_problem_destroy(prob)
+    print(f"q=7: tensor-core vs FP64 {G.rel(ys[B.MIXED_TC], ys[B.FP64]):.2e}, "
+          f"FP32 vs FP64 {G.rel(ys[B.MIXED_FP32], ys[B.FP64]):.2e}")
+    assert G.rel(ys[B.MIXED_FP32], ys[B.FP64]) < MIXED_MATVEC_TOL
+    assert G.rel(ys[B.MIXED_TC], ys[B.FP64]) < MIXED_TC_TOL
 
 
 @pytest.mark.parametrize("hard", [False, True])

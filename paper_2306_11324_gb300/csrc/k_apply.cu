@@ -154,6 +154,142 @@ __global__ void k_l2l(Dims D, int l, const double *__restrict__ T1, const double
   }
 }
 
+// M2M and L2L for many columns with the separable transfer T(c, a, b) = T1(c1, a1, b1) T1(c2, a2, b2)
+// (tensor Chebyshev interpolation, Sec. 4.4): the two 1-D contractions one after the other through
+// shared memory, in precision T (FP32 for the mixed precisions), one block per (parent, 32 columns).
+template <class T> struct CV;
+template <> struct CV<float> { using type = float2; };
+template <> struct CV<double> { using type = double2; };
+constexpr int SEP_COLS = 32;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_m2m_sep(Dims D, int l, const double *__restrict__ T1,
+                                                 const double2 *__restrict__ child, double2 *__restrict__ parent) {
+  using V = typename CV<T>::type;
+  extern __shared__ __align__(16) unsigned char smx[];
+  V *X = reinterpret_cast<V *>(smx);  // [b1][b2][col]
+  V *Z = X + D.Q * SEP_COLS;          // [b1][a2][col]
+  __shared__ T Ts[2 * 16 * 16];
+  const int q = D.q, Q = q * q, CR = D.CR;
+  const int t = blockIdx.x, c0 = blockIdx.y * SEP_COLS, cw = min(SEP_COLS, CR - c0);
+  const int nl = 1 << l, nc = 2 * nl;
+  const int j = t / (nl * nl), cx = (t / nl) % nl, cy = t % nl;
+  for (int i = threadIdx.x; i < 2 * q * q; i += blockDim.x) Ts[i] = (T)T1[i];
+  V acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k].x = acc[k].y = 0;
+  for (int ch = 0; ch < 4; ++ch) {
+    const int c1 = ch >> 1, c2 = ch & 1;
+    const long tc = ((long)j * nc + 2 * cx + c1) * nc + 2 * cy + c2;
+    __syncthreads();
+    for (int i = threadIdx.x; i < Q * SEP_COLS; i += blockDim.x) {
+      const int b = i / SEP_COLS, col = i % SEP_COLS;
+      V v;
+      v.x = v.y = 0;
+      if (col < cw) {
+        const double2 x = child[(tc * Q + b) * CR + c0 + col];
+        v.x = (T)x.x;
+        v.y = (T)x.y;
+      }
+      X[i] = v;
+    }
+    __syncthreads();
+    // second direction: Z[b1][a2][col] = sum_b2 T(c2, a2, b2) X[b1][b2][col]
+    for (int i = threadIdx.x; i < Q * SEP_COLS; i += blockDim.x) {
+      const int b1 = i / (q * SEP_COLS), a2 = (i / SEP_COLS) % q, col = i % SEP_COLS;
+      V sum;
+      sum.x = sum.y = 0;
+      for (int b2 = 0; b2 < q; ++b2) {
+        const T w = Ts[(c2 * q + a2) * q + b2];
+        const V x = X[(b1 * q + b2) * SEP_COLS + col];
+        sum.x += w * x.x;
+        sum.y += w * x.y;
+      }
+      Z[i] = sum;
+    }
+    __syncthreads();
+    // first direction into the parent: acc[a1][a2][col] += sum_b1 T(c1, a1, b1) Z[b1][a2][col]
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      if (i >= Q * SEP_COLS) continue;
+      const int a = i / SEP_COLS, col = i % SEP_COLS, a1 = a / q, a2 = a % q;
+      for (int b1 = 0; b1 < q; ++b1) {
+        const T w = Ts[(c1 * q + a1) * q + b1];
+        const V x = Z[(b1 * q + a2) * SEP_COLS + col];
+        acc[k].x += w * x.x;
+        acc[k].y += w * x.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = threadIdx.x + 256 * k;
+    if (i >= Q * SEP_COLS) continue;
+    const int a = i / SEP_COLS, col = i % SEP_COLS;
+    if (col < cw) parent[((long)t * Q + a) * CR + c0 + col] = make_double2((double)acc[k].x, (double)acc[k].y);
+  }
+}
+
+// L2L: yhat_child[b][cr] += sum_a T(c, a, b) yhat_parent[a][cr] for the four children of the block's
+// parent t on level l.
+template <class T>
+__global__ void __launch_bounds__(256) k_l2l_sep(Dims D, int l, const double *__restrict__ T1,
+                                                 const double2 *__restrict__ parent, double2 *__restrict__ child) {
+  using V = typename CV<T>::type;
+  extern __shared__ __align__(16) unsigned char smy[];
+  const int q = D.q, Q = q * q, CR = D.CR;
+  V *P = reinterpret_cast<V *>(smy);  // [a1][a2][col]
+  V *U = P + Q * SEP_COLS;            // [c2][a1][b2][col]
+  __shared__ T Ts[2 * 16 * 16];
+  const int t = blockIdx.x, c0 = blockIdx.y * SEP_COLS, cw = min(SEP_COLS, CR - c0);
+  const int nl = 1 << l, nc = 2 * nl;
+  const int j = t / (nl * nl), cx = (t / nl) % nl, cy = t % nl;
+  for (int i = threadIdx.x; i < 2 * q * q; i += blockDim.x) Ts[i] = (T)T1[i];
+  for (int i = threadIdx.x; i < Q * SEP_COLS; i += blockDim.x) {
+    const int a = i / SEP_COLS, col = i % SEP_COLS;
+    V v;
+    v.x = v.y = 0;
+    if (col < cw) {
+      const double2 y = parent[((long)t * Q + a) * CR + c0 + col];
+      v.x = (T)y.x;
+      v.y = (T)y.y;
+    }
+    P[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * Q * SEP_COLS; i += blockDim.x) {
+    const int c2 = i / (Q * SEP_COLS), r = i % (Q * SEP_COLS), a1 = r / (q * SEP_COLS), b2 = (r / SEP_COLS) % q,
+              col = r % SEP_COLS;
+    V sum;
+    sum.x = sum.y = 0;
+    for (int a2 = 0; a2 < q; ++a2) {
+      const T w = Ts[(c2 * q + a2) * q + b2];
+      const V v = P[(a1 * q + a2) * SEP_COLS + col];
+      sum.x += w * v.x;
+      sum.y += w * v.y;
+    }
+    U[i] = sum;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * Q * SEP_COLS; i += blockDim.x) {
+    const int ch = i / (Q * SEP_COLS), r = i % (Q * SEP_COLS), b = r / SEP_COLS, col = r % SEP_COLS;
+    if (col >= cw) continue;
+    const int c1 = ch >> 1, c2 = ch & 1, b1 = b / q, b2 = b % q;
+    V sum;
+    sum.x = sum.y = 0;
+    for (int a1 = 0; a1 < q; ++a1) {
+      const T w = Ts[(c1 * q + a1) * q + b1];
+      const V u = U[((c2 * q + a1) * q + b2) * SEP_COLS + col];
+      sum.x += w * u.x;
+      sum.y += w * u.y;
+    }
+    const long tc = ((long)j * nc + 2 * cx + c1) * nc + 2 * cy + c2;
+    double2 *dst = child + (tc * Q + b) * CR + c0 + col;
+    *dst = make_double2(dst->x + (double)sum.x, dst->y + (double)sum.y);
+  }
+}
+
 // M2L on level l: yhat[t][a][cr] = sum_{s in far(t)} sum_b S_ts(a, b) xhat[s][b][cr], with the kernel
 // samples between the Chebyshev nodes generated on the fly:
 //   soft: S = a_y G'(r)/r (x-y).n~_x - i eta a_x a_y G      (pull-back of K' - i eta V)
@@ -360,9 +496,21 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     }
     {
       Phase ph(d.prof, IGABEM_PH_M2M, st);
+      const bool sep = D.CR >= 16 && D.q <= 16 && D.Q * SEP_COLS <= 256 * 8;
+      const bool f32 = o.precision != IGABEM_FP64;
+      const size_t smem = (size_t)2 * D.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
+      if (sep) IGA_CUDA(f32 ? set_max_dynamic_smem(k_m2m_sep<float>, smem) : set_max_dynamic_smem(k_m2m_sep<double>, smem));
       for (int l = S.L - 1; l >= S.lmin; --l) {
         long n = (long)S.lev[l].n * D.Q * D.CR;
-        k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+        if (sep) {
+          dim3 grid(S.lev[l].n, (D.CR + SEP_COLS - 1) / SEP_COLS);
+          if (f32)
+            k_m2m_sep<float><<<grid, 256, smem, st>>>(D, l, d.T1, X(l + 1), X(l));
+          else
+            k_m2m_sep<double><<<grid, 256, smem, st>>>(D, l, d.T1, X(l + 1), X(l));
+        } else {
+          k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+        }
         note_launch();
       }
     }
@@ -386,9 +534,21 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     }
     {
       Phase ph(d.prof, IGABEM_PH_L2L, st);
+      const bool sep = D.CR >= 16 && D.q <= 16;
+      const bool f32 = o.precision != IGABEM_FP64;
+      const size_t smem = (size_t)3 * D.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
+      if (sep) IGA_CUDA(f32 ? set_max_dynamic_smem(k_l2l_sep<float>, smem) : set_max_dynamic_smem(k_l2l_sep<double>, smem));
       for (int l = S.lmin; l < S.L; ++l) {
         long n = (long)S.lev[l + 1].n * D.Q * D.CR;
-        k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+        if (sep) {
+          dim3 grid(S.lev[l].n, (D.CR + SEP_COLS - 1) / SEP_COLS);
+          if (f32)
+            k_l2l_sep<float><<<grid, 256, smem, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+          else
+            k_l2l_sep<double><<<grid, 256, smem, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+        } else {
+          k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+        }
         note_launch();
       }
     }

@@ -746,21 +746,12 @@ void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
   if (R >= 8 && S.nL <= 64) {
     dim3 grid(nleaf, (R + NM_COLS - 1) / NM_COLS);
-    if (d.blk32) {
-      const size_t smem = sizeof(float2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
-      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<float2>, smem));
-      k_near_mrhs<float2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
-                                                       reinterpret_cast<const float2 *>(d.blk32),
-                                                       reinterpret_cast<const double2 *>(d.xX),
-                                                       reinterpret_cast<double2 *>(d.yleaf), S.nL);
-    } else {
-      const size_t smem = sizeof(double2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
-      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<double2>, smem));
-      k_near_mrhs<double2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
-                                                        reinterpret_cast<const double2 *>(d.blk),
-                                                        reinterpret_cast<const double2 *>(d.xX),
-                                                        reinterpret_cast<double2 *>(d.yleaf), S.nL);
-    }
+    const size_t smem = sizeof(double2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
+    IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<double2>, smem));
+    k_near_mrhs<double2><<<grid, threads, smem, st>>>(A, d.ident_ptr, d.ident_src,
+                                                      reinterpret_cast<const double2 *>(d.binv),
+                                                      reinterpret_cast<const double2 *>(d.xX),
+                                                      reinterpret_cast<double2 *>(d.yleaf), S.nL);
     note_launch();
     IGA_CUDA(cudaGetLastError());
     return;
@@ -784,6 +775,27 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
                       cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
+  if (R >= 8 && S.nL <= 64) {
+    dim3 grid(nleaf, (R + NM_COLS - 1) / NM_COLS);
+    if (d.blk32) {
+      const size_t smem = sizeof(float2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
+      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<float2>, smem));
+      k_near_mrhs<float2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
+                                                       reinterpret_cast<const float2 *>(d.blk32),
+                                                       reinterpret_cast<const double2 *>(d.xX),
+                                                       reinterpret_cast<double2 *>(d.yleaf), S.nL);
+    } else {
+      const size_t smem = sizeof(double2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
+      IGA_CUDA(set_max_dynamic_smem(k_near_mrhs<double2>, smem));
+      k_near_mrhs<double2><<<grid, threads, smem, st>>>(A, d.near_ptr, d.near_src,
+                                                        reinterpret_cast<const double2 *>(d.blk),
+                                                        reinterpret_cast<const double2 *>(d.xX),
+                                                        reinterpret_cast<double2 *>(d.yleaf), S.nL);
+    }
+    note_launch();
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   const int G = nout <= threads / 2 ? threads / nout : 1;
   size_t smem = G > 1 ? (size_t)G * nout * sizeof(double2) : 0;
   // enough blocks to keep HBM busy: split long near lists over gridDim.y blocks that add atomically

@@ -1,5 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element, on
 small seeded problems that span several clusters and leaf blocks."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -197,21 +199,54 @@ def test_tensor_core_m2l_q7_against_fp64(hard):
     assert G.rel(ys[B.MIXED_TC], ys[B.FP64]) < MIXED_TC_TOL
 
 
+@functools.lru_cache(maxsize=None)
+def _three_level_rows(hard, col):
+    """Oracle rows of the mode-B product on a three-level tree (far pairs on levels 2 and 3)."""
+    sp = C.sphere_space(3, 1, hard)
+    x = inputs.random_complex(sp.N, seed=91, cols=16)
+    rows = np.array([0, 77, sp.N // 2, sp.N - 1])
+    tree = C.tree(3, 1, 3, 0.5, 4, 2.0, hard)
+    return rows, fmm.cfie_rows(sp, 2.0, 2.0, hard, x[:, col], rows, tree=tree)
+
+
+@pytest.mark.parametrize("prec,hard", [(B.FP64, False), (B.FP64, True), (B.MIXED_TC, True)])
+def test_transfers_three_levels(prec, hard):
+    """M2M / L2L between two levels with many columns (separable transfers): sampled rows of two
+    columns against the oracle, every column against the one-column path."""
+    prob, info = G.problem(level_m=3, degree_p=1, kappa=2.0, eta_cfie=2.0, bc=int(hard), cheb_q=4,
+                           leaf_offset=0, eta_adm=0.5, precision=prec)
+    sp = C.sphere_space(3, 1, hard)
+    assert info["n_far_pairs"] == sum(len(f) for f in C.tree(3, 1, 3, 0.5, 4, 2.0, hard).far)
+    x = inputs.random_complex(sp.N, seed=91, cols=16)
+    y = B.igabem_matvec(prob, x)
+    tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
+    for col in (0, 9):
+        rows, ref = _three_level_rows(hard, col)
+        assert np.abs(y[rows, col] - ref).max() / np.abs(y[:, col]).max() < tol
+    for col in (0, 5, 15):
+        y1 = B.igabem_matvec(prob, np.ascontiguousarray(x[:, col]))
+        assert G.rel(y[:, col], y1) < (1e-12 if prec == B.FP64 else MIXED_MATVEC_TOL)
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("n_dirs", [1, 8])
 @pytest.mark.parametrize("hard", [False, True])
-def test_preconditioned_solve_matches_lu(hard):
-    """The block-Jacobi right preconditioner changes the iterations, not the solution."""
+def test_preconditioned_solve_matches_lu(hard, n_dirs):
+    """The block-Jacobi right preconditioner changes the iterations, not the solution (one column,
+    and eight columns through the many-column SpMV and block apply)."""
     kappa = 2.0
     sp = C.sphere_space(2, 1, hard)
     Amat = C.cfie(2, 1, kappa, kappa, hard)
-    d = np.array([[0.0, 0.6, 0.8]])
-    ref = solve.lu_solve(Amat, A.rhs(sp, kappa, kappa, d[0], hard))
+    d = inputs.fibonacci_directions(n_dirs) if n_dirs > 1 else np.array([[0.0, 0.6, 0.8]])
+    ref = solve.lu_solve(Amat, A.rhs(sp, kappa, kappa, d, hard)).reshape(sp.N, n_dirs)
     its = {}
     for pc in (0, 1):
         prob, info = G.problem(level_m=2, degree_p=1, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=4,
                                leaf_offset=1, eta_adm=0.5, no_fmm=1, tol=1e-10, precond=pc)
         x, sinfo = B.igabem_solve(prob, d, info["n_dofs"])
         assert sinfo["rel_residual"] <= 1e-10
-        assert G.rel(x[:, 0], ref) < 1e-8
+        for r in range(n_dirs):
+            assert G.rel(x[:, r], ref[:, r]) < 1e-8
         its[pc] = sinfo["iterations"]
         B.igabem_problem_destroy(prob)
     if not hard:                   # second-kind equation: the local blocks capture it well

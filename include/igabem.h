@@ -57,9 +57,10 @@ typedef enum {
                              near-field blocks in FP32 with FP32 accumulation per block; singular
                              quadrature, GMRES and residuals in FP64 */
   IGABEM_MIXED_TC = 2     /* IGABEM_MIXED_FP32 with the M2L of R >= 16 right-hand sides (R a multiple
-                             of 16, channels x R <= 512) on the tensor cores: TF32 operands split
-                             into hi + lo, three products, FP32 accumulation; other R as
-                             IGABEM_MIXED_FP32 */
+                             of 16; sound-hard R <= 64, sound-soft R <= 512) on the tensor cores:
+                             operands scaled by exact powers of two and split into FP16 hi + lo,
+                             three products per pair, FP32 accumulation rounded to nearest per pair;
+                             other R as IGABEM_MIXED_FP32 */
 } igabem_precision;
 
 typedef struct {

@@ -105,7 +105,10 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision)
     add((size_t)S.lev[l].n * Q * C * R * cz);
   }
   if (precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
-    for (int l = S.lmin; l <= S.L; ++l) add(m2l_tc_image_bytes(S, l, R));
+    for (int l = S.lmin; l <= S.L; ++l) {
+      add(m2l_tc_image_bytes(S, l, R));
+      add((size_t)S.lev[l].n * sizeof(float));
+    }
   if (gmres_m) {
     add((size_t)(gmres_m + 1) * S.N * R * cz);
     for (int k = 0; k < 6; ++k) add(S.N * R * cz);
@@ -128,6 +131,7 @@ struct ProblemWork {
   double *xX, *yleaf, *gq, *xin, *yout, *red;
   std::vector<void *> xhat, yhat;
   std::vector<uint8_t *> tc_bimg;
+  std::vector<float *> tc_bscale;
   // GMRES
   double *V, *w, *x, *b, *r, *t, *u, *hdev, *nrm, *sdev, *ydev;
 };
@@ -181,8 +185,12 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
     W.yhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
   }
   W.tc_bimg.assign(S.L + 1, nullptr);
+  W.tc_bscale.assign(S.L + 1, nullptr);
   if (P->opt.precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
-    for (int l = S.lmin; l <= S.L; ++l) W.tc_bimg[l] = W.arena.get<uint8_t>(m2l_tc_image_bytes(S, l, R));
+    for (int l = S.lmin; l <= S.L; ++l) {
+      W.tc_bimg[l] = W.arena.get<uint8_t>(m2l_tc_image_bytes(S, l, R));
+      W.tc_bscale[l] = W.arena.get<float>(S.lev[l].n);
+    }
   if (W.gmres_m) {
     W.V = W.arena.get<double>((size_t)(W.gmres_m + 1) * S.N * R * 2);
     W.w = W.arena.get<double>(S.N * R * 2);
@@ -207,6 +215,7 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   d.xhat = W.xhat;
   d.yhat = W.yhat;
   d.tc_bimg = W.tc_bimg;
+  d.tc_bscale = W.tc_bscale;
 }
 
 // the device status word: a kernel whose bounded wait ran out has set it (the stream is synchronised)
@@ -397,7 +406,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   }
   if (S.n_far > 0) {
     Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
-    launch_pair_consts(d, S, opt->kappa, st);
+    launch_pair_consts(d, S, opt->kappa, opt->eta_cfie, st);
   }
   launch_near_field(d, S, *opt, st);
   if (opt->precond) {

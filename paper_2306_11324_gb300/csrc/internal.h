@@ -194,6 +194,7 @@ struct DeviceProblem {
   std::vector<double *> centers;             // per level: [n][3] cluster centres
   std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
   std::vector<uint8_t *> tc_bimg;            // per level: tensor-core M2L operands of the sources
+  std::vector<float *> tc_bscale;            // per level: power-of-two scale of each cluster's operand
   int *status = nullptr;                     // device status word: non-zero after a timed-out wait
   double *lm64 = nullptr;                    // leaf moment matrices [n_leaf][nL][q^2 C] (FP64 precision)
   float *lm32 = nullptr;                     // the same in FP32 (mixed precision)

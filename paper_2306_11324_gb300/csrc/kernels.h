@@ -8,7 +8,7 @@ namespace igabem {
 // set-up (k_setup.cu)
 void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
 void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st);
-void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, cudaStream_t st);
+void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, double eta, cudaStream_t st);
 bool m2l_rows_supported(const HostSetup &S);
 void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      bool fp32, cudaStream_t st);

@@ -85,8 +85,8 @@ def test_solve_sound_soft_sphere():
 
 
 MIXED_MATVEC_TOL = 2e-6   # FP32 far field (phase-split kernel samples, FP32 accumulation)
-# tensor-core M2L: TF32 split products (hi hi + hi lo + lo hi, each operand to ~2^-22) summed by the
-# tensor core into FP32 over K = 2 q^2 terms and the whole interaction list
+# tensor-core M2L: FP16 split products (hi hi + hi lo + lo hi, each scaled operand to ~2^-22 of its
+# largest entry) summed by the tensor core into FP32 per pair, pairs added in FP32
 MIXED_TC_TOL = 1e-5
 
 
@@ -149,7 +149,7 @@ def _m2l_launches(prob):
 
 @pytest.mark.parametrize("hard,R", [(False, 16), (False, 64), (True, 16), (True, 32)])
 def test_tensor_core_m2l_matches_oracle(hard, R):
-    """tcgen05 M2L (TF32 hi/lo split, FP32 accumulation) against the oracle's mode-B matrix, every column."""
+    """tcgen05 M2L (FP16 hi/lo split, FP32 accumulation) against the oracle's mode-B matrix, every column."""
     m, p, leaf, q, kappa = 2, 1, 2, 5, 3.0
     prob, info = G.problem(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q,
                            leaf_offset=m - leaf, eta_adm=0.5, precision=B.MIXED_TC)

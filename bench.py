@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the isogeometric CFIE solver on one GB300 (or N replicas of it under torchrun).
 
-A step is one scattering request through the whole hot path: problem set-up (geometry tables, cluster
-tree, near-field Galerkin quadrature), right-hand side, GMRES with fast multipole matrix-vector
-products, far-field pattern at 100 Fibonacci directions.  Workload (default): sound-soft unit sphere
-as 6 exact rational patches with 32 x 32 elements each (6144 elements), B-splines of degree 2
-(6936 unknowns), kappa = 8, eta = kappa, plane wave d = (0,0,1), interpolation with 7 x 7 Chebyshev
-points per cluster, admissibility eta_adm = 0.5, FP64, GMRES(30) to a relative residual of 1e-6.
+Default workload (a step is one scattering request through the whole hot path: problem set-up with
+geometry tables, cluster tree and near-field Galerkin quadrature, right-hand side, GMRES with fast
+multipole matrix-vector products, far-field pattern at 100 Fibonacci directions): sound-soft unit
+sphere as 6 exact rational patches with 32 x 32 elements each (6144 elements), B-splines of degree 2
+(6936 unknowns), kappa = 8, eta = kappa, plane wave d = (0,0,1), 7 x 7 Chebyshev points per cluster,
+admissibility eta_adm = 0.5, GMRES(30) to 1e-6; timed in the mixed precision (FP32 far field, block
+preconditioner), the FP64 form timed beside it and the far fields of the two compared.
+
+--workload deformed_hard_6x64x64_p2_k20_64dirs: sound-hard deformed sphere, 24576 elements, kappa = 20,
+64 incident directions; a step is one operator application to the 64 columns (tensor-core M2L by
+default), one full solve timed beside the steps, the product checked against the FP64 operator.
+--workload serving_stream: Poisson arrivals of mixed requests into the library's server.
 
 Prints one JSON line (see the keys below).  --impl reference times the CPU oracle instead.
 """
@@ -33,18 +39,22 @@ WORKLOADS = {
     "sphere_soft_6x32x32_p2_k8": dict(geometry="sphere", level_m=5, degree_p=2, kappa=8.0, bc=0,
                                       cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
                                       tol={"fp64": 1e-6, "mixed": 1e-6}, n_dir=100, n_rhs=1, kappa_cap=0.0,
-                                      restart=30, precond={"fp64": 0, "mixed": 1}),
+                                      restart=30, precond={"fp64": 0, "mixed": 1}, precision="mixed"),
     # sound-hard deformed sphere (amplitude 0.15, seed 1), 64 x 64 elements per patch, kappa = 20,
     # 64 incident directions on a Fibonacci sphere solved as one multi-RHS request; admissibility capped
     # at kappa * diameter <= 6 (FMM truncation ~1e-5 against the dense matrix at q = 7)
     # GMRES(30) stagnates on this sound-hard system (the hypersingular part is unbounded and kappa is
     # large): restart 300.
+    # A step of this workload is one operator application to all 64 columns (the hard system needs
+    # ~1000 GMRES iterations, about a minute per solve); one full solve is timed beside the steps.
     "deformed_hard_6x64x64_p2_k20_64dirs": dict(geometry="deformed", level_m=6, degree_p=2, kappa=20.0, bc=1,
-                                                cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
-                                                tol={"fp64": 1e-5, "mixed": 1e-5}, n_dir=100, n_rhs=64,
-                                                kappa_cap=6.0, restart=300, precond={"fp64": 0, "mixed": 0}),
+                                                cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2, "tc": 2},
+                                                tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=100, n_rhs=64,
+                                                kappa_cap=6.0, restart=300, precond={"fp64": 0, "mixed": 0, "tc": 0},
+                                                precision="tc", step="matvec"),
 }
 DEFAULT = "sphere_soft_6x32x32_p2_k8"
+PRECISIONS = {}                              # name -> igabem_precision (filled once the binding is loaded)
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # kernel sample arithmetic, see the design doc
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 FP64_PEAK_TFLOPS = 1.25                      # GB300 nominal FP64 (no measured figure available)
@@ -61,7 +71,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=64, help="serving_stream: requests in the stream")
     ap.add_argument("--rate", type=float, default=2.0, help="serving_stream: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving_stream: concurrent requests")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "tc"], default=None,
+                    help="fp64, mixed (FP32 far field) or tc (mixed with the tensor-core M2L); default: the "
+                         "workload's own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--one-form", action="store_true", help="time only --precision (no second form)")
     return ap.parse_args()
@@ -118,7 +130,7 @@ class Clocks:
 # ---------------------------------------------------------------------------------------------
 # the oracle on the host cores (bounded sample)
 
-def oracle_sample(wl, budget_s=20.0):
+def oracle_sample(wl, budget_s=20.0, with_lu=True):
     """Time the CPU oracle on a bounded sample of the workload and scale to solves/s.
 
     Sample: the exact Galerkin rows of `k` test elements against all 6144 trial elements (dense
@@ -147,10 +159,12 @@ def oracle_sample(wl, budget_s=20.0):
             break
     t_rows = (time.perf_counter() - t0) / k
     n = 1536
-    M = np.random.default_rng(0).standard_normal((n, n)) + 1j * np.random.default_rng(1).standard_normal((n, n))
-    t1 = time.perf_counter()
-    scipy.linalg.lu_factor(M)
-    t_lu = (time.perf_counter() - t1) * (sp.N / n) ** 3
+    t_lu = 0.0
+    if with_lu:
+        M = np.random.default_rng(0).standard_normal((n, n)) + 1j * np.random.default_rng(1).standard_normal((n, n))
+        t1 = time.perf_counter()
+        scipy.linalg.lu_factor(M)
+        t_lu = (time.perf_counter() - t1) * (sp.N / n) ** 3
     t_solve = t_rows * mesh.E + t_lu
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{k} of {mesh.E} element rows of the exact Galerkin matrix ({t_rows:.2f} s each, "
@@ -262,6 +276,118 @@ def run_serving(args):
         print(json.dumps(out))
 
 
+def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist):
+    """Workloads whose step is one operator application to all right-hand-side columns (64 for the
+    sound-hard deformed sphere): matvecs/s counts every column; one full solve is timed beside."""
+    import torch
+    R = wl["n_rhs"]
+    dirs = inputs.fibonacci_directions(R)
+    opt = options(args.precision)
+    prob = B.igabem_problem_create(geom, opt)
+    info = B.igabem_problem_info(prob)
+    N = info["n_dofs"]
+    x_host = inputs.random_complex(N, seed=2026, cols=R)
+    x = torch.tensor(x_host, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        B.igabem_matvec(prob, x, y)
+    B.igabem_profile_get(prob, reset=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            B.igabem_matvec(prob, x, y)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pr = B.igabem_profile_get(prob, reset=True)
+    phases = {k: round(v["ms"] / max(1, v["calls"]), 3) for k, v in pr["phases"].items() if v["calls"]}
+    m2l_ms = pr["phases"]["m2l"]["ms"] / max(1, pr["phases"]["m2l"]["calls"])
+    y_dev = y.cpu().numpy()
+    # end to end through the public API with host buffers (x in, y out every step)
+    ke = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        y_h = B.igabem_matvec(prob, x_host)
+    e2e_s = (time.perf_counter() - t0) / ke
+    # one full solve of the R directions and the far field
+    t0 = time.perf_counter()
+    dens, sinfo = B.igabem_solve(prob, dirs, N, raise_on_not_converged=False)
+    u = B.igabem_farfield(prob, dens, inputs.fibonacci_directions(wl["n_dir"]))
+    solve_s = time.perf_counter() - t0
+    B.igabem_problem_destroy(prob)
+    # the same product through the FP64 path (the accuracy of this precision), rank 0 only
+    err = None
+    if rank == 0 and args.precision != "fp64":
+        p64 = B.igabem_problem_create(geom, options("fp64"))
+        y64 = B.igabem_matvec(p64, x_host)
+        B.igabem_problem_destroy(p64)
+        err = float(np.abs(y_dev - y64).max() / np.abs(y64).max())
+    far = info["n_far_pairs"]
+    Q = wl["cheb_q"] ** 2
+    C = 7 if wl["bc"] else 1
+    useful = far * Q * Q * FLOPS_PER_MAC * C * R                    # complex contraction of the M2L
+    samples = far * Q * Q * FLOPS_PER_SAMPLE[bool(wl["bc"])] * (2 if wl["bc"] else 1)
+    achieved = (useful + samples) / (m2l_ms / 1e3) / 1e12
+    tc = args.precision == "tc"
+    peak = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+            if tc and os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else FP32_PEAK_TFLOPS)
+    kh = (Q + 7) // 8 * 8
+    executed = far * 3 * 2 * 128 * (2 * kh) * C * R                  # tensor-core flops issued (split, padding)
+    roofline = {"bound": "tensor" if tc else "alu", "kernel": "k_m2l_tc" if tc else "k_m2l_gemm<float>",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": ("measured dense BF16 burst (FP16 has the same tensor rate), MEASURED_PEAKS.json"
+                                if tc else "FP32 CUDA-core rate from unit counts and the maximum SM clock"),
+                "algorithmic_flops_per_matvec": useful + samples, "avg_ms_per_matvec": m2l_ms,
+                "executed_tensor_flops_per_matvec": executed if tc else None,
+                "executed_tensor_tflops": executed / (m2l_ms / 1e3) / 1e12 if tc else None}
+    value = R * args.steps * world / (total_ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "tc": "f16x2+f32+f64"}[args.precision],
+           "data": "synthetic (seeded deformed sphere, seeded complex vectors, Fibonacci directions)",
+           "config": {"workload": args.workload, "n_dofs": N, "n_elements": info["n_elements"], "n_rhs": R,
+                      "step": f"one operator application to {R} columns (counted as {R} matvecs)",
+                      "precision": args.precision, "cheb_q": wl["cheb_q"], "eta_adm": wl["eta_adm"],
+                      "kappa": wl["kappa"], "kappa_cap": wl["kappa_cap"], "leaf_offset": wl["leaf_offset"][args.precision],
+                      "n_far_pairs": far, "parallelism": f"replicas x{world}",
+                      "l2": "flushed (256 MB write) before each step"},
+           "phase_ms_per_matvec": phases, "setup_ms": info["setup_ms"],
+           "matvec_rel_err_vs_fp64": err,
+           "solve": {"gmres_iterations": sinfo["iterations"], "rel_residual": sinfo["rel_residual"],
+                     "gmres_restart": wl["restart"], "tol": wl["tol"][args.precision],
+                     "seconds": solve_s, "solves_per_s": 1.0 / solve_s, "n_dir": wl["n_dir"],
+                     "farfield_finite": bool(np.isfinite(u).all())},
+           "gpu_launches": pr["launches"] // max(1, args.steps) * args.steps,
+           "clocks": clk.summary(),
+           "e2e": {"value": R / e2e_s * world, "unit": "matvecs/s", "h2d_bytes_per_step": int(x_host.nbytes),
+                   "d2h_bytes_per_step": int(x_host.nbytes), "ms_per_step": 1e3 * e2e_s},
+           "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(wl, with_lu=False)
+        t_mv = 1.0 / cb["value"]
+        cb.update(value=R / t_mv, unit="matvecs/s",
+                  sample=cb["sample"] + f"; the oracle applies the operator by assembling it (no fast method), so "
+                                        f"one application to {R} columns costs one assembly")
+        out["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -281,6 +407,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.workload]
+    PRECISIONS.update(fp64=B.FP64, mixed=B.MIXED_FP32, tc=B.MIXED_TC)
+    if args.precision is None:
+        args.precision = wl["precision"]
     stream = torch.cuda.current_stream()
     ctx = B.igabem_create(local, stream.cuda_stream)
     patches = patches_of(wl["geometry"])
@@ -296,7 +425,7 @@ def main():
                                         eta_adm=wl["eta_adm"], leaf_offset=leaf, tol=wl["tol"][precision],
                                         kappa_cap=wl["kappa_cap"], gmres_restart=wl["restart"],
                                         max_iter=5000, precond=wl["precond"][precision],
-                                        precision=B.FP64 if precision == "fp64" else B.MIXED_FP32, profile=1)
+                                        precision=PRECISIONS[precision], profile=1)
 
     def request(opt, host=False):
         """One request through the public API; returns (problem, info, solve info, far field)."""
@@ -369,6 +498,8 @@ def main():
                 "prof": prof_tot, "u": u_last.cpu().numpy(), "clocks": clk.summary(),
                 "leaf_offset": wl["leaf_offset"][precision], "tol": wl["tol"][precision]}
 
+    if wl.get("step") == "matvec":
+        return run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist)
     main_form = run_form(args.precision, args.steps, args.warmup, True)
     other = "mixed" if args.precision == "fp64" else "fp64"
     other_form = run_form(other, max(1, min(args.steps, 3)), 1, False) if not args.one_form else None

@@ -102,6 +102,7 @@ typedef struct {
   size_t device_bytes;       /* device memory held by the problem */
   double setup_ms;           /* wall time of igabem_problem_create */
   double host_setup_ms;      /* of which host-side set-up (tree, lists, tables) */
+  long n_singular_points;    /* 4-D quadrature points of the touching pairs (Sec. 4.3 rules) */
 } igabem_info;
 
 typedef struct {
@@ -114,7 +115,7 @@ typedef struct {
 /* Phases of the per-problem profile. */
 enum {
   IGABEM_PH_SETUP_TABLES = 0,  /* geometry at Gauss points and interpolation nodes */
-  IGABEM_PH_SETUP_NEAR,        /* near-field Galerkin quadrature (regular and touching pairs) */
+  IGABEM_PH_SETUP_NEAR,        /* near-field Galerkin quadrature of the regular element pairs */
   IGABEM_PH_GATHER,            /* global <-> patch-wise / leaf-local vector gathers */
   IGABEM_PH_NEAR,              /* near-field block SpMV */
   IGABEM_PH_P2M,               /* leaf moments */
@@ -125,6 +126,7 @@ enum {
   IGABEM_PH_KRYLOV,            /* GMRES vector kernels */
   IGABEM_PH_RHS,               /* right-hand sides */
   IGABEM_PH_FARFIELD,          /* far-field pattern */
+  IGABEM_PH_SETUP_SINGULAR,    /* near-field Galerkin quadrature of the touching element pairs */
   IGABEM_NPHASE
 };
 

@@ -35,7 +35,7 @@ class igabem_info(ctypes.Structure):
     _fields_ = [("n_dofs", c_long), ("n_patch_dofs", c_long), ("n_elements", c_long),
                 ("n_clusters", c_long), ("n_near_pairs", c_long), ("n_near_element_pairs", c_long),
                 ("n_touching_pairs", c_long), ("n_far_pairs", c_long), ("device_bytes", c_size_t),
-                ("setup_ms", c_double), ("host_setup_ms", c_double)]
+                ("setup_ms", c_double), ("host_setup_ms", c_double), ("n_singular_points", c_long)]
 
 
 class igabem_solve_info(ctypes.Structure):
@@ -44,7 +44,7 @@ class igabem_solve_info(ctypes.Structure):
 
 
 PHASES = ["setup_tables", "setup_near", "gather", "near", "p2m", "m2m", "m2l", "l2l", "l2p", "krylov",
-          "rhs", "farfield"]
+          "rhs", "farfield", "setup_singular"]
 
 
 class igabem_profile(ctypes.Structure):

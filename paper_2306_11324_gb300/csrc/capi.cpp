@@ -289,6 +289,7 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
       total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
       total += bytes_of(S.lev[l].center);
       total += ((std::max<size_t>(S.lev[l].far_src.size(), 1) * 8 * sizeof(float)) + 255) & ~size_t(255);
+      total += ((size_t)S.lev[l].n * 2 * sizeof(double) + 255) & ~size_t(255);
     }
     const bool mixed = opt->precision != IGABEM_FP64;
     size_t blk_entries = S.near_src.size() * (size_t)S.nL * S.nL * 2;
@@ -303,10 +304,11 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
       total += 3 * (((nleaf + 1) * sizeof(int) + 255) & ~size_t(255));
     }
     total += 256;  // status word
+    total += bytes_of(S.nbr);
     if (S.n_far > 0 && leaf_moments_supported(S))
       total += ((leaf_moment_entries(S) * (mixed ? sizeof(float) : sizeof(double))) + 255) & ~size_t(255);
     P->arena_bytes = total + 4096;
-    P->temp_bytes = mixed ? blk_bytes : 0;
+    P->temp_bytes = (mixed ? blk_bytes : 0) + near_table_bytes(S, *opt);
   } catch (...) {
     delete P;
     throw;
@@ -362,6 +364,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   d.touch = upload(A, S.touch, st);
   d.touch_blk = upload(A, S.touch_blk, st);
   d.sing = upload(A, S.sing, st);
+  d.nbr = upload(A, S.nbr, st);
   d.x2g = upload(A, S.x2g, st);
   d.g2x_ptr = upload(A, S.g2x_ptr, st);
   d.g2x_idx = upload(A, S.g2x_idx, st);
@@ -377,6 +380,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   d.nodes32.assign(S.L + 1, nullptr);
   d.centers.assign(S.L + 1, nullptr);
   d.pairc.assign(S.L + 1, nullptr);
+  d.cext.assign(S.L + 1, nullptr);
   for (int l = 0; l <= S.L; ++l) {
     d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
     d.far_src[l] = upload(A, S.lev[l].far_src, st);
@@ -384,6 +388,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     d.nodes32[l] = A.get<float>((size_t)7 * S.lev[l].n * Q);
     d.centers[l] = upload(A, S.lev[l].center, st);
     d.pairc[l] = A.get<float>(std::max<size_t>(S.lev[l].far_src.size(), 1) * 8);
+    d.cext[l] = A.get<double>((size_t)S.lev[l].n * 2);
   }
   double *blk_tmp = nullptr;
   if (mixed) {
@@ -394,6 +399,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     d.blk = A.get<double>(blk_entries);
   }
   IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
+  IGA_CUDA(cudaMalloc(&d.near_tab, std::max<size_t>(near_table_bytes(S, *opt), 256)));
   launch_gauss_geometry(d, S, st);
   launch_node_geometry(d, S, cheb, st);
   if (S.n_far > 0 && leaf_moments_supported(S)) {
@@ -430,6 +436,8 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     d.blk = nullptr;
   }
   IGA_CUDA(cudaStreamSynchronize(st));
+  IGA_CUDA(cudaFree(d.near_tab));
+  d.near_tab = nullptr;
   IGA_CUDA(cudaGetLastError());
   P->prof.flush();
   igabem_info &I = P->info;
@@ -443,6 +451,11 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   I.n_near_element_pairs = I.n_near_pairs << (4 * S.b);
   I.n_touching_pairs = (long)S.touch.size() / 5;
   I.n_far_pairs = S.n_far;
+  I.n_singular_points = 0;
+  for (size_t i = 0; i + 6 < S.sing.size(); i += 7) {
+    const int kind = S.sing[i + 2];
+    I.n_singular_points += kind == 0 ? (long)S.r_id.w.size() : (kind == 2 ? (long)S.r_edge.w.size() : (long)S.r_vert.w.size());
+  }
   I.device_bytes = A.cap;
   I.setup_ms = now_ms() - P->t_plan;
 }

@@ -568,6 +568,20 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
 
   // touching pair -> near block
   int npt = (int)S.touch.size() / 5;
+  {  // neighbour lists of the touching pairs (both directions), for the regular near-field kernel
+    std::vector<std::vector<int>> nb(S.E);
+    for (int i = 0; i < npt; ++i) {
+      const int e = S.touch[5 * i], f = S.touch[5 * i + 1];
+      if (e == f) continue;
+      nb[e].push_back(f);
+      nb[f].push_back(e);
+    }
+    S.nbr_w = 1;
+    for (auto &v : nb) S.nbr_w = std::max<int>(S.nbr_w, (int)v.size());
+    S.nbr.assign((size_t)S.E * S.nbr_w, -1);
+    for (int e = 0; e < S.E; ++e)
+      for (size_t c = 0; c < nb[e].size(); ++c) S.nbr[(size_t)e * S.nbr_w + c] = nb[e][c];
+  }
   S.touch_blk.resize(npt);
   const int nlL = 1 << S.L, bsh = S.b;
   auto leaf_of = [&](int e) {

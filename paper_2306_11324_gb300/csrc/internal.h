@@ -106,6 +106,8 @@ struct HostSetup {
   std::vector<TreeLevel> lev;
   std::vector<int> near_ptr, near_src; // near leaf pairs, CSR by target leaf
   std::vector<int> touch_blk;          // per touching pair: index of its near leaf pair
+  std::vector<int> nbr;                // [E][nbr_w]: elements touching each element (-1 padded)
+  int nbr_w = 1;
   // work list of the singular quadrature: each unordered touching pair once,
   // (e, f, kind, Te, Tf, block of (e,f), block of (f,e) or -1 for identical pairs)
   std::vector<int> sing;
@@ -185,6 +187,8 @@ struct DeviceProblem {
   int rule_n[3];
   double *corners;
   int *touch, *touch_blk, *sing;
+  int *nbr = nullptr;                        // [E][nbr_w] touching elements
+  void *near_tab = nullptr;                  // set-up scratch: element tables of the regular quadrature
   int *x2g, *g2x_ptr, *g2x_idx;
   // tree
   int *near_ptr, *near_src, *near_tgt;
@@ -193,6 +197,7 @@ struct DeviceProblem {
   std::vector<float *> nodes32;              // per level: [7][n*q*q] (x - centre, n~, a) in FP32
   std::vector<double *> centers;             // per level: [n][3] cluster centres
   std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
+  std::vector<double *> cext;                // per level: [n][2] node extent and largest Jacobian
   std::vector<uint8_t *> tc_bimg;            // per level: tensor-core M2L operands of the sources
   std::vector<float *> tc_bscale;            // per level: power-of-two scale of each cluster's operand
   int *status = nullptr;                     // device status word: non-zero after a timed-out wait

@@ -308,10 +308,13 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(M2LArgs A, int Wc) {
 // with rho the largest node distance from the cluster centre and a_max the largest Jacobian,
 // |x - y| lies in [|D| - rho_t - rho_s, |D| + rho_t + rho_s] and every kernel type is at most
 // (1 + kappa r_hi)(1 + a_t)(1 + a_s)(1 + |eta|) / (4 pi r_lo).
-__device__ inline void node_extent(const double *__restrict__ nodes, const double *__restrict__ center, long NQ,
-                                   int Q, int c, double &rho, double &amax) {
-  rho = 0.0;
-  amax = 0.0;
+// per cluster: rho = the largest node distance from the centre, a_max = the largest node Jacobian
+__global__ void k_cluster_extent(const double *__restrict__ nodes, const double *__restrict__ center, int n, int Q,
+                                 double2 *__restrict__ ext) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const long NQ = (long)n * Q;
+  double rho = 0.0, amax = 0.0;
   for (int a = 0; a < Q; ++a) {
     const long i = (long)c * Q + a;
     const double dx = nodes[i] - center[3 * c], dy = nodes[NQ + i] - center[3 * c + 1],
@@ -319,32 +322,34 @@ __device__ inline void node_extent(const double *__restrict__ nodes, const doubl
     rho = fmax(rho, sqrt(dx * dx + dy * dy + dz * dz));
     amax = fmax(amax, nodes[6 * NQ + i]);
   }
+  ext[c] = make_double2(rho, amax);
 }
 
+// one thread per admissible pair k (CSR order), its target t from the row pointers
 __global__ void k_pair_consts(const int *__restrict__ far_ptr, const int *__restrict__ far_src,
-                              const double *__restrict__ center, const double *__restrict__ nodes, int n, int Q,
+                              const double *__restrict__ center, const double2 *__restrict__ ext, int n, long nfar,
                               double kappa, double eta, float *__restrict__ pc) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const long NQ = (long)n * Q;
-  double rho_t, a_t;
-  node_extent(nodes, center, NQ, Q, t, rho_t, a_t);
-  for (int k = far_ptr[t]; k < far_ptr[t + 1]; ++k) {
-    int s = far_src[k];
-    double D[3] = {center[3 * t] - center[3 * s], center[3 * t + 1] - center[3 * s + 1],
-                   center[3 * t + 2] - center[3 * s + 2]};
-    double nD = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-    double sn, cs;
-    sincos(fmod(kappa * nD, TWO_PI), &sn, &cs);
-    double rho_s, a_s;
-    node_extent(nodes, center, NQ, Q, s, rho_s, a_s);
-    const double r_lo = fmax(nD - rho_t - rho_s, 1e-3 * nD), r_hi = nD + rho_t + rho_s;
-    const double bound = (1.0 + kappa * r_hi) * (1.0 + a_t) * (1.0 + a_s) * (1.0 + fabs(eta)) / (4.0 * IGA_PI * r_lo);
-    float *o = pc + 8L * k;
-    o[0] = (float)D[0]; o[1] = (float)D[1]; o[2] = (float)D[2]; o[3] = (float)nD;
-    o[4] = (float)(nD * nD); o[5] = (float)cs; o[6] = (float)sn;
-    o[7] = (float)exp2(12.0 - ceil(log2(bound)));
+  const long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k >= nfar) return;
+  int lo = 0, hi = n;  // t with far_ptr[t] <= k < far_ptr[t + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (far_ptr[mid] <= k) lo = mid;
+    else hi = mid;
   }
+  const int t = lo, s = far_src[k];
+  double D[3] = {center[3 * t] - center[3 * s], center[3 * t + 1] - center[3 * s + 1],
+                 center[3 * t + 2] - center[3 * s + 2]};
+  double nD = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+  double sn, cs;
+  sincos(fmod(kappa * nD, TWO_PI), &sn, &cs);
+  const double2 et = ext[t], es = ext[s];
+  const double r_lo = fmax(nD - et.x - es.x, 1e-3 * nD), r_hi = nD + et.x + es.x;
+  const double bound = (1.0 + kappa * r_hi) * (1.0 + et.y) * (1.0 + es.y) * (1.0 + fabs(eta)) / (4.0 * IGA_PI * r_lo);
+  float *o = pc + 8L * k;
+  o[0] = (float)D[0]; o[1] = (float)D[1]; o[2] = (float)D[2]; o[3] = (float)nD;
+  o[4] = (float)(nD * nD); o[5] = (float)cs; o[6] = (float)sn;
+  o[7] = (float)exp2(12.0 - ceil(log2(bound)));
 }
 
 template <class T, int NCR, bool HARD>
@@ -377,8 +382,14 @@ void launch_typed(const M2LArgs &A, int nblocks, cudaStream_t st) {
 void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, double eta, cudaStream_t st) {
   for (int l = S.lmin; l <= S.L; ++l) {
     int n = S.lev[l].n;
-    k_pair_consts<<<(n + 127) / 128, 128, 0, st>>>(d.far_ptr[l], d.far_src[l], d.centers[l], d.nodes[l], n,
-                                                   S.q * S.q, kappa, eta, d.pairc[l]);
+    const long nfar = (long)S.lev[l].far_src.size();
+    k_cluster_extent<<<(n + 127) / 128, 128, 0, st>>>(d.nodes[l], d.centers[l], n, S.q * S.q,
+                                                      reinterpret_cast<double2 *>(d.cext[l]));
+    note_launch();
+    if (nfar == 0) continue;
+    k_pair_consts<<<(int)((nfar + 255) / 256), 256, 0, st>>>(d.far_ptr[l], d.far_src[l], d.centers[l],
+                                                             reinterpret_cast<const double2 *>(d.cext[l]), n, nfar,
+                                                             kappa, eta, d.pairc[l]);
     note_launch();
   }
   IGA_CUDA(cudaGetLastError());

@@ -180,6 +180,11 @@ struct NearArgs {
   double h, kappa, eta, tol;
   bool hard;
   double2 *blk;
+  // per-element tables of the regular quadrature (precision of the kernel): Gauss-point geometry
+  // [E][nq][7] (x, n~, a), weighted basis values [E][nq][nloc], weighted curls [E][nq][nloc][3]
+  const void *tab_pts, *tab_phw, *tab_cuw;
+  const int *nbr;  // [E][nbr_w]: the elements touching each element (-1 padded)
+  int nbr_w;
 };
 
 __device__ inline int leaf_local(int ix, int iy, int ka, int kb, int b, int nL1) {
@@ -209,14 +214,40 @@ __device__ inline void curl_gp(const NearArgs &A, long iq, double ds, double dt,
     c[d] = ds * A.gft[d * A.gstride + iq] - dt * A.gfs[d * A.gstride + iq];
 }
 
+// e and f share a point (the pair is integrated by k_near_singular): the neighbour list of e
 __device__ inline bool touching(const NearArgs &A, int e, int f) {
   if (e == f) return true;
-  for (int c = 0; c < 16; ++c) {
-    const double *pa = A.corners + (e * 4 + (c >> 2)) * 3, *pb = A.corners + (f * 4 + (c & 3)) * 3;
-    double dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
-    if (sqrt(dx * dx + dy * dy + dz * dz) <= A.tol) return true;
-  }
+  for (int c = 0; c < A.nbr_w; ++c)
+    if (A.nbr[(long)e * A.nbr_w + c] == f) return true;
   return false;
+}
+
+// The per-element tables of the regular quadrature in precision T (one thread per Gauss point):
+// they depend on the element alone, so every element pair reads them instead of re-evaluating the
+// B-splines and curls.
+template <class T>
+__global__ void k_elem_tables(NearArgs A, long n_gp, T *__restrict__ pts, T *__restrict__ phw, T *__restrict__ cuw) {
+  const int nq = A.ng * A.ng, nloc = A.nloc;
+  for (long iq = blockIdx.x * (long)blockDim.x + threadIdx.x; iq < n_gp; iq += (long)gridDim.x * blockDim.x) {
+    const long e = iq / nq;
+    const int q = (int)(iq % nq), ix = (int)((e / A.n1) % A.n1), iy = (int)(e % A.n1);
+    for (int c = 0; c < 3; ++c) {
+      pts[iq * 7 + c] = (T)A.gpx[c * A.gstride + iq];
+      pts[iq * 7 + 3 + c] = (T)A.gpn[c * A.gstride + iq];
+    }
+    pts[iq * 7 + 6] = (T)A.gpa[iq];
+    const double w = A.gw[q / A.ng] * A.gw[q % A.ng];
+    for (int k = 0; k < nloc; ++k) {
+      double v, ds, dt;
+      basis_gp(A, ix, iy, k, q, v, ds, dt);
+      phw[iq * nloc + k] = (T)(v * w);
+      if (A.hard) {
+        double c[3];
+        curl_gp(A, iq, ds, dt, c);
+        for (int d = 0; d < 3; ++d) cuw[(iq * nloc + k) * 3 + d] = (T)(c[d] * w);
+      }
+    }
+  }
 }
 
 // One block of threads per near leaf pair, one warp per element pair (touching pairs skipped:
@@ -249,7 +280,8 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
     for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) Bs[i] = make_double2(0, 0);
     __syncthreads();
   }
-  const long st = A.gstride;
+  const T *tpts = static_cast<const T *>(A.tab_pts), *tphw = static_cast<const T *>(A.tab_phw),
+          *tcuw = static_cast<const T *>(A.tab_cuw);
   const T h2 = (T)(A.h * A.h), kap = (T)A.kappa, eta = (T)A.eta;
   const int npair = ne1 * ne1 * ne1 * ne1;
   for (int pr = warp; pr < npair; pr += nwarp) {
@@ -258,29 +290,18 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
     int ixf = cxs * ne1 + es / ne1, iyf = cys * ne1 + es % ne1;
     int e = (jt * A.n1 + ixe) * A.n1 + iye, f = (js * A.n1 + ixf) * A.n1 + iyf;
     if (touching(A, e, f)) continue;  // warp-uniform
-    // stage the Gauss points (x, n~, a) and the weighted basis values / curls of both elements
-    for (int i = lane; i < 2 * nq; i += 32) {
-      int side = i / nq, q = i % nq;
-      long iq = (long)(side ? f : e) * nq + q;
-      T *o = pts + (side * nq + q) * 7;
-      for (int c = 0; c < 3; ++c) {
-        o[c] = (T)A.gpx[c * st + iq];
-        o[3 + c] = (T)A.gpn[c * st + iq];
-      }
-      o[6] = (T)A.gpa[iq];
+    // stage the Gauss points (x, n~, a) and the weighted basis values / curls of both elements from the
+    // element tables
+    for (int i = lane; i < 2 * nq * 7; i += 32) {
+      const int side = i / (nq * 7), r = i % (nq * 7);
+      pts[i] = tpts[(long)(side ? f : e) * nq * 7 + r];
     }
     for (int i = lane; i < 2 * nq * nloc; i += 32) {
-      int side = i / (nq * nloc), q = (i / nloc) % nq, k = i % nloc;
-      int ix = side ? ixf : ixe, iy = side ? iyf : iye, el = side ? f : e;
-      double v, ds, dt;
-      basis_gp(A, ix, iy, k, q, v, ds, dt);
-      double w = A.gw[q / A.ng] * A.gw[q % A.ng];
-      (side ? phf : phe)[q * nloc + k] = (T)(v * w);
-      if (A.hard) {
-        double c[3];
-        curl_gp(A, (long)el * nq + q, ds, dt, c);
-        for (int d = 0; d < 3; ++d) (side ? cuf : cue)[(q * nloc + k) * 3 + d] = (T)(c[d] * w);
-      }
+      const int side = i / (nq * nloc), r = i % (nq * nloc);
+      const long el = side ? f : e;
+      (side ? phf : phe)[r] = tphw[el * nq * nloc + r];
+      if (A.hard)
+        for (int d = 0; d < 3; ++d) (side ? cuf : cue)[r * 3 + d] = tcuw[(el * nq * nloc + r) * 3 + d];
     }
     __syncwarp();
     for (int i = lane; i < nq * nq; i += 32) {
@@ -539,18 +560,44 @@ static NearArgs near_args(const DeviceProblem &d, const HostSetup &S, const igab
   A.L = S.L; A.h = S.h; A.kappa = o.kappa; A.eta = o.eta_cfie; A.tol = 1e-10 * S.scale;
   A.hard = S.hard;
   A.blk = reinterpret_cast<double2 *>(d.blk);
+  A.tab_pts = A.tab_phw = A.tab_cuw = nullptr;
+  A.nbr = d.nbr;
+  A.nbr_w = S.nbr_w;
   return A;
+}
+
+size_t near_table_bytes(const HostSetup &S, const igabem_options &o) {
+  const size_t tsz = o.precision != IGABEM_FP64 ? sizeof(float) : sizeof(double);
+  const size_t ngp = (size_t)S.E * S.ng * S.ng;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(ngp * 7 * tsz) + al(ngp * S.nloc * tsz) + (S.hard ? al(ngp * S.nloc * 3 * tsz) : 0);
 }
 
 void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,
                        cudaStream_t st) {
-  Phase ph(d.prof, IGABEM_PH_SETUP_NEAR, st);
   NearArgs A = near_args(d, S, o);
   int nblk = (int)S.near_src.size();
   if (nblk > 0) {
+    Phase ph(d.prof, IGABEM_PH_SETUP_NEAR, st);
     const int nq = S.ng * S.ng, nloc = S.nloc;
     const bool f32 = o.precision != IGABEM_FP64;
     const size_t tsz = f32 ? sizeof(float) : sizeof(double);
+    // the element tables, in the scratch buffer given with the problem (near_table_bytes)
+    {
+      const long ngp = (long)S.E * nq;
+      auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+      uint8_t *tb = static_cast<uint8_t *>(d.near_tab);
+      A.tab_pts = tb;
+      A.tab_phw = tb + al(ngp * 7 * tsz);
+      A.tab_cuw = tb + al(ngp * 7 * tsz) + al(ngp * nloc * tsz);
+      const int grid = (int)std::min<long>((ngp + 255) / 256, 152L * 16);
+      if (f32)
+        k_elem_tables<float><<<grid, 256, 0, st>>>(A, ngp, (float *)A.tab_pts, (float *)A.tab_phw, (float *)A.tab_cuw);
+      else
+        k_elem_tables<double><<<grid, 256, 0, st>>>(A, ngp, (double *)A.tab_pts, (double *)A.tab_phw,
+                                                    (double *)A.tab_cuw);
+      note_launch();
+    }
     const size_t per = (size_t)(2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc +
                                 6 * nq * nloc) * tsz;
     const size_t bsm = (size_t)S.nL * S.nL * sizeof(double2);
@@ -568,6 +615,7 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
     note_launch();
     IGA_CUDA(cudaGetLastError());
   }
+  Phase ph(d.prof, IGABEM_PH_SETUP_SINGULAR, st);
   SingArgs SA;
   SA.A = A;
   SA.sing = d.sing;

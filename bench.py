@@ -213,6 +213,21 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------------------------
 
+def replica_share(items, rank, world):
+    """The units of work of one rank: replicas deal whole requests round-robin (no data-path exchange)."""
+    return items[rank::world]
+
+
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def serving_requests(n, seed=0):
     """The serving stream: n requests, each a seeded deformed sphere with 16x16 .. 64x64 elements per
     patch, kappa ~ U[1, 30] rejected until there are >= 8 degree-2 unknowns per wavelength
@@ -242,7 +257,7 @@ def run_serving(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
-    reqs = serving_requests(args.requests)[rank::world]        # replicas: requests dealt to the ranks
+    reqs = replica_share(serving_requests(args.requests), rank, world)
     ctx = B.igabem_create(local, None)
     xhat = inputs.fibonacci_directions(100)
     geoms = {}
@@ -322,11 +337,7 @@ def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, w
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist)
     pr = B.igabem_profile_get(prob, reset=True)
     phases = {k: round(v["ms"] / max(1, v["calls"]), 3) for k, v in pr["phases"].items() if v["calls"]}
     m2l_ms = pr["phases"]["m2l"]["ms"] / max(1, pr["phases"]["m2l"]["calls"])
@@ -485,11 +496,7 @@ def main():
         if dist:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-        total_ms = sum(step_ms)
-        if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(step_ms), dist)
         # operator applications on a resident problem
         prob = B.igabem_problem_create(geom, opt)
         info = B.igabem_problem_info(prob)

@@ -66,12 +66,14 @@ def singular_flops_per_point(p, hard, pg=4):
     k_near_singular): both elements' rational Bezier geometry of degree pg (homogeneous rows with their
     v-derivatives, then the columns with value, d/du, d/dv; normal and Jacobian), the kernel (distance,
     sincos, G, G'/r and the weights), both elements' (p+1)^2 B-splines by Bernstein extraction (and their
-    surface curls for sound-hard), and the accumulation of the (p+1)^2 x (p+1)^2 block, the transposed
-    block of a common-edge or common-vertex pair taken from the same points."""
+    surface curls for sound-hard), the kernel value times the test functions (w k psi_k, also for the
+    transposed block of a common-edge or common-vertex pair taken from the same points) and the
+    accumulation of the (p+1)^2 x (p+1)^2 blocks (one complex-by-real multiply-add per entry and block;
+    sound-hard adds the curl product G c_k . c_l)."""
     n = (p + 1) ** 2
     geo = 2 * (2 * (pg + 1) ** 2 * 4 * 2 + (pg + 1) * 4 * 3 * 2 + 30)
-    basis = 2 * (5 * n + (6 * n if hard else 0))
-    acc = n * n * (5 + (9 if hard else 0)) * 2
+    basis = 2 * (5 * n + (6 * n if hard else 0)) + 2 * 4 * n
+    acc = n * n * (2 * 4 + (5 + 8 if hard else 0))
     return geo + basis + 60 + acc
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 

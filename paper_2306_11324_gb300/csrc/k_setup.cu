@@ -424,6 +424,44 @@ __device__ inline void basis_curl_at(const NearArgs &A, int ix, int iy, double u
 constexpr int SING_CHUNK = 128;  // one point per thread
 constexpr int SING_MAXACC = 19;  // (p+1)^4 / 128 rounded up for p <= 6
 
+// The nloc local functions at local point (u, v) of element column (ix, iy), each times the complex
+// weights s1 (into o1) and, when o2 != nullptr, s2 (into o2); with curl != nullptr also the curls as in
+// basis_curl_at.  Folding the kernel value into the test side leaves two multiply-adds per block entry
+// and point in the accumulation.
+__device__ inline void basis_scaled_at(const NearArgs &A, int ix, int iy, double u, double v, const double *fs,
+                                       const double *ft, double2 s1, double2 s2, double2 *o1, double2 *o2,
+                                       double *curl) {
+  const int p = A.p, p1 = p + 1;
+  double Bu[8], dBu[8], Bv[8], dBv[8];
+  bernstein_all(p, u, Bu, curl ? dBu : nullptr);
+  bernstein_all(p, v, Bv, curl ? dBv : nullptr);
+  double fu[8], dfu[8], fv[8], dfv[8];
+  for (int a = 0; a <= p; ++a) {
+    double s0 = 0, s1u = 0, t0 = 0, t1 = 0;
+    for (int c = 0; c <= p; ++c) {
+      double ea = A.ext1[(ix * p1 + a) * p1 + c], eb = A.ext1[(iy * p1 + a) * p1 + c];
+      s0 += ea * Bu[c];
+      t0 += eb * Bv[c];
+      if (curl) {
+        s1u += ea * dBu[c];
+        t1 += eb * dBv[c];
+      }
+    }
+    fu[a] = s0; fv[a] = t0; dfu[a] = s1u * A.n1; dfv[a] = t1 * A.n1;
+  }
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= p; ++b) {
+      const int k = a * p1 + b;
+      const double val = fu[a] * fv[b];
+      o1[k] = cscale(s1, val);
+      if (o2) o2[k] = cscale(s2, val);
+      if (curl) {
+        const double ds = dfu[a] * fv[b], dt = fu[a] * dfv[b];
+        for (int d = 0; d < 3; ++d) curl[k * 3 + d] = ds * ft[d] - dt * fs[d];
+      }
+    }
+}
+
 // One block per unordered touching pair.  Points of the regularising rule of the pair's kind, mapped
 // by the canonical square symmetries; for edge and vertex pairs the same points also give the block
 // of (f, e) with the roles of x and y exchanged (the rules are symmetric under that exchange).
@@ -432,11 +470,12 @@ __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;
   extern __shared__ double smd[];
   const int nloc = A.nloc, p1 = A.p + 1;
-  // shared: ks[C], kb[C], gc[C] (complex), phx[C][nloc], phy[C][nloc], cx[C][nloc][3], cy[C][nloc][3]
-  double2 *ks = reinterpret_cast<double2 *>(smd), *kb = ks + SING_CHUNK, *gc = kb + SING_CHUNK;
-  double *phx = reinterpret_cast<double *>(gc + SING_CHUNK), *phy = phx + SING_CHUNK * nloc;
-  double *cxs = phy + SING_CHUNK * nloc, *cys = cxs + 3 * SING_CHUNK * nloc;
-  double *net_e = cys + 3 * SING_CHUNK * nloc, *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
+  // shared: Ax[C][nloc], Bx[C][nloc] (complex: w k(x,y) psi_k(x) and w k(y,x) psi_k(x)), gc[C] (complex),
+  // phy[C][nloc], and for sound-hard cx[C][nloc][3], cy[C][nloc][3]
+  double2 *Ax = reinterpret_cast<double2 *>(smd), *Bx = Ax + SING_CHUNK * nloc, *gc = Bx + SING_CHUNK * nloc;
+  double *phy = reinterpret_cast<double *>(gc + SING_CHUNK);
+  double *cxs = phy + SING_CHUNK * nloc, *cys = cxs + (A.hard ? 3 * SING_CHUNK * nloc : 0);
+  double *net_e = cys + (A.hard ? 3 * SING_CHUNK * nloc : 0), *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
   const int *W = S.sing + 7 * blockIdx.x;
   const int e = W[0], f = W[1], kind = W[2], te = W[3], tf = W[4], blk_ef = W[5], blk_fe = W[6];
   const bool both = blk_fe >= 0;
@@ -474,10 +513,9 @@ __global__ void k_near_singular(SingArgs S) {
       PairKernel pk;
       double2 kyx;
       cfie_kernel_both(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay, pk, kyx);
-      ks[t] = cscale(pk.ks, w);
       gc[t] = cscale(pk.gc, w);  // gc(y, x) = gc(x, y)
-      kb[t] = cscale(kyx, w);
-      basis_curl_at(A, ixe, iye, ue, ve, fs, ft, phx + t * nloc, A.hard ? cxs + t * nloc * 3 : nullptr);
+      basis_scaled_at(A, ixe, iye, ue, ve, fs, ft, cscale(pk.ks, w), cscale(kyx, w), Ax + t * nloc,
+                      both ? Bx + t * nloc : nullptr, A.hard ? cxs + t * nloc * 3 : nullptr);
       basis_curl_at(A, ixf, iyf, uf, vf, gs, gt, phy + t * nloc, A.hard ? cys + t * nloc * 3 : nullptr);
     }
     __syncthreads();
@@ -487,15 +525,36 @@ __global__ void k_near_singular(SingArgs S) {
       if (i >= nloc * nloc) break;
       const int k = i / nloc, l = i % nloc;
       double2 a = acc[slot], b = accb[slot];
-      for (int t = 0; t < cn; ++t) {
-        const double P = phx[t * nloc + k] * phy[t * nloc + l];
-        double2 g = cmk(0, 0);
-        if (A.hard) {
+      if (A.hard) {
+        for (int t = 0; t < cn; ++t) {
+          const double py = phy[t * nloc + l];
           const double *ck = cxs + (t * nloc + k) * 3, *cl = cys + (t * nloc + l) * 3;
-          g = cscale(gc[t], ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2]);
+          const double dot = ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2];
+          const double2 g = gc[t], ax = Ax[t * nloc + k];
+          a.x = fma(ax.x, py, fma(g.x, dot, a.x));
+          a.y = fma(ax.y, py, fma(g.y, dot, a.y));
+          if (both) {
+            const double2 bx = Bx[t * nloc + k];
+            b.x = fma(bx.x, py, fma(g.x, dot, b.x));
+            b.y = fma(bx.y, py, fma(g.y, dot, b.y));
+          }
         }
-        a = cadd(a, cadd(cscale(ks[t], P), g));
-        if (both) b = cadd(b, cadd(cscale(kb[t], P), g));
+      } else if (both) {
+        for (int t = 0; t < cn; ++t) {
+          const double py = phy[t * nloc + l];
+          const double2 ax = Ax[t * nloc + k], bx = Bx[t * nloc + k];
+          a.x = fma(ax.x, py, a.x);
+          a.y = fma(ax.y, py, a.y);
+          b.x = fma(bx.x, py, b.x);
+          b.y = fma(bx.y, py, b.y);
+        }
+      } else {
+        for (int t = 0; t < cn; ++t) {
+          const double py = phy[t * nloc + l];
+          const double2 ax = Ax[t * nloc + k];
+          a.x = fma(ax.x, py, a.x);
+          a.y = fma(ax.y, py, a.y);
+        }
       }
       acc[slot] = a;
       accb[slot] = b;
@@ -625,7 +684,8 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   }
   const int nsing = (int)S.sing.size() / 7;
   if (S.nloc * S.nloc > SING_MAXACC * 128) fail(IGABEM_EINVAL, "degree_p too large for the singular kernel");
-  const size_t smem = ((size_t)SING_CHUNK * (6 + 8 * S.nloc) + 8 * 49) * sizeof(double);
+  const size_t smem =
+      ((size_t)SING_CHUNK * (2 + 5 * S.nloc + (S.hard ? 6 * S.nloc : 0)) + 8 * 49) * sizeof(double);
   const int nslot = (S.nloc * S.nloc + 127) / 128;
   auto go = [&](auto kfn) {
     IGA_CUDA(set_max_dynamic_smem(kfn, smem));

@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=64, help="serving_stream: requests in the stream")
     ap.add_argument("--rate", type=float, default=2.0, help="serving_stream: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving_stream: concurrent requests")
+    ap.add_argument("--max-iter", type=int, default=1000, help="serving_stream: GMRES iterations per request")
     ap.add_argument("--precision", choices=["fp64", "mixed", "tc"], default=None,
                     help="fp64, mixed (FP32 far field) or tc (mixed with the tensor-core M2L); default: the "
                          "workload's own")
@@ -270,10 +271,12 @@ def run_serving(args):
         return geoms[seed]
 
     def opt(r):
-        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload)
+        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload); the
+        # tensor-core M2L where the direction count allows it (multiples of 16), FP32 otherwise.  A request
+        # that has not reached the tolerance after max_iter iterations is reported as failed.
         return B.igabem_default_options(level_m=r["m"], degree_p=2, kappa=r["kappa"], eta_cfie=r["kappa"],
                                         bc=r["bc"], cheb_q=7, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
-                                        precision=B.MIXED_FP32, tol=1e-5, max_iter=5000,
+                                        precision=B.MIXED_TC, tol=1e-5, max_iter=args.max_iter,
                                         gmres_restart=300 if r["bc"] else 30, precond=0 if r["bc"] else 1)
     for r in reqs:
         geom(r["geom_seed"])
@@ -299,7 +302,8 @@ def run_serving(args):
            "warmup": 0, "ms_per_step": 1e3 * wall / max(1, len(reqs)), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded deformed spheres, Poisson arrivals)",
            "config": {"workload": "serving_stream", "requests": len(reqs), "arrival_rate_per_s": args.rate,
-                      "slots": args.slots, "precision": "mixed", "tol": 1e-5},
+                      "slots": args.slots, "precision": "tc (R a multiple of 16) / mixed", "tol": 1e-5,
+                      "max_iter": args.max_iter},
            "solve_latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
            "completed": st["completed"], "failed": st["failed"], "peak_active": st["peak_active"],
            "peak_bytes": st["peak_bytes"], "statuses": sorted(set(status)), "clocks": clk.summary(),

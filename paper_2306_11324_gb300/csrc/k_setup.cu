@@ -1,5 +1,7 @@
 // Set-up kernels: geometry tables at Gauss points and interpolation nodes, and the near-field
 // Galerkin blocks (Sec. 4.2-4.3 with the quadrature rules for regular and touching element pairs).
+#include <type_traits>
+
 #include "internal.h"
 #include "k_common.cuh"
 #include "kernels.h"
@@ -250,6 +252,11 @@ __global__ void k_elem_tables(NearArgs A, long n_gp, T *__restrict__ pts, T *__r
   }
 }
 
+// per-warp scratch of k_near_regular_t, in elements of its precision
+__host__ __device__ inline int near_regular_scratch(int nq, int nloc, bool hard) {
+  return 2 * nq * 7 + 2 * nq * nloc + 2 * nq * nq + 2 * nq * nloc + (hard ? 6 * nq * nloc + 2 * nq * nq + 6 * nq * nloc : 0);
+}
+
 // One block of threads per near leaf pair, one warp per element pair (touching pairs skipped:
 // k_near_singular integrates them).  Block entry (k of e, l of f) +=
 //   sum_{q,r} w_q w_r h^4 [ks(q,r) psi_k(q) psi_l(r) + gc(q,r) c_k(q) . c_l(r)],
@@ -260,16 +267,18 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
   extern __shared__ __align__(16) unsigned char smr[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int nq = A.ng * A.ng, nloc = A.nloc, p1 = A.p + 1;
-  // per-warp scratch (T): pts[2][nq][7], phi[2][nq][nloc], curl[2][nq][nloc][3], ks/gc[nq*nq][2 each],
-  // Tm[nq][nloc][2], Tc[3][nq][nloc][2]
-  const int per = 2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc + 6 * nq * nloc;
-  double2 *Bs = reinterpret_cast<double2 *>(smr);
-  T *base = reinterpret_cast<T *>(smr + (smem_block ? (size_t)A.nL * A.nL * sizeof(double2) : 0));
+  // per-warp scratch (T): pts[2][nq][7], phi[2][nq][nloc], ks[nq*nq][2], Tm[nq][nloc][2], and for
+  // sound-hard curl[2][nq][nloc][3], gc[nq*nq][2], Tc[3][nq][nloc][2] (near_regular_scratch)
+  using BA = typename std::conditional<sizeof(T) == 4, float2, double2>::type;  // leaf-pair block sums
+  const int hc = A.hard ? 1 : 0;
+  const int per = near_regular_scratch(nq, nloc, A.hard);
+  BA *Bs = reinterpret_cast<BA *>(smr);
+  T *base = reinterpret_cast<T *>(smr + (smem_block ? (size_t)A.nL * A.nL * sizeof(BA) : 0));
   T *pts = base + warp * per;
   T *phe = pts + 2 * nq * 7, *phf = phe + nq * nloc;
-  T *cue = phf + nq * nloc, *cuf = cue + 3 * nq * nloc;
-  T *ks = cuf + 3 * nq * nloc, *gc = ks + 2 * nq * nq;
-  T *Tm = gc + 2 * nq * nq, *Tc = Tm + 2 * nq * nloc;
+  T *cue = phf + nq * nloc, *cuf = cue + hc * 3 * nq * nloc;
+  T *ks = cuf + hc * 3 * nq * nloc, *gc = ks + 2 * nq * nq;
+  T *Tm = gc + hc * 2 * nq * nq, *Tc = Tm + 2 * nq * nloc;
   const int bid = blockIdx.x;
   const int tgt = A.near_tgt[bid], src = A.near_src[bid];
   const int nlL = 1 << A.L, ne1 = 1 << A.b;
@@ -277,7 +286,10 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
   const int js = src / (nlL * nlL), cxs = (src / nlL) % nlL, cys = src % nlL;
   double2 *Bg = A.blk + (size_t)bid * A.nL * A.nL;
   if (smem_block) {
-    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) Bs[i] = make_double2(0, 0);
+    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) {
+      Bs[i].x = 0;
+      Bs[i].y = 0;
+    }
     __syncthreads();
   }
   const T *tpts = static_cast<const T *>(A.tab_pts), *tphw = static_cast<const T *>(A.tab_phw),
@@ -310,8 +322,10 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
       PK<T> pk = cfie_kernel_t<T>(A.hard, kap, eta, X, X + 3, X[6], Y, Y + 3, Y[6]);
       ks[2 * i] = pk.ksx * h2 * h2;
       ks[2 * i + 1] = pk.ksy * h2 * h2;
-      gc[2 * i] = pk.gcx * h2 * h2;
-      gc[2 * i + 1] = pk.gcy * h2 * h2;
+      if (A.hard) {
+        gc[2 * i] = pk.gcx * h2 * h2;
+        gc[2 * i + 1] = pk.gcy * h2 * h2;
+      }
     }
     __syncwarp();
     // Tm[q][l] = sum_r ks[q][r] phi_l(r);  Tc[d][q][l] = sum_r gc[q][r] c_l,d(r)
@@ -357,9 +371,9 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
       int row = leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1);
       int col = leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1);
       if (smem_block) {
-        double2 *dst = Bs + (size_t)col * A.nL + row;
-        atomicAdd(&dst->x, (double)ax);
-        atomicAdd(&dst->y, (double)ay);
+        BA *dst = Bs + (size_t)col * A.nL + row;
+        atomicAdd(&dst->x, ax);
+        atomicAdd(&dst->y, ay);
       } else {
         block_add(Bg, A.nL, row, col, cmk((double)ax, (double)ay));
       }
@@ -369,9 +383,9 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
   if (smem_block) {
     __syncthreads();
     for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) {
-      double2 v = Bs[i];
-      atomicAdd(&Bg[i].x, v.x);
-      atomicAdd(&Bg[i].y, v.y);
+      const BA v = Bs[i];
+      atomicAdd(&Bg[i].x, (double)v.x);
+      atomicAdd(&Bg[i].y, (double)v.y);
     }
   }
 }
@@ -657,9 +671,8 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
                                                     (double *)A.tab_cuw);
       note_launch();
     }
-    const size_t per = (size_t)(2 * nq * 7 + 2 * nq * nloc + 6 * nq * nloc + 4 * nq * nq + 2 * nq * nloc +
-                                6 * nq * nloc) * tsz;
-    const size_t bsm = (size_t)S.nL * S.nL * sizeof(double2);
+    const size_t per = (size_t)near_regular_scratch(nq, nloc, S.hard) * tsz;
+    const size_t bsm = (size_t)S.nL * S.nL * 2 * tsz;
     const int smem_block = bsm <= 48 * 1024 ? 1 : 0;
     int warps = 8;
     while (warps > 1 && per * warps + (smem_block ? bsm : 0) > 200 * 1024) warps /= 2;

@@ -56,7 +56,7 @@ WORKLOADS = {
 }
 DEFAULT = "sphere_soft_6x32x32_p2_k8"
 PRECISIONS = {}                              # name -> igabem_precision (filled once the binding is loaded)
-FLOPS_PER_SAMPLE = {False: 40, True: 52}     # kernel sample arithmetic, see the design doc
+FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic: soft 40 flops, hard 52 per pair of samples
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 FP64_PEAK_TFLOPS = 1.25                      # GB300 nominal FP64 (no measured figure available)
 

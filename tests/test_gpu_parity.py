@@ -106,7 +106,7 @@ def test_mixed_fmm_matvec_matches_interpolated_kernel_matrix(hard, kappa):
 
 @pytest.mark.parametrize("hard", [False, True])
 def test_mixed_solve_far_field_matches_fp64(hard):
-    """The mixed-precision solve reproduces the FP64 far field to 1e-5 (spec bar)."""
+    """The mixed-precision solve reproduces the FP64 far field to 1e-5."""
     kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=int(hard), cheb_q=7, leaf_offset=1)
     xh = inputs.fibonacci_directions(100)
     d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])

@@ -257,6 +257,15 @@ int igabem_server_get_stats(igabem_server *srv, igabem_server_stats *out);
 int igabem_farfield_noalloc(igabem_problem *prob, int n_rhs, const void *density, int n_dir,
                             const double *xhat, void *uinf);
 
+/* Self-test of the bounded device waits (the paper has no counterpart).  The tensor-core M2L waits on
+   mbarriers for its copies and MMAs; every wait gives up after a time limit, after which the kernel
+   releases what it holds, records the failure in the problem's status word and returns, and the call
+   reports IGABEM_ETIMEOUT instead of hanging the device.  This call runs the same wait routine on a
+   barrier that nothing arrives at, with limit_s seconds (0 < limit_s <= 10), on the context's stream:
+   it returns IGABEM_ETIMEOUT (the expected result, with a message) when the wait gave up, IGABEM_OK if it
+   completed, IGABEM_EINVAL for a bad limit, IGABEM_ECUDA on a CUDA error.  The context stays usable. */
+int igabem_wait_selftest(igabem_ctx *ctx, double limit_s);
+
 #ifdef __cplusplus
 }
 #endif

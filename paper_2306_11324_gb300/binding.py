@@ -85,6 +85,7 @@ SIGNATURES = {
     "igabem_profile_enable": (c_int, [c_void_p, c_int]),
     "igabem_profile_get": (c_int, [c_void_p, ctypes.POINTER(igabem_profile), c_int]),
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    "igabem_wait_selftest": (c_int, [c_void_p, ctypes.c_double]),
     "igabem_server_create": (c_int, [c_void_p, c_size_t, c_int, ctypes.POINTER(c_void_p)]),
     "igabem_server_destroy": (c_int, [c_void_p]),
     "igabem_submit": (c_int, [c_void_p, c_void_p, ctypes.POINTER(igabem_options), c_int, c_void_p, c_int,
@@ -291,6 +292,12 @@ def igabem_server_get_stats(srv) -> dict:
     st = igabem_server_stats()
     _check(lib().igabem_server_get_stats(srv, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in igabem_server_stats._fields_}
+
+
+def igabem_wait_selftest(ctx, limit_s: float) -> int:
+    """Runs the bounded device wait on a barrier nothing arrives at; returns the status code
+    (IGABEM_ETIMEOUT = -6 expected)."""
+    return lib().igabem_wait_selftest(ctx, float(limit_s))
 
 
 def igabem_farfield_noalloc(prob, density, xhat, uinf):

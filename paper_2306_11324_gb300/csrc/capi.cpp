@@ -647,6 +647,24 @@ int igabem_rhs(igabem_problem *P, int n_rhs, const double *dirs, void *b) {
   });
 }
 
+int igabem_wait_selftest(igabem_ctx *ctx, double limit_s) {
+  return guarded([&] {
+    if (!ctx || !(limit_s > 0.0) || limit_s > 10.0) fail(IGABEM_EINVAL, "invalid self-test arguments");
+    IGA_CUDA(cudaSetDevice(ctx->device));
+    int *status = nullptr, v = 0;
+    IGA_CUDA(cudaMalloc(&status, sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) {
+      launch_wait_selftest(status, limit_s, ctx->stream);
+      e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&v, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(status);
+    IGA_CUDA(e);
+    if (v) fail(IGABEM_ETIMEOUT, "bounded device wait gave up after its time limit (self-test)");
+  });
+}
+
 int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
   return guarded([&] {
     if (!P || !x || !y || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid matvec arguments");

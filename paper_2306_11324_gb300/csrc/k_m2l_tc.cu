@@ -122,8 +122,8 @@ __device__ inline unsigned long long global_ns() {
   return t;
 }
 
-// wait for the completion of the phase with the given parity; false after TC_WAIT_NS
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+// wait for the completion of the phase with the given parity; false after limit_ns
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = TC_WAIT_NS) {
   unsigned long long t0 = 0;
   for (unsigned it = 0;; ++it) {
     uint32_t ok;
@@ -137,7 +137,7 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
     if ((it & 15) == 0) {
       const unsigned long long t = global_ns();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > TC_WAIT_NS) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }
@@ -484,6 +484,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TCArgs A) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(A.tmem_cols) : "memory");
 }
 
+// Self-test of the bounded waits: one thread waits, with the routine the M2L uses, on an mbarrier that
+// nothing arrives at; the wait must give up after limit_ns and the kernel reports it in status[0].
+__global__ void k_wait_selftest(int *status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    status[0] = mbar_wait(smem_u32(&bar), 0, limit_ns) ? 0 : 1;
+  }
+}
+
 // B operands of one level, one block per cluster s: the cluster's scale 2^(12 - ceil(log2 max|X_s|))
 // first (Re and Im parts), then the CR rows (columns of xhat_s) by K = 2 KH entries (Re xhat_s[b][r] at
 // k = b, Im at k = KH + b, zero padding) scaled and split into FP16 hi and lo, written 8 rows at a time.
@@ -565,6 +576,11 @@ TCSlices tc_slices(const HostSetup &S, int R) {
 }
 
 }  // namespace
+
+void launch_wait_selftest(int *status, double limit_s, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(status, (unsigned long long)(limit_s * 1e9));
+  IGA_CUDA(cudaGetLastError());
+}
 
 bool m2l_tc_supported(const HostSetup &S, int R) {
   const int Q = S.q * S.q, CR = (S.hard ? 7 : 1) * R;

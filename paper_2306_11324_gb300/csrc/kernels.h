@@ -16,6 +16,8 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
 bool m2l_tc_supported(const HostSetup &S, int R);
 size_t m2l_tc_image_bytes(const HostSetup &S, int l, int R);
 void launch_m2l_tc(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, cudaStream_t st);
+// bounded-wait self-test: status[0] = 1 when the wait on an mbarrier nothing arrives at gave up
+void launch_wait_selftest(int *status, double limit_s, cudaStream_t st);
 // set-up scratch bytes of launch_near_field (element tables of the regular quadrature)
 size_t near_table_bytes(const HostSetup &S, const igabem_options &o);
 void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_options &o,

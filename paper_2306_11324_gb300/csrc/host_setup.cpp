@@ -64,14 +64,16 @@ static int find_span(const std::vector<double> &kn, int p, double x) {
   return lo;
 }
 
+constexpr int MAX_DEG = 15;  // largest B-spline degree the host tables handle
+
 static void span_basis(const std::vector<double> &kn, int p, int mu, double x, double *N,
                        double *dN) {
-  std::vector<double> left(p + 1), right(p + 1), prev(p + 1);
+  double left[MAX_DEG + 2], right[MAX_DEG + 2], prev[MAX_DEG + 2];
   N[0] = 1.0;
   for (int d = 1; d <= p; ++d) {
     left[d] = x - kn[mu + 1 - d];
     right[d] = kn[mu + d] - x;
-    if (d == p && dN) std::copy(N, N + p, prev.begin());
+    if (d == p && dN) std::copy(N, N + p, prev);
     double saved = 0.0;
     for (int r = 0; r < d; ++r) {
       double den = right[r + 1] + left[d - r];
@@ -120,6 +122,21 @@ static void patch_h(const Patch &P, int m1, int m2, double s, double t, double H
         Ht[c] += b1[i] * d2[j] * h[c];
       }
     }
+}
+
+// Point of a patch at (s, t) (no derivatives): the same polynomial-piece sums as patch_h.
+static void patch_point(const Patch &P, double s, double t, double F[3]) {
+  const int m1 = find_span(P.kn1, P.p1, s), m2 = find_span(P.kn2, P.p2, t);
+  double b1[MAX_DEG + 1], b2[MAX_DEG + 1];
+  span_basis(P.kn1, P.p1, m1, s, b1, nullptr);
+  span_basis(P.kn2, P.p2, m2, t, b2, nullptr);
+  double H[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i <= P.p1; ++i)
+    for (int j = 0; j <= P.p2; ++j) {
+      const double *h = &P.hw[((m1 - P.p1 + i) * P.k2 + (m2 - P.p2 + j)) * 4];
+      for (int c = 0; c < 4; ++c) H[c] += b1[i] * b2[j] * h[c];
+    }
+  for (int c = 0; c < 3; ++c) F[c] = H[c] / H[3];
 }
 
 static void patch_eval(const Patch &P, double s, double t, double F[3], double Fs[3] = nullptr,
@@ -269,6 +286,23 @@ struct PointHash {
   }
 };
 
+// CSR lists (row pointers, columns ascending within a row) of distinct pairs (row, column) with rows and
+// columns in 0..n-1: two stable counting passes, by column and then by row.
+static void csr_of_pairs(const std::vector<std::pair<int, int>> &pairs, int n, std::vector<int> &ptr,
+                         std::vector<int> &col) {
+  std::vector<int> cnt(n + 1, 0);
+  for (const auto &pr : pairs) cnt[pr.second + 1]++;
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> by_col(pairs.size());
+  for (size_t i = 0; i < pairs.size(); ++i) by_col[cnt[pairs[i].second]++] = (int)i;
+  ptr.assign(n + 1, 0);
+  for (const auto &pr : pairs) ptr[pr.first + 1]++;
+  for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  col.resize(pairs.size());
+  for (int i : by_col) col[fill[pairs[i].first]++] = pairs[i].second;
+}
+
 static double dist3(const double *a, const double *b) {
   return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
                    (a[2] - b[2]) * (a[2] - b[2]));
@@ -313,35 +347,55 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   S.corners.assign(12L * S.E, 0.0);
   for (int j = 0; j < np; ++j) {
     const Patch &P = patches[j];
-    std::vector<double> V1 = bernstein_collocation_inverse(P.p1), V2 = bernstein_collocation_inverse(P.p2);
-    int s1 = P.p1 + 1, s2 = P.p2 + 1;
-    std::vector<double> samp(s1 * s2 * 4), tmp(s1 * s2 * 4);
+    if (P.p1 > MAX_DEG || P.p2 > MAX_DEG) fail(IGABEM_EINVAL, "patch degree above " + std::to_string(MAX_DEG));
+    const int s1 = P.p1 + 1, s2 = P.p2 + 1;
+    // The element's Bezier net is linear in the control points of its polynomial piece:
+    // net = E1[ix] CP E2[iy]^T per homogeneous component, with E = (Bezier collocation inverse) x
+    // (B-spline values at the element's collocation points u_a = a / p) per direction.
+    auto factors = [&](const std::vector<double> &kn, int pd, std::vector<int> &span, std::vector<double> &E) {
+      const int sd = pd + 1;
+      const std::vector<double> Vi = bernstein_collocation_inverse(pd);
+      span.assign(S.n1, 0);
+      E.assign((size_t)S.n1 * sd * sd, 0.0);
+      std::vector<double> B((size_t)sd * sd);
+      for (int ix = 0; ix < S.n1; ++ix) {
+        span[ix] = find_span(kn, pd, (ix + 0.5) * S.h);
+        for (int a = 0; a < sd; ++a) {
+          const double u = pd ? double(a) / pd : 0.0;
+          span_basis(kn, pd, span[ix], (ix + u) * S.h, &B[(size_t)a * sd], nullptr);
+        }
+        for (int a = 0; a < sd; ++a)
+          for (int i = 0; i < sd; ++i) {
+            double acc = 0;
+            for (int k = 0; k < sd; ++k) acc += Vi[a * sd + k] * B[(size_t)k * sd + i];
+            E[((size_t)ix * sd + a) * sd + i] = acc;
+          }
+      }
+    };
+    std::vector<int> span1, span2;
+    std::vector<double> E1, E2;
+    factors(P.kn1, P.p1, span1, E1);
+    factors(P.kn2, P.p2, span2, E2);
+    std::vector<double> T((size_t)s1 * s2 * 4);
     for (int ix = 0; ix < S.n1; ++ix)
       for (int iy = 0; iy < S.n1; ++iy) {
-        int id = (j * S.n1 + ix) * S.n1 + iy;
-        double smid = (ix + 0.5) * S.h, tmid = (iy + 0.5) * S.h;
-        int m1 = find_span(P.kn1, P.p1, smid), m2 = find_span(P.kn2, P.p2, tmid);
-        for (int a = 0; a < s1; ++a)
-          for (int b = 0; b < s2; ++b) {
-            double u = P.p1 ? double(a) / P.p1 : 0.0, v = P.p2 ? double(b) / P.p2 : 0.0;
-            double H[4], Hs[4], Ht[4];
-            patch_h(P, m1, m2, (ix + u) * S.h, (iy + v) * S.h, H, Hs, Ht);
-            for (int c = 0; c < 4; ++c) samp[(a * s2 + b) * 4 + c] = H[c];
-          }
-        // coefficients = V1^-1 samp V2^-T (per component)
-        for (int a = 0; a < s1; ++a)
+        const int id = (j * S.n1 + ix) * S.n1 + iy;
+        const int i0 = span1[ix] - P.p1, j0 = span2[iy] - P.p2;
+        const double *e1 = &E1[(size_t)ix * s1 * s1], *e2 = &E2[(size_t)iy * s2 * s2];
+        // T[i][b] = sum_jj E2[b][jj] CP[i0 + i][j0 + jj]
+        for (int i = 0; i < s1; ++i)
           for (int b = 0; b < s2; ++b)
             for (int c = 0; c < 4; ++c) {
               double acc = 0;
-              for (int k = 0; k < s1; ++k) acc += V1[a * s1 + k] * samp[(k * s2 + b) * 4 + c];
-              tmp[(a * s2 + b) * 4 + c] = acc;
+              for (int jj = 0; jj < s2; ++jj) acc += e2[b * s2 + jj] * P.hw[((i0 + i) * P.k2 + (j0 + jj)) * 4 + c];
+              T[(i * s2 + b) * 4 + c] = acc;
             }
         double *out = &S.ebez[S.eoff[id]];
         for (int a = 0; a < s1; ++a)
           for (int b = 0; b < s2; ++b)
             for (int c = 0; c < 4; ++c) {
               double acc = 0;
-              for (int k = 0; k < s2; ++k) acc += V2[b * s2 + k] * tmp[(a * s2 + k) * 4 + c];
+              for (int i = 0; i < s1; ++i) acc += e1[a * s1 + i] * T[(i * s2 + b) * 4 + c];
               out[(a * s2 + b) * 4 + c] = acc;
             }
         const int ca[4] = {0, P.p1, 0, P.p1}, cb[4] = {0, 0, P.p2, P.p2};
@@ -396,24 +450,98 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
 
   // --- touching element pairs ---
   const double tol = 1e-10 * S.scale;
-  PointHash ph;
-  ph.cell = std::max(1e-7 * S.scale, 1e-300);
-  for (int i = 0; i < 4 * S.E; ++i) ph.insert(&S.corners[3L * i], i);
-  std::unordered_map<long long, int> shared;  // (e*E+f) -> bitmask of e's corners shared with f
-  for (int i = 0; i < 4 * S.E; ++i) {
-    int e = i / 4;
-    ph.near(&S.corners[3L * i], [&](int k) {
-      int f = k / 4;
-      if (f != e && dist3(&S.corners[3L * i], &S.corners[3L * k]) <= tol)
-        shared[(long long)e * S.E + f] |= 1 << (i % 4);
-    });
+  // sh: (e E + f, bitmask of e's corners shared with f) for every ordered pair e != f, sorted.  Element
+  // corners coincide by construction at the grid vertices of a patch, so only the distinct vertices are
+  // compared (coincidences across patch boundaries and of degenerate parametrisations): cells of a grid
+  // much coarser than the tolerance, sorted, searched in every cell within the tolerance; coinciding vertices
+  // are merged (union-find) and every pair of corners at one merged vertex marks its two elements.
+  std::vector<std::pair<long long, int>> sh;
+  std::vector<long> crep(4L * S.E);  // merged vertex of each element corner 4 e + c
+  {
+    const int nv1 = S.n1 + 1;
+    const long NV = (long)np * nv1 * nv1;
+    std::vector<double> vx(3 * NV);
+    for (int j = 0; j < np; ++j)
+      for (int a = 0; a < nv1; ++a)
+        for (int b = 0; b < nv1; ++b) {
+          const int ix = std::min(a, S.n1 - 1), iy = std::min(b, S.n1 - 1), c = (a - ix) + 2 * (b - iy);
+          const long e = ((long)j * S.n1 + ix) * S.n1 + iy, v = ((long)j * nv1 + a) * nv1 + b;
+          for (int k = 0; k < 3; ++k) vx[3 * v + k] = S.corners[(e * 4 + c) * 3 + k];
+        }
+    const double cell = std::max(1e-7 * S.scale, 1e-300);
+    struct Key {
+      long long a, b, c;
+      long id;
+      bool operator<(const Key &o) const {
+        return a != o.a ? a < o.a : b != o.b ? b < o.b : c != o.c ? c < o.c : id < o.id;
+      }
+    };
+    auto ci = [&](double x) { return (long long)std::floor(x / cell); };
+    std::vector<Key> keys(NV);
+    for (long v = 0; v < NV; ++v) keys[v] = {ci(vx[3 * v]), ci(vx[3 * v + 1]), ci(vx[3 * v + 2]), v};
+    std::sort(keys.begin(), keys.end());
+    std::vector<long> parent(NV);
+    std::iota(parent.begin(), parent.end(), 0L);
+    auto find = [&](long x) {
+      while (parent[x] != x) x = parent[x] = parent[parent[x]];
+      return x;
+    };
+    for (long v = 0; v < NV; ++v) {
+      // the cells a point within tol of this vertex can lie in (almost always the vertex's own)
+      const double *x = &vx[3 * v];
+      for (long long i = ci(x[0] - tol); i <= ci(x[0] + tol); ++i)
+        for (long long jj = ci(x[1] - tol); jj <= ci(x[1] + tol); ++jj)
+          for (long long k = ci(x[2] - tol); k <= ci(x[2] + tol); ++k) {
+            auto it = std::lower_bound(keys.begin(), keys.end(), Key{i, jj, k, -1});
+            for (; it != keys.end() && it->a == i && it->b == jj && it->c == k; ++it)
+              if (it->id != v && dist3(&vx[3 * v], &vx[3 * it->id]) <= tol) parent[find(it->id)] = find(v);
+          }
+    }
+    std::vector<std::pair<long, int>> inc(4L * S.E);  // (merged vertex, corner index 4 e + c)
+    for (int j = 0; j < np; ++j)
+      for (int ix = 0; ix < S.n1; ++ix)
+        for (int iy = 0; iy < S.n1; ++iy) {
+          const int e = (j * S.n1 + ix) * S.n1 + iy;
+          for (int c = 0; c < 4; ++c) {
+            crep[4L * e + c] = find(((long)j * nv1 + ix + (c & 1)) * nv1 + iy + (c >> 1));
+            inc[4L * e + c] = {crep[4L * e + c], 4 * e + c};
+          }
+        }
+    std::sort(inc.begin(), inc.end());
+    // per element: its touching neighbours f with the mask of its corners shared with f
+    constexpr int NBMAX = 64;
+    std::vector<int> nbf((size_t)S.E * NBMAX), nbm((size_t)S.E * NBMAX), nbc(S.E, 0);
+    for (size_t g0 = 0; g0 < inc.size();) {
+      size_t g1 = g0;
+      while (g1 < inc.size() && inc[g1].first == inc[g0].first) ++g1;
+      for (size_t x = g0; x < g1; ++x)
+        for (size_t y = g0; y < g1; ++y) {
+          const int e = inc[x].second / 4, f = inc[y].second / 4;
+          if (e == f) continue;
+          int *lf = &nbf[(size_t)e * NBMAX], *lm = &nbm[(size_t)e * NBMAX];
+          int k = 0;
+          while (k < nbc[e] && lf[k] != f) ++k;
+          if (k == nbc[e]) {
+            if (k == NBMAX) fail(IGABEM_EINVAL, "an element touches more than 64 others");
+            lf[k] = f;
+            lm[k] = 0;
+            ++nbc[e];
+          }
+          lm[k] |= 1 << (inc[x].second % 4);
+        }
+      g0 = g1;
+    }
+    for (int e = 0; e < S.E; ++e) {
+      const size_t b0 = sh.size();
+      for (int k = 0; k < nbc[e]; ++k)
+        sh.push_back({(long long)e * S.E + nbf[(size_t)e * NBMAX + k], nbm[(size_t)e * NBMAX + k]});
+      std::sort(sh.begin() + b0, sh.end());
+    }
   }
   S.touch.clear();
   for (int e = 0; e < S.E; ++e) {
     S.touch.insert(S.touch.end(), {e, e, 0, 0, 0});
   }
-  std::vector<std::pair<long long, int>> sh(shared.begin(), shared.end());
-  std::sort(sh.begin(), sh.end());
   for (auto &kv : sh) {
     int e = int(kv.first / S.E), f = int(kv.first % S.E);
     int nsh = __builtin_popcount(kv.second);
@@ -422,14 +550,15 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     int te = -1, tf = -1;
     for (int a = 0; a < 8 && te < 0; ++a)
       for (int b = 0; b < 8; ++b) {
+        // corners coincide iff they were merged into one vertex above
         int u, v;
-        d4(a, 0, 0, u, v); const double *pe0 = &S.corners[(e * 4 + u + 2 * v) * 3];
-        d4(b, 0, 0, u, v); const double *pf0 = &S.corners[(f * 4 + u + 2 * v) * 3];
-        if (dist3(pe0, pf0) > tol) continue;
+        d4(a, 0, 0, u, v); const long re0 = crep[e * 4L + u + 2 * v];
+        d4(b, 0, 0, u, v); const long rf0 = crep[f * 4L + u + 2 * v];
+        if (re0 != rf0) continue;
         if (kind == 2) {
-          d4(a, 0, 1, u, v); const double *pe1 = &S.corners[(e * 4 + u + 2 * v) * 3];
-          d4(b, 0, 1, u, v); const double *pf1 = &S.corners[(f * 4 + u + 2 * v) * 3];
-          if (dist3(pe1, pf1) > tol) continue;
+          d4(a, 0, 1, u, v); const long re1 = crep[e * 4L + u + 2 * v];
+          d4(b, 0, 1, u, v); const long rf1 = crep[f * 4L + u + 2 * v];
+          if (re1 != rf1) continue;
         }
         te = a; tf = b;
         break;
@@ -503,12 +632,12 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
         for (int cy = 0; cy < nl; ++cy) {
           int t = (j * nl + cx) * nl + cy;
           double *c = &T.center[3L * t];
-          patch_eval(patches[j], (cx + 0.5) / nl, (cy + 0.5) / nl, c);
+          patch_point(patches[j], (cx + 0.5) / nl, (cy + 0.5) / nl, c);
           double r = 0;
           for (int a = 0; a <= 8; ++a)
             for (int b = 0; b <= 8; ++b) {
               double F[3];
-              patch_eval(patches[j], (cx + a / 8.0) / nl, (cy + b / 8.0) / nl, F);
+              patch_point(patches[j], (cx + a / 8.0) / nl, (cy + b / 8.0) / nl, F);
               r = std::max(r, dist3(F, c));
             }
           T.radius[t] = r;
@@ -547,24 +676,14 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
                            (js * nc + 2 * xs + (b >> 1)) * nc + 2 * ys + (b & 1)});
       }
     }
-    std::sort(far.begin(), far.end());
     TreeLevel &T = S.lev[l];
-    T.far_ptr.assign(T.n + 1, 0);
-    for (auto &pr : far) T.far_ptr[pr.first + 1]++;
-    for (int i = 0; i < T.n; ++i) T.far_ptr[i + 1] += T.far_ptr[i];
-    T.far_src.resize(far.size());
-    for (size_t i = 0; i < far.size(); ++i) T.far_src[i] = far[i].second;
+    csr_of_pairs(far, T.n, T.far_ptr, T.far_src);
     if (!far.empty()) S.lmin = std::min(S.lmin, l);
     S.n_far += (long)far.size();
     cand.swap(nxt);
   }
-  std::sort(near.begin(), near.end());
   int nleaf = S.lev[S.L].n;
-  S.near_ptr.assign(nleaf + 1, 0);
-  for (auto &pr : near) S.near_ptr[pr.first + 1]++;
-  for (int i = 0; i < nleaf; ++i) S.near_ptr[i + 1] += S.near_ptr[i];
-  S.near_src.resize(near.size());
-  for (size_t i = 0; i < near.size(); ++i) S.near_src[i] = near[i].second;
+  csr_of_pairs(near, nleaf, S.near_ptr, S.near_src);
 
   // touching pair -> near block
   int npt = (int)S.touch.size() / 5;
@@ -602,14 +721,24 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   // unordered work list: identical pairs, and (e, f) with e < f for the others (the block of (f, e)
   // comes from the same quadrature points with the roles of x and y exchanged)
   S.sing.clear();
-  std::unordered_map<long long, int> blk_of;
-  for (int i = 0; i < npt; ++i) blk_of[(long long)S.touch[5 * i] * S.E + S.touch[5 * i + 1]] = S.touch_blk[i];
+  // S.touch: the E identical pairs, then the other pairs (e, f) in ascending order of e E + f
+  auto touch_index = [&](int e, int f) {
+    int lo = S.E, hi = npt;  // the first entry whose key is not below e E + f
+    const long long key = (long long)e * S.E + f;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if ((long long)S.touch[5 * mid] * S.E + S.touch[5 * mid + 1] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= npt || S.touch[5 * lo] != e || S.touch[5 * lo + 1] != f) fail(IGABEM_EINVAL, "touching pair without its reverse");
+    return lo;
+  };
   for (int i = 0; i < npt; ++i) {
     const int *t = &S.touch[5 * i];
     if (t[2] == 0) {
       S.sing.insert(S.sing.end(), {t[0], t[1], 0, 0, 0, S.touch_blk[i], -1});
     } else if (t[0] < t[1]) {
-      int back = blk_of.at((long long)t[1] * S.E + t[0]);
+      int back = S.touch_blk[touch_index(t[1], t[0])];
       S.sing.insert(S.sing.end(), {t[0], t[1], t[2], t[3], t[4], S.touch_blk[i], back});
     }
   }

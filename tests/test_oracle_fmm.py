@@ -30,19 +30,29 @@ def test_lagrange_interpolation_reproduces_polynomials():
         assert np.abs(L @ nodes ** q - s ** q).max() > 1e-10
 
 
-def test_mode_b_converges_to_the_exact_matrix_in_q():
-    ex = C.operators(2, 1, 1.0, ("V", "Kp"))
+@pytest.mark.parametrize("hard", [False, True])
+def test_mode_b_converges_to_the_exact_matrix_in_q(hard):
+    """Sec. 4.4: the interpolated kernel tends to the exact one as q grows, so every operator's mode-B
+    matrix tends to its exact Galerkin matrix.  Sound-soft checks V and K'; sound-hard checks K (the
+    pull-back kernel a_x dG/dn_y with the normal at the source nodes) and W (G alone interpolated, the
+    curl and normal factors of Maue's form kept at the quadrature points).  A transposed normal, a
+    wrong channel factor or a dropped term would leave an O(1) far-block error that does not decay."""
+    ops = ("K", "W") if hard else ("V", "Kp")
+    ex = C.operators(2, 1, 1.0, ops, hard)
     errs = []
     for q in (3, 5):
-        mb = C.modeb(2, 1, 1.0, ("V", "Kp"), 2, 0.5, q)
-        errs.append(max(np.abs(mb[o] - ex[o]).max() / np.abs(ex[o]).max() for o in ("V", "Kp")))
+        mb = C.modeb(2, 1, 1.0, ops, 2, 0.5, q, hard=hard)
+        errs.append(max(np.abs(mb[o] - ex[o]).max() / np.abs(ex[o]).max() for o in ops))
     assert errs[0] < 1e-4 and errs[1] < 1e-7 and errs[0] / errs[1] > 100
 
 
-def test_sampled_rows_equal_the_dense_mode_b_matrix():
-    sp = C.sphere_space(2, 1)
-    Amat = C.cfie(2, 1, 1.0, 1.0, False, mode_b=(2, 0.5, 3))
+@pytest.mark.parametrize("hard", [False, True])
+def test_sampled_rows_equal_the_dense_mode_b_matrix(hard):
+    """cfie_rows (the row-by-row reference of the large GPU parity tests) equals the dense mode-B CFIE
+    matrix: sound-soft 1/2 M + K' - i eta V on S^2, sound-hard 1/2 M - K - i eta W on S^0 (Sec. 4.1)."""
+    sp = C.sphere_space(2, 1, hard)
+    Amat = C.cfie(2, 1, 1.0, 1.0, hard, mode_b=(2, 0.5, 3))
     x = inputs.random_complex(sp.N)
-    rows = np.array([0, 7, 33, 149])
-    r = fmm.cfie_rows(sp, 1.0, 1.0, False, x, rows, C.tree(2, 1, 2, 0.5, 3, 1.0))
+    rows = np.array([0, 7, 33, sp.N - 1])
+    r = fmm.cfie_rows(sp, 1.0, 1.0, hard, x, rows, C.tree(2, 1, 2, 0.5, 3, 1.0, hard))
     assert np.abs(r - (Amat @ x)[rows]).max() < 1e-13 * np.abs(Amat @ x).max()

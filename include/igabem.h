@@ -246,7 +246,8 @@ int igabem_server_get_stats(igabem_server *srv, igabem_server_stats *out);
    pool), or a serving loop that must not stall on the implicit device synchronisation of
    cudaMalloc/cudaFree.  Same result as igabem_farfield, but density ([N][n_rhs] complex), xhat
    ([n_dir][3] doubles) and uinf ([n_dir][n_rhs] complex) must all be device memory of the context's
-   device (host pointers are refused with IGABEM_EINVAL).  The problem must already exist (creating it
+   device or managed memory (host memory, page-locked or not, and another GPU's memory are refused
+   with IGABEM_EINVAL); n_rhs <= 65535.  The work runs on the problem's stream.  The problem must already exist (creating it
    allocates).  Scratch: a fixed 32 MiB device array inside the library (2^21 complex values, one per
    element x Gauss point x right-hand side), held by every device that loads the library until the
    process exits; calls with n_elements * gauss_regular^2 * n_rhs > 2^21 are refused with

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,8 @@ template <class F> int guarded(F &&f) {
 }  // namespace
 
 void set_error(const std::string &msg) { g_error = msg; }
+
+int run_guarded(const std::function<void()> &f) { return guarded(f); }
 
 void fail(int code, const std::string &msg) {
   g_error = msg;
@@ -878,7 +881,7 @@ int igabem_farfield(igabem_problem *P, int n_rhs, const void *density, int n_dir
     IGA_CUDA(cudaMallocAsync(&dx, 3 * sizeof(double) * n_dir, st));
     IGA_CUDA(cudaMallocAsync(&du_, 2 * sizeof(double) * n_dir * n_rhs, st));
     IGA_CUDA(cudaMemcpyAsync(dx, xhat, 3 * sizeof(double) * n_dir, cudaMemcpyHostToDevice, st));
-    launch_farfield(P->d, P->S, P->opt, n_rhs, dens, n_dir, dx, du_, st);
+    launch_farfield(P->d, P->S, P->opt, n_rhs, dens, n_dir, dx, du_, P->d.gq, st);
     IGA_CUDA(cudaMemcpyAsync(uinf, du_, 2 * sizeof(double) * n_dir * n_rhs,
                              du ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     IGA_CUDA(cudaFreeAsync(dx, st));

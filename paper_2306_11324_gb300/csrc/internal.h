@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,10 @@ struct Error {
 };
 void set_error(const std::string &msg);
 [[noreturn]] void fail(int code, const std::string &msg);
+// Runs the body of a C entry point: returns IGABEM_OK, or the code of a fail() (its message left for
+// igabem_last_error), IGABEM_ENOMEM for a host allocation failure, IGABEM_EINVAL for another exception.
+// No C++ exception crosses the C ABI.
+int run_guarded(const std::function<void()> &f);
 
 #define IGA_CUDA(call)                                                                        \
   do {                                                                                        \

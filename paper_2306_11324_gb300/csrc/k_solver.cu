@@ -197,12 +197,13 @@ void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options
 }
 
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
-                     const double *dens, int n_dir, const double *xhat_dev, double *uinf,
+                     const double *dens, int n_dir, const double *xhat_dev, double *uinf, double *scratch,
                      cudaStream_t st) {
+  if (R > 65535) fail(IGABEM_EINVAL, "the far field takes at most 65535 right-hand sides per call");
   Phase ph(d.prof, IGABEM_PH_FARFIELD, st);
   RhsArgs A = rhs_args(d, S, o, R);
   long npts = (long)S.E * S.ng * S.ng;
-  double2 *rho = reinterpret_cast<double2 *>(d.gq);  // scratch of size >= E nq R
+  double2 *rho = reinterpret_cast<double2 *>(scratch);  // E nq R complex values
   k_density<<<grid_for(npts * R), 256, 0, st>>>(A, d.x2g, reinterpret_cast<const double2 *>(dens), S.E, rho);
   note_launch();
   dim3 grid(n_dir, R);

@@ -48,8 +48,9 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
 // right-hand sides and far field (k_solver.cu)
 void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                 const double *dirs_dev, double *b, cudaStream_t st);
+// scratch: device space for E ng^2 R complex values (the weighted density at the Gauss points)
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
-                     const double *dens, int n_dir, const double *xhat_dev, double *uinf,
+                     const double *dens, int n_dir, const double *xhat_dev, double *uinf, double *scratch,
                      cudaStream_t st);
 
 // GMRES vector kernels (k_solver.cu); vectors [N][R] complex, per-column results [.][R]

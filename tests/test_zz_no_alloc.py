@@ -50,4 +50,21 @@ def test_noalloc_far_field_refuses_what_it_cannot_hold():
     with pytest.raises(B.IgabemError) as ei:
         B.igabem_farfield_noalloc(prob, dens[:, :1].contiguous().cpu().numpy(), xh, out[:, :1].contiguous())
     assert ei.value.code == -1 and "device memory" in str(ei.value)
+    # so is page-locked host memory, which kernels could reach but which is not the device's own
+    pinned = torch.zeros((N, 1), dtype=torch.complex128).pin_memory()
+    with pytest.raises(B.IgabemError) as ei:
+        B.igabem_farfield_noalloc(prob, pinned, xh, out[:, :1].contiguous())
+    assert ei.value.code == -1 and "device memory" in str(ei.value)
+    # more right-hand sides than the kernel's grid can hold: refused before any launch
+    wide = torch.zeros((N, 65536), dtype=torch.complex128, device="cuda")
+    out_w = torch.empty((1, 65536), dtype=torch.complex128, device="cuda")
+    with pytest.raises(B.IgabemError) as ei:
+        B.igabem_farfield_noalloc(prob, wide, xh[:1].contiguous(), out_w)
+    assert ei.value.code == -1 and "65535" in str(ei.value)
+    del wide, out_w
+    # the context is still usable after the refusals
+    good = torch.tensor(inputs.random_complex(N, seed=5, cols=1), device="cuda")
+    o1 = torch.empty((4, 1), dtype=torch.complex128, device="cuda")
+    B.igabem_farfield_noalloc(prob, good, xh, o1)
+    assert G.rel(o1.cpu().numpy(), B.igabem_farfield(prob, good, xh).cpu().numpy()) < TOL
     B.igabem_problem_destroy(prob)

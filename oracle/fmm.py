@@ -25,8 +25,22 @@ interpolation points per direction (9) but defines neither; the readings used he
 "Mode B" is the Galerkin matrix with k~ in place of k on the element pairs of far blocks and the exact
 rules on all other pairs, every element pair integrated with the same rules as the exact matrix; the
 fast multipole matrix-vector product reproduces it up to rounding.
+
+Level-adaptive interpolation (not in the paper, whose wavenumbers stay below 2.5 on objects of size <= 5
+and which uses one q everywhere).  For kappa diam >> 1 a fixed q either loses accuracy on coarse levels
+or, with a kappa cap, pushes every block down to fine levels.  Reading used here: with the
+textbook bound for Chebyshev interpolation of exp(i omega t) on [-1, 1] with q points,
+    eps(q, omega) = omega^q / (2^(q-1) q!),
+the finest-level pair (q0 = cheb_q, cap0 = kappa_cap) fixes the accuracy eps_ref = eps(q0, cap0 / 2)
+(omega = kappa diam / 2: the phase of the kernel changes by at most kappa diam across a cluster); on
+level l with largest cluster diameter D_l = max 2 r the level takes the smallest q in [q0, q_max] with
+eps(q, kappa D_l / 2) <= eps_ref (q_max if none does), and its cap is the kappa diam at which that q
+reaches eps_ref: cap_l = 2 (eps_ref 2^(q-1) q!)^(1/q) (cap0 itself where q = q0).  A far block on level
+l uses q_l points per direction; mode B is defined with these per-level q.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -52,9 +66,29 @@ def lagrange(nodes: np.ndarray, s: np.ndarray) -> np.ndarray:
     return out
 
 
+def cheb_error_bound(q: int, omega: float) -> float:
+    """Bound on the max error of q-point Chebyshev interpolation of exp(i omega t) on [-1, 1]:
+    max|f^(q)| / (2^(q-1) q!) with |f^(q)| = omega^q."""
+    return omega ** q / (2.0 ** (q - 1) * math.factorial(q))
+
+
+def level_q_and_caps(kappa, diam, q0, cap0, q_max):
+    """Per-level interpolation points and kappa caps (see the module header): diam[l] is the largest
+    cluster diameter bound 2 r on level l."""
+    if q_max is None or q_max <= q0 or not np.isfinite(cap0):
+        return [q0] * len(diam), [cap0] * len(diam)
+    eps_ref = cheb_error_bound(q0, cap0 / 2)
+    qs, caps = [], []
+    for D in diam:
+        q = next((qq for qq in range(q0, q_max + 1) if cheb_error_bound(qq, kappa * D / 2) <= eps_ref), q_max)
+        qs.append(q)
+        caps.append(cap0 if q == q0 else 2.0 * (eps_ref * 2.0 ** (q - 1) * math.factorial(q)) ** (1.0 / q))
+    return qs, caps
+
+
 class ClusterTree:
     def __init__(self, mesh, leaf_level: int, eta_adm: float, q: int, kappa: float = 0.0,
-                 kappa_cap: float = np.inf):
+                 kappa_cap: float = np.inf, q_max: int | None = None):
         if not 0 <= leaf_level <= mesh.m:
             raise ValueError("leaf level must lie in 0..m")
         self.mesh, self.L, self.eta, self.q = mesh, leaf_level, eta_adm, q
@@ -78,6 +112,7 @@ class ClusterTree:
                 c[sl] = mid
                 r[sl] = np.linalg.norm(P - mid[:, None, :], axis=2).max(axis=1)
             self.center.append(c); self.radius.append(r)
+        self.ql, self.caps = level_q_and_caps(kappa, [2 * r.max() for r in self.radius], q, kappa_cap, q_max)
         self.far = [[] for _ in range(leaf_level + 1)]
         self.near = []
         cand = [(t, s) for t in range(n) for s in range(n)]
@@ -100,7 +135,7 @@ class ClusterTree:
         dist = np.linalg.norm(ct - cs) - rt - rs
         if dist <= 0 or diam > self.eta * dist:
             return False
-        return self.kappa * diam <= self.cap
+        return self.kappa * diam <= self.caps[l]
 
     @staticmethod
     def decode(l, t):
@@ -127,13 +162,14 @@ class ClusterTree:
         return j * mesh.n1 * mesh.n1 + ix.ravel() * mesh.n1 + iy.ravel()
 
     def nodes(self, l, t):
-        """Chebyshev nodes of cluster t at level l: patch index and parameters (s, t) (q*q,), node
-        index a = a1 q + a2."""
+        """Chebyshev nodes of cluster t at level l (q = q_l per direction): patch index and parameters
+        (s, t) (q*q,), node index a = a1 q + a2."""
         j, cx, cy = self.decode(l, t)
         nl = 2 ** l
-        n1 = cheb_nodes(self.q, cx / nl, (cx + 1) / nl)
-        n2 = cheb_nodes(self.q, cy / nl, (cy + 1) / nl)
-        return j, np.repeat(n1, self.q), np.tile(n2, self.q), n1, n2
+        q = self.ql[l]
+        n1 = cheb_nodes(q, cx / nl, (cx + 1) / nl)
+        n2 = cheb_nodes(q, cy / nl, (cy + 1) / nl)
+        return j, np.repeat(n1, q), np.tile(n2, q), n1, n2
 
     def cover_check(self):
         """Every ordered element pair lies in exactly one far block or one near block."""
@@ -178,7 +214,7 @@ class InterpolatedKernel:
         """(len(elems), nq, q*q) tensor Lagrange values of cluster t at the Gauss points."""
         _, _, _, n1, n2 = self.node_data(l, t)
         pts = self.rules.pts
-        q = self.tree.q
+        q = self.tree.ql[l]
         idx = (np.asarray(elems)[:, None] * self.rules.nq + np.arange(self.rules.nq)[None, :]).ravel()
         s, tt = self.tree.mesh.params(pts.e[idx], *self._local_uv(idx))
         L1 = lagrange(n1, s)
@@ -219,12 +255,15 @@ def modeB_operators(space, kappa, ops, tree: ClusterTree, rules: ElementRules | 
 def cfie_rows(space, kappa, eta, hard: bool, x, rows, tree: ClusterTree | None = None,
               rules: ElementRules | None = None):
     """Selected entries (A x)[rows] of the global CFIE operator (mode B if a tree is given, else the
-    exact matrix), computed element row by element row without forming A."""
+    exact matrix), computed element row by element row without forming A.  x is (N,) or (N, R); the
+    result is (len(rows),) or (len(rows), R)."""
     mesh = space.mesh
     rules = rules or ElementRules(space)
     ops = ["K", "W"] if hard else ["Kp", "V"]
     coef = {"K": -1.0, "W": -1j * eta} if hard else {"Kp": 1.0, "V": -1j * eta}
-    xX = np.asarray(x, complex)[space.x2g]
+    x = np.asarray(x, complex)
+    single = x.ndim == 1
+    xX = (x[:, None] if single else x)[space.x2g]                # (NX, R)
     rows = np.asarray(rows)
     want = np.nonzero(np.isin(space.x2g, rows))[0]             # X indices of the wanted rows
     elems = sorted({e for X in want for e in np.nonzero((space.l2x == X).any(axis=1))[0]})
@@ -240,7 +279,7 @@ def cfie_rows(space, kappa, eta, hard: bool, x, rows, tree: ClusterTree | None =
         for op in ops:
             if ik is not None:
                 for fs, blocks in ik.far_blocks(op, e):
-                    acc = acc + coef[op] * np.einsum("fkl,fl->k", blocks, xX[space.l2x[fs]])
+                    acc = acc + coef[op] * np.einsum("fkl,flr->kr", blocks, xX[space.l2x[fs]])
                     done[fs] = True
         pairs = [(e, e, 0)] + [(e, f, k) for f, k in touch.get(e, []) if not done[f]]
         sb = singular_blocks(ops, kappa, space, pairs)
@@ -251,10 +290,10 @@ def cfie_rows(space, kappa, eta, hard: bool, x, rows, tree: ClusterTree | None =
         reg = np.nonzero(~done)[0]
         for op in ops:
             blocks = regular_row_blocks(op, kappa, rules, e, reg)
-            acc = acc + coef[op] * np.einsum("fkl,fl->k", blocks, xX[space.l2x[reg]])
+            acc = acc + coef[op] * np.einsum("fkl,flr->kr", blocks, xX[space.l2x[reg]])
         for k, X in enumerate(space.l2x[e]):
             yX[X] = yX.get(X, 0.0) + acc[k]
-    out = np.zeros(len(rows), dtype=complex)
+    out = np.zeros((len(rows), xX.shape[1]), dtype=complex)
     for i, r in enumerate(rows):
         out[i] = sum(yX[X] for X in np.nonzero(space.x2g == r)[0])
-    return out
+    return out[:, 0] if single else out

@@ -39,7 +39,7 @@ WORKLOADS = {
     "sphere_soft_6x32x32_p2_k8": dict(geometry="sphere", level_m=5, degree_p=2, kappa=8.0, bc=0,
                                       cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2},
                                       tol={"fp64": 1e-6, "mixed": 1e-6}, n_dir=100, n_rhs=1, kappa_cap=0.0,
-                                      restart=30, precond={"fp64": 0, "mixed": 1}, precision="mixed"),
+                                      restart=30, precond={"fp64": 1, "mixed": 1}, precision="mixed", eta=8.0),
     # sound-hard deformed sphere (amplitude 0.15, seed 1), 64 x 64 elements per patch, kappa = 20,
     # 64 incident directions on a Fibonacci sphere solved as one multi-RHS request; admissibility capped
     # at kappa * diameter <= 6 (FMM truncation ~1e-5 against the dense matrix at q = 7)
@@ -52,13 +52,26 @@ WORKLOADS = {
                                                 cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2, "tc": 2},
                                                 tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=100, n_rhs=64,
                                                 kappa_cap=6.0, restart=300, precond={"fp64": 0, "mixed": 0, "tc": 0},
-                                                precision="tc", step="matvec", solve_max_iter=1500),
+                                                precision="tc", step="matvec", solve_max_iter=1500, eta=0.05),
+    # the large single scatterer: deformed sphere (amplitude 0.15, seed 1), 256 x 256 elements per patch
+    # (393216 elements, 399384 unknowns), sound-soft, a frequency sweep of 16 kappa in [50, 60] with 8
+    # incident directions each, far field at 2048 directions.  A step is one kappa of the sweep: problem
+    # set-up (near field, tree, tables), GMRES(30) with the block preconditioner to 1e-5 for the 8
+    # directions at once, far field.  Level-adaptive interpolation: 7 points per direction where
+    # kappa * diameter <= 6, up to 12 on coarser levels (the Chebyshev bound of the finest level's accuracy).
+    "deformed_soft_6x256x256_p2_k50-60_8dirs": dict(geometry="deformed", level_m=8, degree_p=2, kappa=50.0, bc=0,
+                                                    cheb_q=7, q_max=12, eta_adm=0.5, kappa_cap=6.0,
+                                                    leaf_offset={"fp64": 2, "mixed": 2, "tc": 2},
+                                                    tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=2048,
+                                                    n_rhs=8, restart=30, precond={"fp64": 1, "mixed": 1, "tc": 1},
+                                                    precision="mixed", step="sweep", eta="kappa",
+                                                    kappas=[50.0 + 10.0 * i / 15 for i in range(16)],
+                                                    solve_max_iter=2000),
 }
 DEFAULT = "sphere_soft_6x32x32_p2_k8"
 PRECISIONS = {}                              # name -> igabem_precision (filled once the binding is loaded)
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic: soft 40 flops, hard 52 per pair of samples
 FLOPS_PER_MAC = 8                            # one complex multiply-add
-FP64_PEAK_TFLOPS = 1.25                      # GB300 nominal FP64 (no measured figure available)
 
 
 def singular_flops_per_point(p, hard, pg=4):
@@ -75,7 +88,45 @@ def singular_flops_per_point(p, hard, pg=4):
     basis = 2 * (5 * n + (6 * n if hard else 0)) + 2 * 4 * n
     acc = n * n * (2 * 4 + (5 + 8 if hard else 0))
     return geo + basis + 60 + acc
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def mie_soft_far_field(kappa, xhat, d=(0.0, 0.0, 1.0)):
+    """Far field of a plane wave scattered by the sound-soft unit sphere (the Mie series, a textbook
+    closed form; e^{-i omega t}, outgoing Hankel functions): u_inf = (i/kappa) sum_n (2n+1)
+    j_n(kappa)/h_n(kappa) P_n(x^.d), summed to n = kappa + 4 kappa^(1/3) + 20."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    c = np.clip(np.asarray(xhat, float) @ np.asarray(d, float), -1.0, 1.0)
+    out = np.zeros(c.shape, dtype=complex)
+    for n in range(int(kappa + 4 * kappa ** (1 / 3) + 20) + 1):
+        j = spherical_jn(n, kappa)
+        out += (2 * n + 1) * (j / (j + 1j * spherical_yn(n, kappa))) * eval_legendre(n, c)
+    return 1j / kappa * out
+
+
+def m2l_alu_roofline(kernel, far_pairs, Q, hard, R, ms, peaks, fp64):
+    """Roofline of an M2L of kernel samples generated on the fly (R columns per sample pass): FP flops
+    (sample arithmetic + complex contraction) against the measured FMA rate, and the special-function
+    work (one sincos and one rsqrt per node pair) against the measured XU rates; the bound is the
+    larger of the two fractions."""
+    C = 7 if hard else 1
+    samples = far_pairs * Q * Q
+    flops = samples * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C * R)
+    achieved = flops / (ms / 1e3) / 1e12
+    fpk = "fp64_tflops" if fp64 else "fp32_tflops"
+    out = {"kernel": kernel, "achieved": achieved, "unit": "TFLOP/s", "peak": peaks[fpk],
+           "frac": achieved / peaks[fpk], "algorithmic_flops_per_matvec": flops, "avg_ms_per_matvec": ms,
+           "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA rate (igabem_measure_peaks, this run)",
+           "node_pairs_per_matvec": samples}
+    if fp64:
+        t_sfu = samples / (peaks["sincos_fp64_gops"] * 1e9)
+        out["sincos_fp64_frac"] = t_sfu / (ms / 1e3)
+        out["bound"] = "alu"
+    else:
+        t_xu = samples / (peaks["sincosf_gops"] * 1e9) + samples / (peaks["rsqrtf_gops"] * 1e9)
+        out["xu_frac"] = t_xu / (ms / 1e3)
+        out["xu_source"] = "one __sincosf and one rsqrtf per node pair at the measured rates"
+        out["bound"] = "alu" if out["frac"] >= out["xu_frac"] else "xu"
+    return out
 
 
 def parse():
@@ -148,13 +199,10 @@ class Clocks:
 # ---------------------------------------------------------------------------------------------
 # the oracle on the host cores (bounded sample)
 
-def oracle_sample(wl, budget_s=20.0, with_lu=True):
-    """Time the CPU oracle on a bounded sample of the workload and scale to solves/s.
-
-    Sample: the exact Galerkin rows of `k` test elements against all 6144 trial elements (dense
-    FP64 assembly, regular and singular quadrature), scaled by E/k to the full matrix, plus the dense
-    LU of an n x n complex matrix (n = 1536) scaled by (N/n)^3 to the N x N system."""
-    import scipy.linalg
+def _oracle_rows_worker(job):
+    """One host process of the oracle sample: the exact Galerkin rows of the test elements job[2]
+    (against every trial element), until job[3] seconds have passed; returns (rows done, seconds)."""
+    wl, worker, elems, budget, n_trial = job
     from oracle import assemble as A
     from oracle import space as S
     mesh = S.Mesh(patches_of(wl["geometry"]), wl["level_m"])
@@ -164,30 +212,67 @@ def oracle_sample(wl, budget_s=20.0, with_lu=True):
     touch = {}
     for e, f, k in mesh.touching():
         touch.setdefault(e, []).append((f, k))
+    trial = np.arange(mesh.E) if n_trial >= mesh.E else np.arange(0, mesh.E, mesh.E // n_trial)
     t0 = time.perf_counter()
     k = 0
-    for e in range(0, mesh.E, 97):
+    for e in elems:
         pairs = [(e, e, 0)] + [(e, f, kk) for f, kk in touch.get(e, [])]
         A.singular_blocks(ops, wl["kappa"], sp, pairs)
-        reg = np.array(sorted(set(range(mesh.E)) - {f for _, f, _ in pairs}))
+        reg = np.setdiff1d(trial, [f for _, f, _ in pairs])
         for op in ops:
             A.regular_row_blocks(op, wl["kappa"], rules, e, reg)
         k += 1
-        if time.perf_counter() - t0 > budget_s * 0.6:
+        if time.perf_counter() - t0 > budget:
             break
-    t_rows = (time.perf_counter() - t0) / k
+    return k, (time.perf_counter() - t0) * mesh.E / len(trial)
+
+
+def oracle_sample(wl, budget_s=20.0, with_lu=True):
+    """Time the CPU oracle on a bounded sample of the workload on all host cores and scale to solves/s.
+
+    Sample: the exact Galerkin rows of some test elements against all trial elements (dense FP64
+    assembly, regular and singular quadrature), computed by one spawned process per host core (each
+    process builds the mesh, space and rules first, outside its timed loop), the rows per second of all
+    processes together scaled to the E rows of the full matrix; plus the dense LU of an n x n complex
+    matrix (n = 1536) on the BLAS threads, scaled by (N/n)^3 to the N x N system."""
+    import multiprocessing
+    import scipy.linalg
+    E = 6 * 4 ** wl["level_m"]
+    N = 6 * (2 ** wl["level_m"] + wl["degree_p"]) ** 2
+    # one process per host core; on the largest meshes at most 4 (each process holds the oracle's
+    # Gauss-point tables of all E elements, ~2.5 kB per element)
+    cores = os.cpu_count() or 1
+    if E > 24576:
+        cores = min(cores, 4)
+    n_trial = min(E, 6144)     # rows against at most 6144 trial elements, the time scaled to all E
+    jobs = [(wl, w, list(range(97 * w, E, 97 * cores)), budget_s * 0.5, n_trial) for w in range(cores)]
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")   # one thread per process
+    try:
+        with multiprocessing.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_rows_worker, jobs)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rows = sum(k for k, _ in res)
+    rate = sum(k / t for k, t in res if t > 0)          # rows per second of all processes together
+    t_rows = 1.0 / rate
     n = 1536
     t_lu = 0.0
     if with_lu:
         M = np.random.default_rng(0).standard_normal((n, n)) + 1j * np.random.default_rng(1).standard_normal((n, n))
         t1 = time.perf_counter()
         scipy.linalg.lu_factor(M)
-        t_lu = (time.perf_counter() - t1) * (sp.N / n) ** 3
-    t_solve = t_rows * mesh.E + t_lu
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{k} of {mesh.E} element rows of the exact Galerkin matrix ({t_rows:.2f} s each, "
-                      f"scaled by E) + dense LU of a {n}^2 complex matrix scaled by (N/{n})^3 = "
-                      f"{t_lu:.1f} s; numpy element loops single-threaded, LU on the BLAS threads",
+        t_lu = (time.perf_counter() - t1) * (N / n) ** 3
+    t_solve = t_rows * E + t_lu
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} of {E} element rows of the exact Galerkin matrix on {cores} processes "
+                      f"(each row against {n_trial} of the {E} trial elements, its time scaled by "
+                      f"{E / n_trial:.0f}; {rate:.3f} full rows/s together, scaled by E) + dense LU of a "
+                      f"{n}^2 complex matrix scaled by (N/{n})^3 = {t_lu:.1f} s on the BLAS threads",
             "extrapolated_s_per_solve": t_solve}
 
 
@@ -274,7 +359,8 @@ def run_serving(args):
         # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload); the
         # tensor-core M2L where the direction count allows it (multiples of 16), FP32 otherwise.  A request
         # that has not reached the tolerance after max_iter iterations is reported as failed.
-        return B.igabem_default_options(level_m=r["m"], degree_p=2, kappa=r["kappa"], eta_cfie=r["kappa"],
+        return B.igabem_default_options(level_m=r["m"], degree_p=2, kappa=r["kappa"],
+                                        eta_cfie=1.0 / r["kappa"] if r["bc"] else r["kappa"],
                                         bc=r["bc"], cheb_q=7, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
                                         precision=B.MIXED_TC, tol=1e-5, max_iter=args.max_iter,
                                         gmres_restart=300 if r["bc"] else 30, precond=0 if r["bc"] else 1)
@@ -312,7 +398,7 @@ def run_serving(args):
         print(json.dumps(out))
 
 
-def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist):
+def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist, peaks):
     """Workloads whose step is one operator application to all right-hand-side columns (64 for the
     sound-hard deformed sphere): matvecs/s counts every column; one full solve is timed beside."""
     import torch
@@ -375,13 +461,13 @@ def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, w
     achieved = (useful + samples) / (m2l_ms / 1e3) / 1e12
     tc = args.precision == "tc"
     peak = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-            if tc and os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else FP32_PEAK_TFLOPS)
+            if tc and os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else peaks["fp32_tflops"])
     kh = (Q + 7) // 8 * 8
     executed = far * 3 * 2 * 128 * (2 * kh) * C * R                  # tensor-core flops issued (split, padding)
     roofline = {"bound": "tensor" if tc else "alu", "kernel": "k_m2l_tc" if tc else "k_m2l_gemm<float>",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": ("measured dense BF16 burst (FP16 has the same tensor rate), MEASURED_PEAKS.json"
-                                if tc else "FP32 CUDA-core rate from unit counts and the maximum SM clock"),
+                                if tc else "measured FP32 FMA rate (igabem_measure_peaks, this run)"),
                 "algorithmic_flops_per_matvec": useful + samples, "avg_ms_per_matvec": m2l_ms,
                 "executed_tensor_flops_per_matvec": executed if tc else None,
                 "executed_tensor_tflops": executed / (m2l_ms / 1e3) / 1e12 if tc else None}
@@ -396,7 +482,7 @@ def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, w
                       "kappa": wl["kappa"], "kappa_cap": wl["kappa_cap"], "leaf_offset": wl["leaf_offset"][args.precision],
                       "n_far_pairs": far, "parallelism": f"replicas x{world}",
                       "l2": "flushed (256 MB write) before each step"},
-           "phase_ms_per_matvec": phases, "setup_ms": info["setup_ms"],
+           "phase_ms_per_matvec": phases, "setup_ms": info["setup_ms"], "measured_peaks": peaks,
            "matvec_rel_err_vs_fp64": err,
            "solve": {"gmres_iterations": sinfo["iterations"], "rel_residual": sinfo["rel_residual"],
                      "converged": sinfo["rel_residual"] <= wl["tol"][args.precision],
@@ -415,6 +501,186 @@ def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, w
         cb.update(value=R / t_mv, unit="matvecs/s",
                   sample=cb["sample"] + f"; the oracle applies the operator by assembling it (no fast method), so "
                                         f"one application to {R} columns costs one assembly")
+        out["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, world, rank, dist, peaks, ctx):
+    """The frequency-sweep workload: a step is one kappa of the sweep (set-up, GMRES for all incident
+    directions at once, far field); solves/s counts every incident direction.  Beside the timed steps:
+    operator applications on a resident problem, the product against the plain FP64 operator on the
+    same seeded vector (the FP64 form is compared by matrix-vector products only), and the same steps
+    through the public API with host buffers."""
+    import torch
+    R = wl["n_rhs"]
+    dirs = inputs.fibonacci_directions(R)
+    xhat = inputs.fibonacci_directions(wl["n_dir"])
+    kappas = wl["kappas"]
+
+    def options(precision, kappa, **kw):
+        o = dict(level_m=wl["level_m"], degree_p=wl["degree_p"], kappa=kappa,
+                 eta_cfie=kappa if wl["eta"] == "kappa" else wl["eta"], bc=wl["bc"], cheb_q=wl["cheb_q"],
+                 q_max=wl["q_max"], eta_adm=wl["eta_adm"], leaf_offset=wl["leaf_offset"][precision],
+                 tol=wl["tol"][precision], kappa_cap=wl["kappa_cap"], gmres_restart=wl["restart"],
+                 max_iter=wl["solve_max_iter"], precond=wl["precond"][precision],
+                 precision=PRECISIONS[precision], profile=1)
+        o.update(kw)
+        return B.igabem_default_options(**o)
+
+    def step(i, host=False):
+        kappa = kappas[i % len(kappas)]
+        g = B.igabem_geometry_create(ctx, patches) if host else geom
+        prob = B.igabem_problem_create(g, options(args.precision, kappa))
+        info = B.igabem_problem_info(prob)
+        N = info["n_dofs"]
+        dens = None if host else torch.empty((N, R), dtype=torch.complex128, device="cuda")
+        dens, sinfo = B.igabem_solve(prob, dirs, N, density=dens, raise_on_not_converged=False)
+        u = B.igabem_farfield(prob, dens, xhat)
+        return g, prob, info, sinfo, u, kappa
+
+    for i in range(args.warmup):
+        _, prob, *_ = step(i)
+        B.igabem_problem_destroy(prob)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    prof_tot, launches, steps_rec = {}, 0, []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            _, prob, info, sinfo, u, kappa = step(args.warmup + k)
+            ev[k][1].record(stream)
+            pr = B.igabem_profile_get(prob)
+            launches += pr["launches"]
+            for name, v in pr["phases"].items():
+                a = prof_tot.setdefault(name, {"ms": 0.0, "calls": 0, "launches": 0})
+                for key in a:
+                    a[key] += v[key]
+            steps_rec.append({"kappa": kappa, "gmres_iterations": sinfo["iterations"],
+                              "rel_residual": sinfo["rel_residual"], "matvecs": sinfo["n_matvecs"],
+                              "converged": sinfo["rel_residual"] <= wl["tol"][args.precision],
+                              "farfield_finite": bool(torch.isfinite(torch.view_as_real(u)).all().item())
+                              if hasattr(u, "device") else bool(np.isfinite(u).all())})
+            B.igabem_problem_destroy(prob)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    phases = {k: round(v["ms"] / args.steps, 3) for k, v in prof_tot.items() if v["ms"] > 0}
+    # operator applications on a resident problem (kappa of the sweep's first value)
+    prob = B.igabem_problem_create(geom, options(args.precision, kappas[0]))
+    info = B.igabem_problem_info(prob)
+    N = info["n_dofs"]
+    x_host = inputs.random_complex(N, seed=2028, cols=R)
+    x = torch.tensor(x_host, device="cuda")
+    y = torch.empty_like(x)
+    B.igabem_matvec(prob, x, y)
+    B.igabem_profile_get(prob, reset=True)
+    nmv = 5
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(nmv):
+        B.igabem_matvec(prob, x, y)
+    b.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = a.elapsed_time(b) / nmv
+    mv_prof = B.igabem_profile_get(prob, reset=True)
+    mv_phases = {k: round(v["ms"] / max(1, v["calls"]), 3) for k, v in mv_prof["phases"].items() if v["calls"]}
+    y_mixed = y.cpu().numpy()
+    B.igabem_problem_destroy(prob)
+    # the plain FP64 operator on the same vector (rank 0)
+    err64, fp64_mv_ms = None, None
+    if rank == 0 and args.precision != "fp64" and not args.one_form:
+        p64 = B.igabem_problem_create(geom, options("fp64", kappas[0]))
+        y64 = torch.empty_like(x)
+        B.igabem_matvec(p64, x, y64)
+        torch.cuda.synchronize()
+        a.record(stream)
+        B.igabem_matvec(p64, x, y64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_mv_ms = a.elapsed_time(b)
+        y64h = y64.cpu().numpy()
+        err64 = float(np.abs(y_mixed - y64h).max() / np.abs(y64h).max())
+        B.igabem_problem_destroy(p64)
+    # end to end through the public API with host buffers (geometry, problem, solve, far field)
+    ke = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ke):
+        g2, p2, *_ = step(args.warmup + i, host=True)
+        B.igabem_problem_destroy(p2)
+        B.igabem_geometry_destroy(g2)
+    e2e_s = (time.perf_counter() - t0) / ke
+    _, _, knots, ctrl, w = inputs.patches_to_arrays(patches)
+    h2d = int(knots.nbytes + ctrl.nbytes + w.nbytes + 8 * 2 * 2 * len(patches) + dirs.nbytes + xhat.nbytes)
+    d2h = int(N * 16 * R + len(xhat) * 16 * R)
+    # roofline: the FP64 singular quadrature of the set-up and the M2L of a product
+    hard = bool(wl["bc"])
+    sing = prof_tot.get("setup_singular", {"ms": 0.0, "calls": 0})
+    sing_ms = sing["ms"] / max(1, sing["calls"])
+    sing_flops = info["n_singular_points"] * singular_flops_per_point(wl["degree_p"], hard)
+    sing_ach = sing_flops / (sing_ms / 1e3) / 1e12 if sing_ms > 0 else 0.0
+    m2l_ms = mv_phases.get("m2l", 0.0)
+    qs = info["level_q"]
+    far_by_level = info["level_far"]
+    C = 7 if hard else 1
+    m2l_samples = sum(f * q ** 4 for f, q in zip(far_by_level, qs))
+    m2l_flops = sum(f * q ** 4 * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C * R)
+                    for f, q in zip(far_by_level, qs))
+    m2l_ach = m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_near_singular (FP64)", "achieved": sing_ach,
+                "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": sing_ach / peaks["fp64_tflops"],
+                "traffic": None,
+                "peak_source": "measured FP64 FMA rate (igabem_measure_peaks, this run; 2 flops per FMA)",
+                "algorithmic_flops_per_setup": sing_flops, "avg_ms_per_setup": sing_ms,
+                "singular_points": info["n_singular_points"],
+                "m2l": {"kernel": "k_m2l_rows<float> / k_m2l_gemm<float>", "achieved": m2l_ach, "unit": "TFLOP/s",
+                        "peak": peaks["fp32_tflops"], "frac": m2l_ach / peaks["fp32_tflops"],
+                        "xu_frac": (m2l_samples / (peaks["sincosf_gops"] * 1e9) + m2l_samples / (peaks["rsqrtf_gops"] * 1e9))
+                        / (m2l_ms / 1e3) if m2l_ms > 0 else None,
+                        "algorithmic_flops_per_matvec": m2l_flops, "avg_ms_per_matvec": m2l_ms,
+                        "node_pairs_per_matvec": m2l_samples,
+                        "peak_source": "measured FP32 FMA rate (igabem_measure_peaks, this run)"}}
+    lat = sorted(step_ms)
+    value = R * args.steps * world / (total_ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "tc": "f16x2+f32+f64"}[args.precision],
+           "data": "synthetic (seeded deformed sphere, Fibonacci directions, seeded complex vectors)",
+           "config": {"workload": args.workload, "n_dofs": N, "n_elements": info["n_elements"], "n_rhs": R,
+                      "step": f"one kappa of the sweep: set-up, GMRES for {R} directions, far field at "
+                              f"{wl['n_dir']} directions (counted as {R} solves)",
+                      "kappas": [kappas[(args.warmup + k) % len(kappas)] for k in range(args.steps)],
+                      "precision": args.precision, "cheb_q": wl["cheb_q"], "q_max": wl["q_max"],
+                      "level_q": qs, "level_far": far_by_level, "eta_adm": wl["eta_adm"],
+                      "kappa_cap": wl["kappa_cap"], "leaf_offset": wl["leaf_offset"][args.precision],
+                      "gmres_restart": wl["restart"], "tol": wl["tol"][args.precision],
+                      "precond": wl["precond"][args.precision], "n_far_pairs": info["n_far_pairs"],
+                      "parallelism": f"replicas x{world}",
+                      "l2": "working set far above L2 (and a 256 MB write before each step)"},
+           "steps_detail": steps_rec,
+           "solve_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "phase_ms_per_step": phases, "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
+           "matvecs_per_s": R * 1e3 / mv_ms * world, "matvec_ms": mv_ms, "phase_ms_per_matvec": mv_phases,
+           "matvec_rel_err_vs_fp64": err64, "fp64_matvec_ms": fp64_mv_ms,
+           "fp64_matvecs_per_s": R * 1e3 / fp64_mv_ms if fp64_mv_ms else None,
+           "gpu_launches": launches, "clocks": clk.summary(), "measured_peaks": peaks,
+           "e2e": {"value": R / e2e_s * world, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
+           "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(wl, with_lu=True)
+        cb.update(value=R * cb["value"],
+                  sample=cb["sample"] + f"; {R} directions per solve counted as {R} solves")
         out["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(out))
@@ -455,11 +721,11 @@ def main():
     def options(precision, max_iter=5000):
         leaf = wl["leaf_offset"][precision]
         return B.igabem_default_options(level_m=wl["level_m"], degree_p=wl["degree_p"], kappa=wl["kappa"],
-                                        eta_cfie=wl["kappa"], bc=wl["bc"], cheb_q=wl["cheb_q"],
+                                        eta_cfie=wl["eta"], bc=wl["bc"], cheb_q=wl["cheb_q"],
                                         eta_adm=wl["eta_adm"], leaf_offset=leaf, tol=wl["tol"][precision],
                                         kappa_cap=wl["kappa_cap"], gmres_restart=wl["restart"],
                                         max_iter=max_iter, precond=wl["precond"][precision],
-                                        precision=PRECISIONS[precision], profile=1)
+                                        precision=PRECISIONS[precision], profile=1, q_max=wl.get("q_max", 0))
 
     def request(opt, host=False):
         """One request through the public API; returns (problem, info, solve info, far field)."""
@@ -528,8 +794,12 @@ def main():
                 "prof": prof_tot, "u": u_last.cpu().numpy(), "clocks": clk.summary(),
                 "leaf_offset": wl["leaf_offset"][precision], "tol": wl["tol"][precision]}
 
+    peaks = B.igabem_measure_peaks(ctx)
+    if wl.get("step") == "sweep":
+        return run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, world, rank, dist, peaks,
+                               ctx)
     if wl.get("step") == "matvec":
-        return run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist)
+        return run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, world, rank, dist, peaks)
     main_form = run_form(args.precision, args.steps, args.warmup, True)
     other = "mixed" if args.precision == "fp64" else "fp64"
     other_form = run_form(other, max(1, min(args.steps, 3)), 1, False) if not args.one_form else None
@@ -539,6 +809,12 @@ def main():
         far_err = float(np.abs(mix_u - fp64_u).max() / np.abs(fp64_u).max())
     else:
         far_err = None
+
+    # the unit sphere's far field against the Mie series (discretisation + FMM + solver error)
+    mie_err = None
+    if wl["geometry"] == "sphere" and not wl["bc"] and len(dirs) == 1:
+        ref = mie_soft_far_field(wl["kappa"], xhat, dirs[0])
+        mie_err = float(np.abs(main_form["u"][:, 0] - ref).max() / np.abs(ref).max())
 
     # ---- end to end through the public API with host buffers ----
     opt = options(args.precision)
@@ -567,29 +843,21 @@ def main():
     far = info["n_far_pairs"]
     Q = wl["cheb_q"] ** 2
     hard = bool(wl["bc"])
-    C = 7 if hard else 1
     fp64 = args.precision == "fp64"
     sing = main_form["prof"].get("setup_singular", {"ms": 0.0, "calls": 0})
     sing_ms = sing["ms"] / max(1, sing["calls"])
     sing_flops = info["n_singular_points"] * singular_flops_per_point(wl["degree_p"], hard)
     sing_achieved = sing_flops / (sing_ms / 1e3) / 1e12 if sing_ms > 0 else 0.0
     m2l = main_form["prof"].get("m2l", {"ms": 0.0, "calls": 0})
-    flops_per_mv = far * Q * Q * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C * len(dirs))
     m2l_ms = m2l["ms"] / max(1, m2l["calls"])
-    achieved = flops_per_mv / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else 0.0
-    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     roofline = {"bound": "alu", "kernel": "k_near_singular (FP64)", "achieved": sing_achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": sing_achieved / FP64_PEAK_TFLOPS,
+                "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": sing_achieved / peaks["fp64_tflops"],
                 "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate of the profiling recipe (no measured FP64 figure in "
-                               "MEASURED_PEAKS.json)",
+                "peak_source": "measured FP64 FMA rate (igabem_measure_peaks, this run; 2 flops per FMA)",
                 "algorithmic_flops_per_setup": sing_flops, "avg_ms_per_setup": sing_ms,
                 "singular_points": info["n_singular_points"],
-                "m2l": {"kernel": "k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>", "bound": "alu",
-                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                        "peak_source": ("nominal GB300 FP64 rate of the profiling recipe" if fp64 else
-                                        "FP32 CUDA-core rate from unit counts and the maximum SM clock"),
-                        "algorithmic_flops_per_matvec": flops_per_mv, "avg_ms_per_matvec": m2l_ms}}
+                "m2l": m2l_alu_roofline("k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>", far, Q, hard,
+                                        len(dirs), m2l_ms, peaks, fp64)}
 
     def summary(f):
         return {"precision": f["precision"], "precond": wl["precond"][f["precision"]], "solves_per_s": f["solves_per_s"], "matvecs_per_s": f["matvecs_per_s"],
@@ -617,6 +885,8 @@ def main():
         "phase_ms_per_step": main_form["phases"],
         "other_form": summary(other_form) if other_form is not None else None,
         "farfield_rel_err_mixed_vs_fp64": far_err,
+        "farfield_rel_err_vs_mie": mie_err,
+        "measured_peaks": peaks,
         "gpu_launches": main_form["launches"],
         "clocks": main_form["clocks"],
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

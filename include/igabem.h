@@ -84,10 +84,25 @@ typedef struct {
   int precond;         /* GMRES preconditioner (the paper uses none): 0 none; 1 right preconditioner by the
                           inverses of the leaf clusters' diagonal near-field blocks, summed over the
                           overlapping leaves (block Jacobi).  The stopping test stays ||b - A x|| <= tol ||b||. */
+  int q_max;           /* level-adaptive interpolation (the paper uses one q everywhere, Sec. 4.4): 0 or
+                          cheb_q: cheb_q points on every level.  cheb_q < q_max <= 16 (needs kappa_cap > 0):
+                          with eps(q, w) = w^q / (2^(q-1) q!), the bound of q-point Chebyshev interpolation
+                          of exp(i w t) on [-1,1], and eps_ref = eps(cheb_q, kappa_cap / 2), level l takes
+                          the smallest q in [cheb_q, q_max] with eps(q, kappa D_l / 2) <= eps_ref (D_l the
+                          level's largest cluster diameter bound), else q_max, and admits pairs with
+                          kappa max(2r) <= cap_l, eps(q_l, cap_l / 2) = eps_ref (kappa_cap where q_l =
+                          cheb_q).  Expansions of a level whose q differs from its children's are formed
+                          from and evaluated at the Gauss points directly. */
+  int no_graph;        /* 0: each GMRES iteration (matrix-vector product, Gram-Schmidt, Givens update, next
+                          basis vector) is captured once as a CUDA graph with its state on the device and
+                          replayed, the host only reading the finished flags one iteration behind;
+                          1: the same kernels launched one by one (per-phase timing of the solve's
+                          products, igabem_profile_*) */
 } igabem_options;
 
 /* Fills the defaults: p = 2, m = 3, kappa = 1, eta_cfie = kappa, sound-soft, q = 7, b = 0,
-   eta_adm = 0.5, no cap, 4 / 5 Gauss points, FP64, restart 30, 1000 iterations, tol 1e-6. */
+   eta_adm = 0.5, no cap, 4 / 5 Gauss points, FP64, restart 30, 1000 iterations, tol 1e-6, one q on
+   every level. */
 void igabem_default_options(igabem_options *opt);
 
 typedef struct {
@@ -103,6 +118,9 @@ typedef struct {
   double setup_ms;           /* wall time of igabem_problem_create */
   double host_setup_ms;      /* of which host-side set-up (tree, lists, tables) */
   long n_singular_points;    /* 4-D quadrature points of the touching pairs (Sec. 4.3 rules) */
+  int n_levels;              /* tree levels 0 .. m - b (at most 24 reported below) */
+  int level_q[24];           /* interpolation points per direction on each level */
+  long level_far[24];        /* admissible pairs on each level */
 } igabem_info;
 
 typedef struct {
@@ -266,6 +284,23 @@ int igabem_farfield_noalloc(igabem_problem *prob, int n_rhs, const void *density
    it returns IGABEM_ETIMEOUT (the expected result, with a message) when the wait gave up, IGABEM_OK if it
    completed, IGABEM_EINVAL for a bad limit, IGABEM_ECUDA on a CUDA error.  The context stays usable. */
 int igabem_wait_selftest(igabem_ctx *ctx, double limit_s);
+
+/* Measured arithmetic rates of the context's device (the paper has no counterpart: these are the
+   denominators against which the library's benchmark quotes the roofline fractions of its ALU-bound
+   kernels).  Each rate is timed with CUDA events on the context's stream, best of five launches after
+   a warm-up, over a grid of 8 x 256 threads per SM whose threads run 8 independent chains of the
+   operation; no setting of the GPU is changed (the clocks are whatever the GPU runs at).  Takes about
+   a tenth of a second; allocates 2 KiB of device memory for the duration of the call. */
+typedef struct {
+  double fp32_tflops;       /* FP32 fused multiply-add rate, 2 flops per FMA */
+  double fp64_tflops;       /* FP64 fused multiply-add rate, 2 flops per FMA */
+  double sincosf_gops;      /* __sincosf calls per second (a sine and a cosine each, special-function unit) */
+  double rsqrtf_gops;       /* rsqrtf calls per second */
+  double sincos_fp64_gops;  /* FP64 sincos calls per second (the CUDA math library routine) */
+  int sm_count;             /* multiprocessors of the device */
+  double sm_clock_mhz_attr; /* the device's reported SM clock attribute (MHz), for reference */
+} igabem_peaks;
+int igabem_measure_peaks(igabem_ctx *ctx, igabem_peaks *out);
 
 #ifdef __cplusplus
 }

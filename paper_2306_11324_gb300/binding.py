@@ -28,14 +28,16 @@ class igabem_options(ctypes.Structure):
                 ("bc", c_int), ("cheb_q", c_int), ("leaf_offset", c_int), ("eta_adm", c_double),
                 ("kappa_cap", c_double), ("gauss_regular", c_int), ("gauss_singular", c_int),
                 ("precision", c_int), ("gmres_restart", c_int), ("max_iter", c_int), ("tol", c_double),
-                ("no_fmm", c_int), ("profile", c_int), ("precond", c_int)]
+                ("no_fmm", c_int), ("profile", c_int), ("precond", c_int), ("q_max", c_int),
+                ("no_graph", c_int)]
 
 
 class igabem_info(ctypes.Structure):
     _fields_ = [("n_dofs", c_long), ("n_patch_dofs", c_long), ("n_elements", c_long),
                 ("n_clusters", c_long), ("n_near_pairs", c_long), ("n_near_element_pairs", c_long),
                 ("n_touching_pairs", c_long), ("n_far_pairs", c_long), ("device_bytes", c_size_t),
-                ("setup_ms", c_double), ("host_setup_ms", c_double), ("n_singular_points", c_long)]
+                ("setup_ms", c_double), ("host_setup_ms", c_double), ("n_singular_points", c_long),
+                ("n_levels", c_int), ("level_q", c_int * 24), ("level_far", c_long * 24)]
 
 
 class igabem_solve_info(ctypes.Structure):
@@ -56,6 +58,12 @@ class igabem_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_long), ("completed", c_long), ("failed", c_long), ("p50_ms", c_double),
                 ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
                 ("peak_bytes", c_size_t), ("budget_bytes", c_size_t), ("peak_active", c_int)]
+
+
+class igabem_peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", c_double), ("fp64_tflops", c_double), ("sincosf_gops", c_double),
+                ("rsqrtf_gops", c_double), ("sincos_fp64_gops", c_double), ("sm_count", c_int),
+                ("sm_clock_mhz_attr", c_double)]
 
 
 class IgabemError(RuntimeError):
@@ -86,6 +94,7 @@ SIGNATURES = {
     "igabem_profile_get": (c_int, [c_void_p, ctypes.POINTER(igabem_profile), c_int]),
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_wait_selftest": (c_int, [c_void_p, ctypes.c_double]),
+    "igabem_measure_peaks": (c_int, [c_void_p, ctypes.POINTER(igabem_peaks)]),
     "igabem_server_create": (c_int, [c_void_p, c_size_t, c_int, ctypes.POINTER(c_void_p)]),
     "igabem_server_destroy": (c_int, [c_void_p]),
     "igabem_submit": (c_int, [c_void_p, c_void_p, ctypes.POINTER(igabem_options), c_int, c_void_p, c_int,
@@ -193,7 +202,11 @@ def igabem_problem_create(geom, opt: igabem_options):
 def igabem_problem_info(prob) -> dict:
     i = igabem_info()
     _check(lib().igabem_problem_info(prob, ctypes.byref(i)))
-    return {k: getattr(i, k) for k, _ in igabem_info._fields_}
+    out = {k: getattr(i, k) for k, _ in igabem_info._fields_}
+    n = min(i.n_levels, 24)
+    out["level_q"] = list(i.level_q[:n])
+    out["level_far"] = list(i.level_far[:n])
+    return out
 
 
 def igabem_problem_destroy(prob):
@@ -306,6 +319,13 @@ def igabem_farfield_noalloc(prob, density, xhat, uinf):
     R = _ncols(density)
     _check(lib().igabem_farfield_noalloc(prob, R, _ptr(density), int(xhat.shape[0]), _ptr(xhat), _ptr(uinf)))
     return uinf
+
+
+def igabem_measure_peaks(ctx) -> dict:
+    """Measured FP32 / FP64 FMA, sincosf, rsqrtf and FP64 sincos rates of the context's device."""
+    p = igabem_peaks()
+    _check(lib().igabem_measure_peaks(ctx, ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in igabem_peaks._fields_}
 
 
 def igabem_profile_enable(prob, on: bool = True):

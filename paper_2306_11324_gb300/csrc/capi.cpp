@@ -92,7 +92,7 @@ void Arena::release() {
 
 // device bytes of the per-call work buffers for R columns (and a GMRES basis of gmres_m + 1 vectors)
 size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision) {
-  const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
+  const int C = S.hard ? 7 : 1, nq = S.ng * S.ng;
   const size_t cz = 2 * sizeof(double);
   const long nleaf = S.lev[S.L].n;
   size_t total = 0;
@@ -102,8 +102,9 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision)
   add((size_t)S.E * nq * C * R * cz);
   add(S.N * R * cz);
   add(S.N * R * cz);
-  add((size_t)34 * 304 * R * cz + 4096);
+  add((size_t)std::max(34, gmres_m + 2) * 304 * R * cz + 4096);
   for (int l = S.lmin; l <= S.L; ++l) {
+    const size_t Q = (size_t)S.lev[l].q * S.lev[l].q;
     add((size_t)S.lev[l].n * Q * C * R * cz);
     add((size_t)S.lev[l].n * Q * C * R * cz);
   }
@@ -113,12 +114,15 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision)
       add((size_t)S.lev[l].n * sizeof(float));
     }
   if (gmres_m) {
-    add((size_t)(gmres_m + 1) * S.N * R * cz);
-    for (int k = 0; k < 6; ++k) add(S.N * R * cz);
-    add((size_t)(gmres_m + 2) * R * cz);
-    add(R * sizeof(double));
-    add(R * sizeof(double));
-    add((size_t)(gmres_m + 1) * R * cz);
+    const size_t m = gmres_m;
+    add((m + 1) * S.N * R * cz);
+    for (int k = 0; k < 7; ++k) add(S.N * R * cz);
+    add((m + 1) * m * R * cz);                            // H
+    for (int k = 0; k < 2; ++k) add(m * R * cz);          // cs, sn
+    for (int k = 0; k < 4; ++k) add((m + 1) * R * cz);    // g, y, hA, hB
+    for (int k = 0; k < 4; ++k) add(R * sizeof(double));  // nrm, s, bn, beta
+    for (int k = 0; k < 4; ++k) add(R * sizeof(int));     // k, its, done, active
+    add(16);                                              // j, flags
   }
   return total;
 }
@@ -126,6 +130,20 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision)
 }  // namespace igabem
 
 using namespace igabem;
+
+// one GMRES iteration (Sec. 5.1) captured as a CUDA graph for a problem's work buffers
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  int R = 0, precond = -1;
+  const void *base = nullptr;        // the work arena the graph's pointers belong to
+  long launches = 0;                 // kernels per replay (for the launch counters)
+  long phase_launches[IGABEM_NPHASE] = {};
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    base = nullptr;
+  }
+};
 
 struct ProblemWork {
   int R = 0;
@@ -136,7 +154,16 @@ struct ProblemWork {
   std::vector<uint8_t *> tc_bimg;
   std::vector<float *> tc_bscale;
   // GMRES
-  double *V, *w, *x, *b, *r, *t, *u, *hdev, *nrm, *sdev, *ydev;
+  double *V, *w, *x, *b, *r, *t, *u, *vj;
+  GmDev G{};
+  double *beta = nullptr;
+  int *active = nullptr;
+  int *hflags = nullptr;             // page-locked copy of G.flags, written by every iteration
+  IterGraph graph;
+  ~ProblemWork() {
+    graph.release();
+    if (hflags) cudaFreeHost(hflags);
+  }
 };
 
 namespace {
@@ -170,7 +197,7 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   if (W.R >= R && (!with_gmres || W.gmres_m >= m)) return;
   R = std::max(R, W.R);
   if (with_gmres) W.gmres_m = std::max(W.gmres_m, m);
-  const int C = S.hard ? 7 : 1, Q = S.q * S.q, nq = S.ng * S.ng;
+  const int C = S.hard ? 7 : 1, nq = S.ng * S.ng;
   const long nleaf = S.lev[S.L].n;
   size_t total = problem_work_bytes(S, R, W.gmres_m, P->opt.precision);
   W.arena.reserve(total);
@@ -184,6 +211,7 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   W.xhat.assign(S.L + 1, nullptr);
   W.yhat.assign(S.L + 1, nullptr);
   for (int l = S.lmin; l <= S.L; ++l) {
+    const size_t Q = (size_t)S.lev[l].q * S.lev[l].q;
     W.xhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
     W.yhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
   }
@@ -194,18 +222,40 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
       W.tc_bimg[l] = W.arena.get<uint8_t>(m2l_tc_image_bytes(S, l, R));
       W.tc_bscale[l] = W.arena.get<float>(S.lev[l].n);
     }
+  W.graph.release();  // its pointers belong to the previous arena
   if (W.gmres_m) {
-    W.V = W.arena.get<double>((size_t)(W.gmres_m + 1) * S.N * R * 2);
+    const size_t m = W.gmres_m;
+    W.V = W.arena.get<double>((m + 1) * S.N * R * 2);
     W.w = W.arena.get<double>(S.N * R * 2);
     W.x = W.arena.get<double>(S.N * R * 2);
     W.b = W.arena.get<double>(S.N * R * 2);
     W.r = W.arena.get<double>(S.N * R * 2);
     W.t = W.arena.get<double>(S.N * R * 2);
     W.u = W.arena.get<double>(S.N * R * 2);
-    W.hdev = W.arena.get<double>((size_t)(W.gmres_m + 2) * R * 2);
-    W.nrm = W.arena.get<double>(R);
-    W.sdev = W.arena.get<double>(R);
-    W.ydev = W.arena.get<double>((size_t)(W.gmres_m + 1) * R * 2);
+    W.vj = W.arena.get<double>(S.N * R * 2);
+    GmDev &G = W.G;
+    G.m = (int)m;
+    G.R = R;
+    G.H = W.arena.get<double2>((m + 1) * m * R);
+    G.cs = W.arena.get<double2>(m * R);
+    G.sn = W.arena.get<double2>(m * R);
+    G.g = W.arena.get<double2>((m + 1) * R);
+    G.y = W.arena.get<double2>((m + 1) * R);
+    G.hA = W.arena.get<double2>((m + 1) * R);
+    G.hB = W.arena.get<double2>((m + 1) * R);
+    G.nrm = W.arena.get<double>(R);
+    G.s = W.arena.get<double>(R);
+    G.bn = W.arena.get<double>(R);
+    W.beta = W.arena.get<double>(R);
+    G.k = W.arena.get<int>(R);
+    G.its = W.arena.get<int>(R);
+    G.done = W.arena.get<int>(R);
+    W.active = W.arena.get<int>(R);
+    G.j = W.arena.get<int>(4);
+    G.flags = G.j + 2;
+    G.V = W.V;
+    G.w = W.w;
+    if (!W.hflags) IGA_CUDA(cudaMallocHost(&W.hflags, 2 * sizeof(int)));
   }
   DeviceProblem &d = P->d;
   d.max_rhs = R;
@@ -273,7 +323,7 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     HostSetup &S = P->S;
     build_setup(geom->patches, *opt, S);
     P->info.host_setup_ms = now_ms() - P->t_plan;
-    const int Q = S.q * S.q, nq = S.ng * S.ng;
+    const int nq = S.ng * S.ng;
     size_t total = 0;
     std::vector<int> dummy_tgt(S.near_src.size());
     size_t nrule = S.r_id.w.size() + S.r_edge.w.size() + S.r_vert.w.size();
@@ -285,8 +335,10 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.sing) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) +
              bytes_of(S.g2x_idx);
     total += bytes_of(S.near_ptr) + bytes_of(S.near_src) + bytes_of(dummy_tgt);
-    total += bytes_of(S.cheb) + bytes_of(S.T1) + bytes_of(S.LG1);
+    total += bytes_of(S.T1) + bytes_of(S.LG1);
     for (int l = 0; l <= S.L; ++l) {
+      const size_t Q = (size_t)S.lev[l].q * S.lev[l].q;
+      total += bytes_of(S.lev[l].cheb) + bytes_of(S.lev[l].T1) + bytes_of(S.lev[l].LG);
       total += bytes_of(S.lev[l].far_ptr) + bytes_of(S.lev[l].far_src);
       total += ((size_t)7 * S.lev[l].n * Q * sizeof(double) + 255) & ~size_t(255);
       total += ((size_t)7 * S.lev[l].n * Q * sizeof(float) + 255) & ~size_t(255);
@@ -325,7 +377,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   P->stream = st;
   HostSetup &S = P->S;
   IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
-  const int Q = S.q * S.q, nq = S.ng * S.ng;
+  const int nq = S.ng * S.ng;
   const long nleaf = S.lev[S.L].n;
   std::vector<int> near_tgt(S.near_src.size());
   for (long t = 0; t < nleaf; ++t)
@@ -374,7 +426,6 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   d.near_ptr = upload(A, S.near_ptr, st);
   d.near_src = upload(A, S.near_src, st);
   d.near_tgt = upload(A, near_tgt, st);
-  double *cheb = upload(A, S.cheb, st);
   d.T1 = upload(A, S.T1, st);
   d.LG1 = upload(A, S.LG1, st);
   d.far_ptr.assign(S.L + 1, nullptr);
@@ -384,7 +435,14 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   d.centers.assign(S.L + 1, nullptr);
   d.pairc.assign(S.L + 1, nullptr);
   d.cext.assign(S.L + 1, nullptr);
+  d.chebl.assign(S.L + 1, nullptr);
+  d.T1l.assign(S.L + 1, nullptr);
+  d.LGl.assign(S.L + 1, nullptr);
   for (int l = 0; l <= S.L; ++l) {
+    const size_t Q = (size_t)S.lev[l].q * S.lev[l].q;
+    d.chebl[l] = upload(A, S.lev[l].cheb, st);
+    d.T1l[l] = upload(A, S.lev[l].T1, st);
+    d.LGl[l] = upload(A, S.lev[l].LG, st);
     d.far_ptr[l] = upload(A, S.lev[l].far_ptr, st);
     d.far_src[l] = upload(A, S.lev[l].far_src, st);
     d.nodes[l] = A.get<double>((size_t)7 * S.lev[l].n * Q);
@@ -404,7 +462,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   IGA_CUDA(cudaMemsetAsync(d.blk, 0, blk_bytes, st));
   IGA_CUDA(cudaMalloc(&d.near_tab, std::max<size_t>(near_table_bytes(S, *opt), 256)));
   launch_gauss_geometry(d, S, st);
-  launch_node_geometry(d, S, cheb, st);
+  launch_node_geometry(d, S, st);
   if (S.n_far > 0 && leaf_moments_supported(S)) {
     if (mixed)
       d.lm32 = A.get<float>(leaf_moment_entries(S));
@@ -458,6 +516,11 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   for (size_t i = 0; i + 6 < S.sing.size(); i += 7) {
     const int kind = S.sing[i + 2];
     I.n_singular_points += kind == 0 ? (long)S.r_id.w.size() : (kind == 2 ? (long)S.r_edge.w.size() : (long)S.r_vert.w.size());
+  }
+  I.n_levels = S.L + 1;
+  for (int l = 0; l <= S.L && l < 24; ++l) {
+    I.level_q[l] = S.lev[l].q;
+    I.level_far[l] = (long)S.lev[l].far_src.size();
   }
   I.device_bytes = A.cap;
   I.setup_ms = now_ms() - P->t_plan;
@@ -699,133 +762,137 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     ProblemWork &W = ext(P)->work;
     const HostSetup &S = P->S;
     const long N = S.N;
-    const int R = n_rhs, m = std::max(1, P->opt.gmres_restart);
+    const int R = n_rhs, m = W.gmres_m;
     const double tol = P->opt.tol;
     const size_t vb = N * R * 2 * sizeof(double);
+    const int maxit = std::max(1, P->opt.max_iter);
+    GmDev G = W.G;
+    G.R = R;  // the buffers may be sized for more columns; every kernel works on the first R
+    G.maxit = maxit;
+    G.tol = tol;
     IGA_CUDA(cudaMemcpyAsync(W.red, dirs, 3 * sizeof(double) * R, cudaMemcpyHostToDevice, st));
     launch_rhs(P->d, S, P->opt, R, W.red, W.b, st);
-    std::vector<double> bn(R), beta(R), hn(R), s(R);
-    auto norms = [&](const double *v, std::vector<double> &out) {
+    std::vector<double> bn(R), beta(R);
+    std::vector<int> its(R, 0), act(R);
+    auto norms = [&](const double *v, std::vector<double> &out, double *dev_copy) {
       {
         Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-        launch_norms(v, N, R, W.red, W.nrm, st);
+        launch_norms(v, N, R, W.red, G.nrm, st);
       }
-      IGA_CUDA(cudaMemcpyAsync(out.data(), W.nrm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (dev_copy) IGA_CUDA(cudaMemcpyAsync(dev_copy, G.nrm, R * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      IGA_CUDA(cudaMemcpyAsync(out.data(), G.nrm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
       IGA_CUDA(cudaStreamSynchronize(st));
     };
-    norms(W.b, bn);
+    norms(W.b, bn, G.bn);
     IGA_CUDA(cudaMemsetAsync(W.x, 0, vb, st));
     IGA_CUDA(cudaMemsetAsync(W.u, 0, vb, st));
+    IGA_CUDA(cudaMemsetAsync(G.its, 0, R * sizeof(int), st));
     IGA_CUDA(cudaMemcpyAsync(W.r, W.b, vb, cudaMemcpyDeviceToDevice, st));
     beta = bn;
-    std::vector<int> its(R, 0);
-    std::vector<char> active(R);
-    for (int r = 0; r < R; ++r) active[r] = beta[r] > tol * bn[r];
     int n_mv = 0;
-    const int maxit = std::max(1, P->opt.max_iter);
-    using cd = std::complex<double>;
-    std::vector<double> hbuf(2 * (m + 1) * R);
-    auto any_active = [&] { return std::any_of(active.begin(), active.end(), [](char c) { return c; }); };
+    const bool pc = P->opt.precond != 0;
+    // one Arnoldi step on the device: w = A V_j (A M^-1 V_j with the preconditioner), two CGS passes,
+    // the Givens update and V_{j+1}; the finished flags are copied to page-locked host memory
+    auto iteration = [&] {
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_copy_vj(G, W.vj, N, st);
+        if (pc) launch_precond(P->d, S, P->opt, R, W.vj, W.t, st);
+      }
+      matvec_dev(P, R, pc ? W.t : W.vj, W.w);
+      {
+        Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
+        launch_gm_iteration_tail(G, W.red, N, st);
+      }
+      IGA_CUDA(cudaMemcpyAsync(W.hflags, G.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    };
+    const bool use_graph = !P->opt.no_graph;
+    IterGraph &IG = W.graph;
+    if (use_graph && (!IG.exec || IG.R != R || IG.precond != (int)pc || IG.base != W.arena.base)) {
+      IG.release();
+      Profiler &pf = P->prof;
+      const bool on = pf.on;
+      const long l0 = pf.launches;
+      long p0[IGABEM_NPHASE];
+      std::copy(pf.phase_launches, pf.phase_launches + IGABEM_NPHASE, p0);
+      pf.on = false;  // no event records inside the graph
+      cudaGraph_t graph = nullptr;
+      IGA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+      try {
+        iteration();
+      } catch (...) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        pf.on = on;
+        throw;
+      }
+      pf.on = on;
+      IGA_CUDA(cudaStreamEndCapture(st, &graph));
+      cudaError_t e = cudaGraphInstantiate(&IG.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      IGA_CUDA(e);
+      IG.R = R;
+      IG.precond = (int)pc;
+      IG.base = W.arena.base;
+      IG.launches = pf.launches - l0;
+      for (int i = 0; i < IGABEM_NPHASE; ++i) {
+        IG.phase_launches[i] = pf.phase_launches[i] - p0[i];
+        pf.phase_launches[i] = p0[i];  // counted again at every replay
+      }
+      pf.launches = l0;
+    }
+    auto run_iteration = [&] {
+      if (use_graph) {
+        IGA_CUDA(cudaGraphLaunch(IG.exec, st));
+        P->prof.launches += IG.launches;
+        for (int i = 0; i < IGABEM_NPHASE; ++i) P->prof.phase_launches[i] += IG.phase_launches[i];
+      } else {
+        iteration();
+      }
+    };
+    cudaEvent_t ev[2];
+    IGA_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    IGA_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    struct EvGuard {
+      cudaEvent_t *e;
+      ~EvGuard() {
+        cudaEventDestroy(e[0]);
+        cudaEventDestroy(e[1]);
+      }
+    } ev_guard{ev};
     auto max_its = [&] { return *std::max_element(its.begin(), its.end()); };
+    for (int r = 0; r < R; ++r) act[r] = beta[r] > tol * bn[r];
+    auto any_active = [&] { return std::any_of(act.begin(), act.end(), [](int c) { return c != 0; }); };
     while (any_active() && max_its() < maxit) {
-      std::vector<Col> col(R);
-      for (int r = 0; r < R; ++r) {
-        col[r].H.assign((m + 1) * m, 0.0);
-        col[r].cs.assign(m, 0.0);
-        col[r].sn.assign(m, 0.0);
-        col[r].g.assign(m + 1, 0.0);
-        col[r].g[0] = beta[r];
-        col[r].done = !active[r];
-        s[r] = active[r] ? 1.0 / beta[r] : 0.0;
-      }
-      IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+      IGA_CUDA(cudaMemcpyAsync(W.beta, beta.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
+      IGA_CUDA(cudaMemcpyAsync(W.active, act.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
       {
         Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-        launch_scale(W.r, W.sdev, W.V, N, R, st);
+        launch_gm_init(G, W.beta, W.active, st);
+        launch_scale(W.r, G.s, W.V, N, R, st);  // V_0 = r / beta
       }
+      W.hflags[0] = W.hflags[1] = 0;
       for (int j = 0; j < m; ++j) {
-        double *Vj = W.V + (size_t)j * N * R * 2;
-        if (P->opt.precond) {  // right preconditioning: w = A M^-1 v_j
-          {
-            Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-            launch_precond(P->d, S, P->opt, R, Vj, W.t, st);
-          }
-          matvec_dev(P, R, W.t, W.w);
-        } else {
-          matvec_dev(P, R, Vj, W.w);
-        }
+        run_iteration();
         ++n_mv;
-        std::vector<cd> h((j + 1) * R, 0.0);
-        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          {
-            Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-            launch_multidot(W.V, j + 1, W.w, N, R, W.red, W.hdev, st);
-            launch_multiaxpy(W.V, j + 1, W.hdev, W.w, N, R, st);
-          }
-          IGA_CUDA(cudaMemcpyAsync(hbuf.data(), W.hdev, (j + 1) * R * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-          IGA_CUDA(cudaStreamSynchronize(st));
-          for (int i = 0; i < (j + 1) * R; ++i) h[i] += cd(hbuf[2 * i], hbuf[2 * i + 1]);
+        IGA_CUDA(cudaEventRecord(ev[j & 1], st));
+        // look one iteration behind: the flags only ever turn on within a cycle
+        if (j >= 1) {
+          IGA_CUDA(cudaEventSynchronize(ev[(j - 1) & 1]));
+          if (W.hflags[0] || W.hflags[1]) break;
         }
-        norms(W.w, hn);
-        for (int r = 0; r < R; ++r) s[r] = (!col[r].done && hn[r] > 0) ? 1.0 / hn[r] : 0.0;
-        IGA_CUDA(cudaMemcpyAsync(W.sdev, s.data(), R * sizeof(double), cudaMemcpyHostToDevice, st));
-        {
-          Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-          launch_scale(W.w, W.sdev, W.V + (size_t)(j + 1) * N * R * 2, N, R, st);
-        }
-        bool all_done = true;
-        for (int r = 0; r < R; ++r) {
-          Col &c = col[r];
-          if (c.done) continue;
-          for (int i = 0; i <= j; ++i) c.H[i * m + j] = h[i * R + r];
-          c.H[(j + 1) * m + j] = hn[r];
-          for (int i = 0; i < j; ++i) {
-            cd t = c.cs[i] * c.H[i * m + j] + c.sn[i] * c.H[(i + 1) * m + j];
-            c.H[(i + 1) * m + j] = -std::conj(c.sn[i]) * c.H[i * m + j] + std::conj(c.cs[i]) * c.H[(i + 1) * m + j];
-            c.H[i * m + j] = t;
-          }
-          cd a = c.H[j * m + j], bb = c.H[(j + 1) * m + j];
-          double den = std::sqrt(std::norm(a) + std::norm(bb));
-          c.cs[j] = den > 0 ? std::conj(a) / den : 1.0;
-          c.sn[j] = den > 0 ? std::conj(bb) / den : 0.0;
-          c.H[j * m + j] = den;
-          c.H[(j + 1) * m + j] = 0.0;
-          c.g[j + 1] = -std::conj(c.sn[j]) * c.g[j];
-          c.g[j] = c.cs[j] * c.g[j];
-          c.k = j + 1;
-          its[r]++;
-          if (std::abs(c.g[j + 1]) <= tol * bn[r] || its[r] >= maxit || hn[r] == 0.0) c.done = true;
-          if (!std::isfinite(std::abs(c.g[j + 1]))) fail(IGABEM_ENUMERIC, "GMRES met a non-finite value");
-          all_done = all_done && c.done;
-        }
-        if (all_done) break;
       }
-      // x += V y with y = H^-1 g per column (zero beyond the column's Krylov dimension)
-      std::vector<double> Y(2 * (m + 1) * R, 0.0);
-      int kmax = 0;
-      for (int r = 0; r < R; ++r) {
-        Col &c = col[r];
-        if (!active[r]) continue;
-        std::vector<cd> y(c.k);
-        for (int i = c.k - 1; i >= 0; --i) {
-          cd acc = c.g[i];
-          for (int k = i + 1; k < c.k; ++k) acc -= c.H[i * m + k] * y[k];
-          y[i] = acc / c.H[i * m + i];
-        }
-        for (int i = 0; i < c.k; ++i) {
-          Y[2 * (i * R + r)] = y[i].real();
-          Y[2 * (i * R + r) + 1] = y[i].imag();
-        }
-        kmax = std::max(kmax, c.k);
-      }
-      IGA_CUDA(cudaMemcpyAsync(W.ydev, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      IGA_CUDA(cudaStreamSynchronize(st));
+      if (W.hflags[1]) fail(IGABEM_ENUMERIC, "GMRES met a non-finite value");
       {
         Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
-        if (P->opt.precond) {  // u += V y;  x = M^-1 u
-          launch_update(W.V, kmax, W.ydev, W.u, N, R, st);
+        launch_gm_solve(G, st);
+        if (pc) {  // u += V y;  x = M^-1 u
+          launch_update(W.V, m, reinterpret_cast<const double *>(G.y), W.u, N, R, st);
           launch_precond(P->d, S, P->opt, R, W.u, W.x, st);
         } else {
-          launch_update(W.V, kmax, W.ydev, W.x, N, R, st);
+          launch_update(W.V, m, reinterpret_cast<const double *>(G.y), W.x, N, R, st);
         }
       }
       matvec_dev(P, R, W.x, W.w);
@@ -834,11 +901,12 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
         Phase ph(&P->prof, IGABEM_PH_KRYLOV, st);
         launch_sub(W.b, W.w, W.r, N * R * 2, st);
       }
-      norms(W.r, beta);
+      norms(W.r, beta, nullptr);
       check_status(P);
+      IGA_CUDA(cudaMemcpy(its.data(), G.its, R * sizeof(int), cudaMemcpyDeviceToHost));
       for (int r = 0; r < R; ++r) {
         if (!std::isfinite(beta[r])) fail(IGABEM_ENUMERIC, "GMRES met a non-finite residual");
-        active[r] = beta[r] > tol * bn[r];
+        act[r] = beta[r] > tol * bn[r] && its[r] < maxit;
       }
     }
     bool dev = is_device_ptr(density);

@@ -643,7 +643,40 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
           T.radius[t] = r;
         }
   }
+  // interpolation points and kappa cap per level (level-adaptive when q_max > cheb_q): the bound
+  // eps(q, w) = w^q / (2^(q-1) q!) of q-point Chebyshev interpolation of exp(i w t) on [-1,1]; the
+  // finest-level pair (cheb_q, kappa_cap) fixes eps_ref = eps(cheb_q, kappa_cap / 2); each level takes
+  // the smallest q in [cheb_q, q_max] with eps(q, kappa D_l / 2) <= eps_ref (else q_max) and the cap
+  // cap_l solving eps(q_l, cap_l / 2) = eps_ref.
   const double cap = opt.kappa_cap > 0 ? opt.kappa_cap : INFINITY;
+  const int qmax = opt.q_max;
+  const bool adaptive = qmax > S.q && !S.no_fmm;
+  if (qmax != 0 && (qmax < S.q || qmax > 16)) fail(IGABEM_EINVAL, "q_max must be 0 or lie in cheb_q..16");
+  if (adaptive && !(opt.kappa_cap > 0)) fail(IGABEM_EINVAL, "level-adaptive q (q_max > cheb_q) needs kappa_cap > 0");
+  auto eps_bound = [](int q, double w) {
+    double f = 1.0;
+    for (int k = 2; k <= q; ++k) f *= k;
+    return std::pow(w, q) / (std::pow(2.0, q - 1) * f);
+  };
+  for (int l = 0; l <= S.L; ++l) {
+    TreeLevel &T = S.lev[l];
+    T.q = S.q;
+    T.cap = cap;
+    if (!adaptive) continue;
+    double D = 0;
+    for (double r : T.radius) D = std::max(D, 2 * r);
+    const double eps_ref = eps_bound(S.q, cap / 2);
+    int q = qmax;
+    for (int qq = S.q; qq <= qmax; ++qq)
+      if (eps_bound(qq, opt.kappa * D / 2) <= eps_ref) {
+        q = qq;
+        break;
+      }
+    double f = 1.0;
+    for (int k = 2; k <= q; ++k) f *= k;
+    T.q = q;
+    T.cap = q == S.q ? cap : 2.0 * std::pow(eps_ref * std::pow(2.0, q - 1) * f, 1.0 / q);
+  }
   auto admissible = [&](int l, int t, int s) {
     if (S.no_fmm) return false;
     const TreeLevel &T = S.lev[l];
@@ -651,7 +684,7 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     double diam = std::max(2 * rt, 2 * rs);
     double dist = dist3(&T.center[3L * t], &T.center[3L * s]) - rt - rs;
     if (dist <= 0 || diam > opt.eta_adm * dist) return false;
-    return opt.kappa * diam <= cap;
+    return opt.kappa * diam <= T.cap;
   };
   std::vector<std::pair<int, int>> cand, nxt, near;
   for (int t = 0; t < np; ++t)
@@ -743,26 +776,36 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     }
   }
 
-  // --- interpolation tables ---
-  S.cheb.resize(S.q);
-  for (int a = 0; a < S.q; ++a) S.cheb[a] = 0.5 + 0.5 * std::cos((2 * a + 1) * M_PI / (2 * S.q));
-  auto lag = [&](int a, double s) {
-    double v = 1.0;
-    for (int k = 0; k < S.q; ++k)
-      if (k != a) v *= (s - S.cheb[k]) / (S.cheb[a] - S.cheb[k]);
-    return v;
-  };
-  S.T1.resize(2L * S.q * S.q);
-  for (int c = 0; c < 2; ++c)
-    for (int a = 0; a < S.q; ++a)
-      for (int a2 = 0; a2 < S.q; ++a2)
-        S.T1[(c * S.q + a) * S.q + a2] = lag(a, 0.5 * c + 0.5 * S.cheb[a2]);
-  int nb2 = 1 << S.b;
-  S.LG1.resize((size_t)nb2 * S.ng * S.q);
-  for (int o = 0; o < nb2; ++o)
-    for (int g = 0; g < S.ng; ++g)
-      for (int a = 0; a < S.q; ++a)
-        S.LG1[(o * S.ng + g) * S.q + a] = lag(a, (o + S.gx[g]) / nb2);
+  // --- interpolation tables (per level: its q; the leaf level's q is S.q of the leaf kernels) ---
+  for (int l = 0; l <= S.L; ++l) {
+    TreeLevel &T = S.lev[l];
+    const int q = T.q;
+    T.cheb.resize(q);
+    for (int a = 0; a < q; ++a) T.cheb[a] = 0.5 + 0.5 * std::cos((2 * a + 1) * M_PI / (2 * q));
+    auto lag = [&](int a, double x) {
+      double v = 1.0;
+      for (int k = 0; k < q; ++k)
+        if (k != a) v *= (x - T.cheb[k]) / (T.cheb[a] - T.cheb[k]);
+      return v;
+    };
+    // transfer to the children (same q): L_a(parent) at the child's node a2, child c of 2 per direction
+    T.T1.assign(2L * q * q, 0.0);
+    for (int c = 0; c < 2; ++c)
+      for (int a = 0; a < q; ++a)
+        for (int a2 = 0; a2 < q; ++a2) T.T1[(c * q + a) * q + a2] = lag(a, 0.5 * c + 0.5 * T.cheb[a2]);
+    T.band_bottom = l < S.L && S.lev[l + 1].q != q;
+    if (T.band_bottom || l == S.L) {  // Lagrange values at the Gauss points of the 2^(m-l) element columns
+      const int ne = 1 << (m - l);
+      T.LG.assign((size_t)ne * S.ng * q, 0.0);
+      for (int o = 0; o < ne; ++o)
+        for (int g = 0; g < S.ng; ++g)
+          for (int a = 0; a < q; ++a) T.LG[((size_t)o * S.ng + g) * q + a] = lag(a, (o + S.gx[g]) / ne);
+    }
+  }
+  S.q = S.lev[S.L].q;
+  S.cheb = S.lev[S.L].cheb;
+  S.T1 = S.lev[S.L].T1;
+  S.LG1 = S.lev[S.L].LG;
 }
 
 }  // namespace igabem

@@ -80,6 +80,13 @@ struct TreeLevel {
   std::vector<double> center;       // 3 per cluster
   std::vector<double> radius;
   std::vector<int> far_ptr, far_src;  // admissible pairs, CSR by target cluster
+  // interpolation on this level: q points per direction, kappa cap of its admissible pairs
+  int q = 0;
+  double cap = 0;
+  std::vector<double> cheb;         // the q Chebyshev points on [0,1]
+  std::vector<double> T1;           // [2][q][q] transfer to the children (when they use the same q)
+  std::vector<double> LG;           // band bottom: [2^(m-l)][ng][q] Lagrange values at the Gauss points
+  bool band_bottom = false;         // expansions built from / evaluated at the Gauss points directly
 };
 
 struct HostSetup {
@@ -203,6 +210,9 @@ struct DeviceProblem {
   std::vector<double *> centers;             // per level: [n][3] cluster centres
   std::vector<float *> pairc;                // per level: [n_far][8] FP32 pair constants
   std::vector<double *> cext;                // per level: [n][2] node extent and largest Jacobian
+  std::vector<double *> chebl;               // per level: its q Chebyshev points on [0,1]
+  std::vector<double *> T1l;                 // per level: [2][q][q] transfer to the children (same q)
+  std::vector<double *> LGl;                 // per band-bottom level: [2^(m-l)][ng][q] Lagrange at Gauss points
   std::vector<uint8_t *> tc_bimg;            // per level: tensor-core M2L operands of the sources
   std::vector<float *> tc_bscale;            // per level: power-of-two scale of each cluster's operand
   int *status = nullptr;                     // device status word: non-zero after a timed-out wait

@@ -425,6 +425,188 @@ __global__ void k_l2p_test(Dims D, Tables T, const double2 *__restrict__ g, doub
   }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Levels whose q differs from their children's ("band bottoms" of the level-adaptive interpolation):
+// their expansions are formed from, and evaluated at, the Gauss points directly, since the child
+// expansions of fewer points cannot carry the parent's Lagrange polynomials exactly.
+
+// channel fields at the Gauss points, weighted by w_q h^2 (the integrand of the moments):
+//   F[e][q][cr]: soft c0 = u;  hard c0 = u, c1..3 = d_s u d_t F - d_t u d_s F, c4..6 = n~ u
+__global__ void k_gauss_channels(Dims D, Tables T, const double2 *__restrict__ xX, double2 *__restrict__ F) {
+  const int p1 = D.p + 1;
+  const long gst = D.E * D.nq;
+  GRID_STRIDE(o, D.E * D.nq * D.CR) {
+    const long e = o / (D.nq * D.CR);
+    const int q = int((o / D.CR) % D.nq), cr = int(o % D.CR), c = cr / D.R, r = cr % D.R;
+    const int q1 = q / D.ng, q2 = q % D.ng;
+    const int j = int(e / ((long)D.n1 * D.n1)), ix = int((e / D.n1) % D.n1), iy = int(e % D.n1);
+    double2 u = cmk(0, 0), us = cmk(0, 0), ut = cmk(0, 0);
+    for (int ka = 0; ka < p1; ++ka) {
+      const double bs = T.phi1[(ix * D.ng + q1) * p1 + ka], ds = T.dphi1[(ix * D.ng + q1) * p1 + ka];
+      for (int kb = 0; kb < p1; ++kb) {
+        const double bt = T.phi1[(iy * D.ng + q2) * p1 + kb], dt = T.dphi1[(iy * D.ng + q2) * p1 + kb];
+        const double2 xv = xX[xindex(D, j, ix + ka, iy + kb) * D.R + r];
+        u = cadd(u, cscale(xv, bs * bt));
+        if (c >= 1 && c <= 3) {
+          us = cadd(us, cscale(xv, ds * bt));
+          ut = cadd(ut, cscale(xv, bs * dt));
+        }
+      }
+    }
+    const long iq = e * D.nq + q;
+    double2 f;
+    if (c == 0) {
+      f = u;
+    } else if (c <= 3) {
+      f = csub(cscale(us, T.gft[(c - 1) * gst + iq]), cscale(ut, T.gfs[(c - 1) * gst + iq]));
+    } else {
+      f = cscale(u, T.gpn[(c - 4) * gst + iq]);
+    }
+    F[o] = cscale(f, T.gw[q1] * T.gw[q2] * D.h * D.h);
+  }
+}
+
+constexpr int BAND_COLS = 16;
+
+// P2M of a band bottom on level l (q = D.q): xhat[t][a1 q + a2][cr] = sum over the cluster's Gauss
+// grid (i1, i2) of LG(i1, a1) LG(i2, a2) F(i1, i2, cr), separably: per row i1 of the grid
+// Z[a2] = sum_i2 LG(i2, a2) F(i1, i2), then xhat[a1][a2] += LG(i1, a1) Z[a2].  One block per
+// (cluster, 16 columns).
+template <class T>
+__global__ void __launch_bounds__(256) k_p2m_band(Dims D, int l, const double *__restrict__ LG,
+                                                  const double2 *__restrict__ F, double2 *__restrict__ xhat) {
+  using V = typename CV<T>::type;
+  extern __shared__ __align__(16) unsigned char smb[];
+  const int q = D.q, Q = q * q, ne = 1 << (D.m - l), n1d = ne * D.ng;
+  T *LGs = reinterpret_cast<T *>(smb);                               // [n1d][q]
+  V *Fs = reinterpret_cast<V *>(LGs + ((n1d * q + 3) & ~3));         // [n1d][BAND_COLS]
+  V *Z = Fs + n1d * BAND_COLS;                                       // [q][BAND_COLS]
+  const int t = blockIdx.x, c0 = blockIdx.y * BAND_COLS, cw = min(BAND_COLS, D.CR - c0);
+  const int nl = 1 << l, j = t / (nl * nl), cx = (t / nl) % nl, cy = t % nl;
+  for (int i = threadIdx.x; i < n1d * q; i += blockDim.x) LGs[i] = (T)LG[i];
+  constexpr int MO = 16;  // outputs per thread: Q * BAND_COLS <= 256 * 16
+  V acc[MO];
+#pragma unroll
+  for (int k = 0; k < MO; ++k) acc[k].x = acc[k].y = 0;
+  for (int i1 = 0; i1 < n1d; ++i1) {
+    const int ix = cx * ne + i1 / D.ng, g1 = i1 % D.ng;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1d * BAND_COLS; i += blockDim.x) {
+      const int i2 = i / BAND_COLS, col = i % BAND_COLS;
+      const int iy = cy * ne + i2 / D.ng, g2 = i2 % D.ng;
+      const long e = ((long)j * D.n1 + ix) * D.n1 + iy;
+      V v;
+      v.x = v.y = 0;
+      if (col < cw) {
+        const double2 f = F[((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col];
+        v.x = (T)f.x;
+        v.y = (T)f.y;
+      }
+      Fs[i] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < q * BAND_COLS; i += blockDim.x) {
+      const int a2 = i / BAND_COLS, col = i % BAND_COLS;
+      V sum;
+      sum.x = sum.y = 0;
+      for (int i2 = 0; i2 < n1d; ++i2) {
+        const T w = LGs[i2 * q + a2];
+        const V f = Fs[i2 * BAND_COLS + col];
+        sum.x += w * f.x;
+        sum.y += w * f.y;
+      }
+      Z[i] = sum;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < MO; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      if (i < Q * BAND_COLS) {
+        const int a = i / BAND_COLS, col = i % BAND_COLS, a1 = a / q, a2 = a % q;
+        const T w = LGs[i1 * q + a1];
+        const V z = Z[a2 * BAND_COLS + col];
+        acc[k].x += w * z.x;
+        acc[k].y += w * z.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < MO; ++k) {
+    const int i = threadIdx.x + 256 * k;
+    if (i < Q * BAND_COLS) {
+      const int a = i / BAND_COLS, col = i % BAND_COLS;
+      if (col < cw) xhat[((long)t * Q + a) * D.CR + c0 + col] = make_double2((double)acc[k].x, (double)acc[k].y);
+    }
+  }
+}
+
+// L2P of a band bottom on level l: G(i1, i2, cr) += sum_a1 LG(i1, a1) sum_a2 LG(i2, a2) yhat[t][a1 q + a2][cr]
+// at every Gauss point of the cluster (G[e][q][cr], tested against the basis by k_l2p_test), separably:
+// per grid row i1, U[a2] = sum_a1 LG(i1, a1) yhat[a1][a2], then G(i1, i2) += sum_a2 LG(i2, a2) U[a2].
+template <class T>
+__global__ void __launch_bounds__(256) k_l2p_band(Dims D, int l, const double *__restrict__ LG,
+                                                  const double2 *__restrict__ yhat, double2 *__restrict__ G) {
+  using V = typename CV<T>::type;
+  extern __shared__ __align__(16) unsigned char smb[];
+  const int q = D.q, Q = q * q, ne = 1 << (D.m - l), n1d = ne * D.ng;
+  T *LGs = reinterpret_cast<T *>(smb);                               // [n1d][q]
+  V *Ys = reinterpret_cast<V *>(LGs + ((n1d * q + 3) & ~3));         // [Q][BAND_COLS]
+  V *U = Ys + Q * BAND_COLS;                                         // [q][BAND_COLS]
+  const int t = blockIdx.x, c0 = blockIdx.y * BAND_COLS, cw = min(BAND_COLS, D.CR - c0);
+  const int nl = 1 << l, j = t / (nl * nl), cx = (t / nl) % nl, cy = t % nl;
+  for (int i = threadIdx.x; i < n1d * q; i += blockDim.x) LGs[i] = (T)LG[i];
+  for (int i = threadIdx.x; i < Q * BAND_COLS; i += blockDim.x) {
+    const int a = i / BAND_COLS, col = i % BAND_COLS;
+    V v;
+    v.x = v.y = 0;
+    if (col < cw) {
+      const double2 y = yhat[((long)t * Q + a) * D.CR + c0 + col];
+      v.x = (T)y.x;
+      v.y = (T)y.y;
+    }
+    Ys[i] = v;
+  }
+  for (int i1 = 0; i1 < n1d; ++i1) {
+    const int ix = cx * ne + i1 / D.ng, g1 = i1 % D.ng;
+    __syncthreads();
+    for (int i = threadIdx.x; i < q * BAND_COLS; i += blockDim.x) {
+      const int a2 = i / BAND_COLS, col = i % BAND_COLS;
+      V sum;
+      sum.x = sum.y = 0;
+      for (int a1 = 0; a1 < q; ++a1) {
+        const T w = LGs[i1 * q + a1];
+        const V y = Ys[(a1 * q + a2) * BAND_COLS + col];
+        sum.x += w * y.x;
+        sum.y += w * y.y;
+      }
+      U[i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1d * BAND_COLS; i += blockDim.x) {
+      const int i2 = i / BAND_COLS, col = i % BAND_COLS;
+      if (col >= cw) continue;
+      V sum;
+      sum.x = sum.y = 0;
+      for (int a2 = 0; a2 < q; ++a2) {
+        const T w = LGs[i2 * q + a2];
+        const V u = U[a2 * BAND_COLS + col];
+        sum.x += w * u.x;
+        sum.y += w * u.y;
+      }
+      const int iy = cy * ne + i2 / D.ng, g2 = i2 % D.ng;
+      const long e = ((long)j * D.n1 + ix) * D.n1 + iy;
+      double2 *dst = G + ((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col;
+      *dst = make_double2(dst->x + (double)sum.x, dst->y + (double)sum.y);
+    }
+  }
+}
+
+size_t band_smem(int n1d, int q, bool fp32, bool l2p) {
+  const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+  const size_t lg = ((size_t)(n1d * q + 3) & ~size_t(3)) * ts;
+  return lg + 2 * ts * BAND_COLS * (l2p ? ((size_t)q * q + q) : ((size_t)n1d + q));
+}
+
 // y[i][r] = sum_{X in g2x(i)} sum_{leaves t containing X} y_leaf[t][local(X)][r]
 __global__ void k_gather_out(Dims D, const int *__restrict__ g2x_ptr, const int *__restrict__ g2x_idx,
                              const double2 *__restrict__ yleaf, double2 *__restrict__ y) {
@@ -484,6 +666,40 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     Tables T{d.phi1, d.dphi1, d.gw, d.LG1, d.T1, d.gpn, d.gfs, d.gft};
     auto X = [&](int l) { return reinterpret_cast<double2 *>(d.xhat[l]); };
     auto Y = [&](int l) { return reinterpret_cast<double2 *>(d.yhat[l]); };
+    auto level_dims = [&](int l) {  // the dimensions with level l's interpolation points
+      Dims Dl = D;
+      Dl.q = S.lev[l].q;
+      Dl.Q = Dl.q * Dl.q;
+      return Dl;
+    };
+    const bool f32 = o.precision != IGABEM_FP64;
+    bool bands = false;  // levels whose expansions come from the Gauss points directly
+    for (int l = S.lmin; l < S.L; ++l) bands = bands || S.lev[l].band_bottom;
+    double2 *gq = reinterpret_cast<double2 *>(d.gq);
+    auto band_launch = [&](int l, bool l2p) {
+      const Dims Dl = level_dims(l);
+      const int n1d = (1 << (S.m - l)) * S.ng;
+      const size_t smem = band_smem(n1d, Dl.q, f32, l2p);
+      dim3 grid(S.lev[l].n, (D.CR + BAND_COLS - 1) / BAND_COLS);
+      if (l2p) {
+        if (f32) {
+          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<float>, smem));
+          k_l2p_band<float><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
+        } else {
+          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<double>, smem));
+          k_l2p_band<double><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
+        }
+      } else {
+        if (f32) {
+          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<float>, smem));
+          k_p2m_band<float><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
+        } else {
+          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<double>, smem));
+          k_p2m_band<double><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
+        }
+      }
+      note_launch();
+    };
     long nleafQ = (long)nleaf * D.Q * D.CR;
     {
       Phase ph(d.prof, IGABEM_PH_P2M, st);
@@ -493,67 +709,86 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         k_p2m<<<grid_for(nleafQ), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX), X(S.L));
         note_launch();
       }
+      if (bands) {
+        k_gauss_channels<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX),
+                                                                       gq);
+        note_launch();
+      }
     }
     {
       Phase ph(d.prof, IGABEM_PH_M2M, st);
-      const bool sep = D.CR >= 16 && D.q <= 16 && D.Q * SEP_COLS <= 256 * 8;
-      const bool f32 = o.precision != IGABEM_FP64;
-      const size_t smem = (size_t)2 * D.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
-      if (sep) IGA_CUDA(f32 ? set_max_dynamic_smem(k_m2m_sep<float>, smem) : set_max_dynamic_smem(k_m2m_sep<double>, smem));
       for (int l = S.L - 1; l >= S.lmin; --l) {
-        long n = (long)S.lev[l].n * D.Q * D.CR;
+        if (S.lev[l].band_bottom) {
+          band_launch(l, false);
+          continue;
+        }
+        const Dims Dl = level_dims(l);  // the children have the same q
+        long n = (long)S.lev[l].n * Dl.Q * D.CR;
+        const bool sep = D.CR >= 16 && Dl.q <= 16 && Dl.Q * SEP_COLS <= 256 * 8;
+        const size_t smem = (size_t)2 * Dl.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
         if (sep) {
+          IGA_CUDA(f32 ? set_max_dynamic_smem(k_m2m_sep<float>, smem) : set_max_dynamic_smem(k_m2m_sep<double>, smem));
           dim3 grid(S.lev[l].n, (D.CR + SEP_COLS - 1) / SEP_COLS);
           if (f32)
-            k_m2m_sep<float><<<grid, 256, smem, st>>>(D, l, d.T1, X(l + 1), X(l));
+            k_m2m_sep<float><<<grid, 256, smem, st>>>(Dl, l, d.T1l[l], X(l + 1), X(l));
           else
-            k_m2m_sep<double><<<grid, 256, smem, st>>>(D, l, d.T1, X(l + 1), X(l));
+            k_m2m_sep<double><<<grid, 256, smem, st>>>(Dl, l, d.T1l[l], X(l + 1), X(l));
         } else {
-          k_m2m<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, X(l + 1), X(l));
+          k_m2m<<<grid_for(n), 256, 0, st>>>(Dl, l, d.T1l[l], X(l + 1), X(l));
         }
         note_launch();
       }
     }
-    if (m2l_rows_supported(S)) {
+    if (m2l_rows_supported(S, o, R)) {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       if (o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() && d.tc_bimg[S.L])
         launch_m2l_tc(d, S, o, R, st);
       else
-        launch_m2l_rows(d, S, o, R, o.precision != IGABEM_FP64, st);
+        launch_m2l_rows(d, S, o, R, f32, st);
     } else {
-      int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / D.Q));
-      int ntypes = D.hard ? 2 : 1;
-      size_t smem = (size_t)(ntypes * D.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
-      IGA_CUDA(set_max_dynamic_smem(k_m2l, smem));
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       for (int l = S.lmin; l <= S.L; ++l) {
+        const Dims Dl = level_dims(l);
+        int crc = std::max(1, std::min(D.CR, (M2L_MO * 256) / Dl.Q));
+        int ntypes = D.hard ? 2 : 1;
+        size_t smem = (size_t)(ntypes * Dl.Q * M2L_BT + M2L_BT * crc) * sizeof(double2);
+        IGA_CUDA(set_max_dynamic_smem(k_m2l, smem));
         dim3 grid(S.lev[l].n, (D.CR + crc - 1) / crc);
-        k_m2l<<<grid, 256, smem, st>>>(D, S.lev[l].n, d.far_ptr[l], d.far_src[l], d.nodes[l], X(l), Y(l), crc);
+        k_m2l<<<grid, 256, smem, st>>>(Dl, S.lev[l].n, d.far_ptr[l], d.far_src[l], d.nodes[l], X(l), Y(l), crc);
         note_launch();
       }
     }
     {
       Phase ph(d.prof, IGABEM_PH_L2L, st);
-      const bool sep = D.CR >= 16 && D.q <= 16;
-      const bool f32 = o.precision != IGABEM_FP64;
-      const size_t smem = (size_t)3 * D.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
-      if (sep) IGA_CUDA(f32 ? set_max_dynamic_smem(k_l2l_sep<float>, smem) : set_max_dynamic_smem(k_l2l_sep<double>, smem));
+      if (bands) IGA_CUDA(cudaMemsetAsync(gq, 0, sizeof(double2) * D.E * D.nq * D.CR, st));
       for (int l = S.lmin; l < S.L; ++l) {
-        long n = (long)S.lev[l + 1].n * D.Q * D.CR;
-        if (sep) {
+        if (S.lev[l].band_bottom) {
+          band_launch(l, true);
+          continue;
+        }
+        const Dims Dl = level_dims(l);
+        long n = (long)S.lev[l + 1].n * Dl.Q * D.CR;
+        const bool sep = D.CR >= 16 && Dl.q <= 16;
+        const size_t smem = (size_t)3 * Dl.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
+        if (sep && smem <= (size_t)max_optin_smem() - 4096) {
+          IGA_CUDA(f32 ? set_max_dynamic_smem(k_l2l_sep<float>, smem) : set_max_dynamic_smem(k_l2l_sep<double>, smem));
           dim3 grid(S.lev[l].n, (D.CR + SEP_COLS - 1) / SEP_COLS);
           if (f32)
-            k_l2l_sep<float><<<grid, 256, smem, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+            k_l2l_sep<float><<<grid, 256, smem, st>>>(Dl, l, d.T1l[l], Y(l), Y(l + 1));
           else
-            k_l2l_sep<double><<<grid, 256, smem, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+            k_l2l_sep<double><<<grid, 256, smem, st>>>(Dl, l, d.T1l[l], Y(l), Y(l + 1));
         } else {
-          k_l2l<<<grid_for(n), 256, 0, st>>>(D, l, d.T1, Y(l), Y(l + 1));
+          k_l2l<<<grid_for(n), 256, 0, st>>>(Dl, l, d.T1l[l], Y(l), Y(l + 1));
         }
         note_launch();
       }
     }
     {
       Phase ph(d.prof, IGABEM_PH_L2P, st);
+      if (bands) {  // the band bottoms' fields at the Gauss points, tested (before gq is reused below)
+        k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, gq, reinterpret_cast<double2 *>(d.yleaf));
+        note_launch();
+      }
       if (leafk) {
         launch_l2p(d, S, o, R, st);
       } else {

@@ -2,10 +2,12 @@
 // Chebyshev nodes generated on the fly, FP64 and FP32.
 //
 // Layout: one thread block per target cluster (all levels in one launch), its warps share the
-// target's interaction list; lane l owns target nodes l and l + 32 (q*q <= 64) and generates their
-// rows of the coupling block in registers while streaming the source nodes of one pair from shared
-// memory (broadcast reads).  Accumulation is blocked: q source nodes per partial sum, q partial sums
-// per pair, then the pairs; the warps are reduced through shared memory at the end.
+// target's interaction list; lane l owns target nodes a0 + l and a0 + l + 32 of a chunk of 64 target
+// nodes (levels with q*q > 64 take several chunks, each streaming the interaction list again) and
+// generates their rows of the coupling block in registers while streaming the source nodes of one pair
+// from shared memory (broadcast reads).  Accumulation is blocked: q source nodes per partial sum, q
+// partial sums per pair, then the pairs; the warps are reduced through shared memory at the end of a
+// chunk.  Each level has its own q (level-adaptive interpolation).
 //
 // FP32 phase split: the sample phase kappa r is formed as kappa |D| (D = c_t - c_s, the distance of
 // the two cluster centres, taken in FP64 once per pair and reduced mod 2 pi) plus kappa (r - |D|),
@@ -37,12 +39,14 @@ struct M2LLevel {
   double2 *yhat;
   int n;                 // clusters on the level
   int first;             // first block index of the level in the flattened grid
+  int q, Q;              // interpolation points per direction / per cluster on the level
 };
 
 struct M2LArgs {
   M2LLevel lev[16];
   int nlev;
-  int q, Q, CR, R;
+  int QS;                // source nodes per warp in shared memory (the largest Q of the launch)
+  int CR, R;
   double kappa, eta;
   bool hard;
 };
@@ -67,149 +71,153 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_rows(M2LArgs A, int cr0)
   while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
   const M2LLevel &L = A.lev[li];
   const int t = blockIdx.x - L.first;
-  const int Q = A.Q;
+  const int Q = L.Q, q = L.q, QS = A.QS;
   const long NQ = (long)L.n * Q;
   const int ncr = min(NCR, A.CR - cr0);
-  // shared memory: per warp Q source nodes + Q x NCR source coefficients; then the reduction area
-  SrcNode<T> *src = reinterpret_cast<SrcNode<T> *>(smraw) + warp * 64;
-  C2<T> *xs = reinterpret_cast<C2<T> *>(reinterpret_cast<SrcNode<T> *>(smraw) + M2L_WARPS * 64) + warp * 64 * NCR;
+  // shared memory: per warp QS source nodes + QS x NCR source coefficients; then the reduction area
+  SrcNode<T> *src = reinterpret_cast<SrcNode<T> *>(smraw) + warp * QS;
+  C2<T> *xs = reinterpret_cast<C2<T> *>(reinterpret_cast<SrcNode<T> *>(smraw) + M2L_WARPS * QS) + warp * QS * NCR;
   double2 *red = reinterpret_cast<double2 *>(smraw);
   const T kappa = (T)A.kappa, eta = (T)A.eta;
-  // target rows of this lane
-  T tx[2][3], tn[2][3], ta[2];
-  bool valid[2];
-  for (int k = 0; k < 2; ++k) {
-    int a = lane + 32 * k;
-    valid[k] = a < Q;
-    long ia = (long)t * Q + (valid[k] ? a : 0);
-    for (int c = 0; c < 3; ++c) {
-      tx[k][c] = F32 ? (T)L.nodes32[c * NQ + ia] : (T)L.nodes[c * NQ + ia];
-      tn[k][c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ia] : (T)L.nodes[(3 + c) * NQ + ia];
-    }
-    ta[k] = F32 ? (T)L.nodes32[6 * NQ + ia] : (T)L.nodes[6 * NQ + ia];
-  }
-  C2<T> tot[2][NCR];
-  for (int k = 0; k < 2; ++k)
-    for (int c = 0; c < NCR; ++c) tot[k][c] = c2((T)0, (T)0);
   const T inv4pi = (T)(0.25 / IGA_PI);
-  for (int kk = L.far_ptr[t] + warp; kk < L.far_ptr[t + 1]; kk += M2L_WARPS) {
-    const int s = L.far_src[kk];
-    // pair constants (FP32 path): D = c_t - c_s, |D|, |D|^2 and exp(i kappa |D|), from the set-up
-    T D[3] = {0, 0, 0}, Dn = 0, D2 = 0;
-    C2<T> e0 = c2((T)1, (T)0);
-    if constexpr (F32) {
-      const float4 p0 = reinterpret_cast<const float4 *>(L.pc)[2 * kk];
-      const float4 p1 = reinterpret_cast<const float4 *>(L.pc)[2 * kk + 1];
-      D[0] = p0.x; D[1] = p0.y; D[2] = p0.z; Dn = p0.w;
-      D2 = p1.x;
-      e0 = c2(p1.y, p1.z);
-    }
-    // stage the source nodes and coefficients of this pair
-    __syncwarp();
-    for (int b = lane; b < Q; b += 32) {
-      long ib = (long)s * Q + b;
-      SrcNode<T> sn;
-      for (int c = 0; c < 3; ++c) {
-        sn.dy[c] = F32 ? (T)L.nodes32[c * NQ + ib] : (T)L.nodes[c * NQ + ib];
-        sn.ny[c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ib] : (T)L.nodes[(3 + c) * NQ + ib];
-      }
-      sn.ay = F32 ? (T)L.nodes32[6 * NQ + ib] : (T)L.nodes[6 * NQ + ib];
-      sn.Ddy = D[0] * sn.dy[0] + D[1] * sn.dy[1] + D[2] * sn.dy[2];
-      sn.Dny = D[0] * sn.ny[0] + D[1] * sn.ny[1] + D[2] * sn.ny[2];
-      src[b] = sn;
-      for (int c = 0; c < ncr; ++c) {
-        double2 v = L.xhat[ib * A.CR + cr0 + c];
-        xs[b * NCR + c] = c2((T)v.x, (T)v.y);
-      }
-    }
-    __syncwarp();
+  for (int a0 = 0; a0 < Q; a0 += 64) {
+    // target rows of this lane in the chunk
+    T tx[2][3], tn[2][3], ta[2];
+    bool valid[2];
     for (int k = 0; k < 2; ++k) {
-      if (!valid[k]) continue;
-      const T Ddx = D[0] * tx[k][0] + D[1] * tx[k][1] + D[2] * tx[k][2];
-      const T Dnx = D[0] * tn[k][0] + D[1] * tn[k][1] + D[2] * tn[k][2];
-      C2<T> acc[NCR];
-      for (int c = 0; c < NCR; ++c) acc[c] = c2((T)0, (T)0);
-      for (int b1 = 0; b1 < A.q; ++b1) {
-        C2<T> part[NCR];
-        for (int c = 0; c < NCR; ++c) part[c] = c2((T)0, (T)0);
-        for (int b2 = 0; b2 < A.q; ++b2) {
-          const int b = b1 * A.q + b2;
-          const SrcNode<T> &y = src[b];
-          T d0 = tx[k][0] - y.dy[0], d1 = tx[k][1] - y.dy[1], d2 = tx[k][2] - y.dy[2];
-          T r2, ir, r, cph, sph;
-          T dn_x, dn_y;  // (x-y).n~x and (x-y).n~y
-          if constexpr (F32) {
-            // delta = d; x - y = D + delta
-            T Dd = Ddx - y.Ddy;
-            T dd = d0 * d0 + d1 * d1 + d2 * d2;
-            T num = (T)2 * Dd + dd;
-            r2 = D2 + num;
-            ir = rsqrtf((float)r2);
-            r = r2 * ir;
-            T del = __fdividef((float)num, (float)(r + Dn));
-            T ph = kappa * del;
-            T kq = rintf((float)(ph * (T)0.15915494309189535));
-            ph = fmaf(-(float)kq, 6.28318548202514648f, (float)ph);
-            ph = fmaf(-(float)kq, -1.7484556e-07f, (float)ph);
-            float sf, cf;
-            __sincosf((float)ph, &sf, &cf);
-            cph = cf;
-            sph = sf;
-            dn_x = Dnx + d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
-            dn_y = y.Dny + d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
-          } else {
-            r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            ir = rsqrt((double)r2);
-            r = r2 * ir;
-            double sd, cd;
-            sincos(A.kappa * (double)r, &sd, &cd);
-            cph = cd;
-            sph = sd;
-            dn_x = d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
-            dn_y = d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
-          }
-          const T f = ir * inv4pi;
-          const T kr = kappa * r;
-          const T g2 = f * ir * ir;
-          // G = e f;  G'(r)/r = e (-1 + i kappa r) f / r^2
-          const C2<T> G = c2(cph * f, sph * f);
-          const C2<T> dG = c2((-cph - sph * kr) * g2, (-sph + cph * kr) * g2);
-          if (!HARD) {
-            const T w1 = y.ay * dn_x, w2 = ta[k] * y.ay * eta;
-            // ks = dG w1 - i eta a_x a_y G
-            const C2<T> ks = c2(dG.x * w1 + G.y * w2, dG.y * w1 - G.x * w2);
-            for (int c = 0; c < NCR; ++c) part[c] = fma2(ks, xs[b * NCR + c], part[c]);
-          } else {
-            const T w1 = -ta[k] * dn_y;  // a_x (y-x).n~y
-            const C2<T> kk2 = c2(dG.x * w1, dG.y * w1);
-            for (int c = 0; c < NCR; ++c) {
-              const int ch = (cr0 + c) / A.R;
-              part[c] = fma2(ch == 0 ? kk2 : G, xs[b * NCR + c], part[c]);
+      int a = a0 + lane + 32 * k;
+      valid[k] = a < Q;
+      long ia = (long)t * Q + (valid[k] ? a : 0);
+      for (int c = 0; c < 3; ++c) {
+        tx[k][c] = F32 ? (T)L.nodes32[c * NQ + ia] : (T)L.nodes[c * NQ + ia];
+        tn[k][c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ia] : (T)L.nodes[(3 + c) * NQ + ia];
+      }
+      ta[k] = F32 ? (T)L.nodes32[6 * NQ + ia] : (T)L.nodes[6 * NQ + ia];
+    }
+    C2<T> tot[2][NCR];
+    for (int k = 0; k < 2; ++k)
+      for (int c = 0; c < NCR; ++c) tot[k][c] = c2((T)0, (T)0);
+    for (int kk = L.far_ptr[t] + warp; kk < L.far_ptr[t + 1]; kk += M2L_WARPS) {
+      const int s = L.far_src[kk];
+      // pair constants (FP32 path): D = c_t - c_s, |D|, |D|^2 and exp(i kappa |D|), from the set-up
+      T D[3] = {0, 0, 0}, Dn = 0, D2 = 0;
+      C2<T> e0 = c2((T)1, (T)0);
+      if constexpr (F32) {
+        const float4 p0 = reinterpret_cast<const float4 *>(L.pc)[2 * kk];
+        const float4 p1 = reinterpret_cast<const float4 *>(L.pc)[2 * kk + 1];
+        D[0] = p0.x; D[1] = p0.y; D[2] = p0.z; Dn = p0.w;
+        D2 = p1.x;
+        e0 = c2(p1.y, p1.z);
+      }
+      // stage the source nodes and coefficients of this pair
+      __syncwarp();
+      for (int b = lane; b < Q; b += 32) {
+        long ib = (long)s * Q + b;
+        SrcNode<T> sn;
+        for (int c = 0; c < 3; ++c) {
+          sn.dy[c] = F32 ? (T)L.nodes32[c * NQ + ib] : (T)L.nodes[c * NQ + ib];
+          sn.ny[c] = F32 ? (T)L.nodes32[(3 + c) * NQ + ib] : (T)L.nodes[(3 + c) * NQ + ib];
+        }
+        sn.ay = F32 ? (T)L.nodes32[6 * NQ + ib] : (T)L.nodes[6 * NQ + ib];
+        sn.Ddy = D[0] * sn.dy[0] + D[1] * sn.dy[1] + D[2] * sn.dy[2];
+        sn.Dny = D[0] * sn.ny[0] + D[1] * sn.ny[1] + D[2] * sn.ny[2];
+        src[b] = sn;
+        for (int c = 0; c < ncr; ++c) {
+          double2 v = L.xhat[ib * A.CR + cr0 + c];
+          xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+        }
+      }
+      __syncwarp();
+      for (int k = 0; k < 2; ++k) {
+        if (!valid[k]) continue;
+        const T Ddx = D[0] * tx[k][0] + D[1] * tx[k][1] + D[2] * tx[k][2];
+        const T Dnx = D[0] * tn[k][0] + D[1] * tn[k][1] + D[2] * tn[k][2];
+        C2<T> acc[NCR];
+        for (int c = 0; c < NCR; ++c) acc[c] = c2((T)0, (T)0);
+        for (int b1 = 0; b1 < q; ++b1) {
+          C2<T> part[NCR];
+          for (int c = 0; c < NCR; ++c) part[c] = c2((T)0, (T)0);
+          for (int b2 = 0; b2 < q; ++b2) {
+            const int b = b1 * q + b2;
+            const SrcNode<T> &y = src[b];
+            T d0 = tx[k][0] - y.dy[0], d1 = tx[k][1] - y.dy[1], d2 = tx[k][2] - y.dy[2];
+            T r2, ir, r, cph, sph;
+            T dn_x, dn_y;  // (x-y).n~x and (x-y).n~y
+            if constexpr (F32) {
+              // delta = d; x - y = D + delta
+              T Dd = Ddx - y.Ddy;
+              T dd = d0 * d0 + d1 * d1 + d2 * d2;
+              T num = (T)2 * Dd + dd;
+              r2 = D2 + num;
+              ir = rsqrtf((float)r2);
+              r = r2 * ir;
+              T del = __fdividef((float)num, (float)(r + Dn));
+              T ph = kappa * del;
+              T kq = rintf((float)(ph * (T)0.15915494309189535));
+              ph = fmaf(-(float)kq, 6.28318548202514648f, (float)ph);
+              ph = fmaf(-(float)kq, -1.7484556e-07f, (float)ph);
+              float sf, cf;
+              __sincosf((float)ph, &sf, &cf);
+              cph = cf;
+              sph = sf;
+              dn_x = Dnx + d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
+              dn_y = y.Dny + d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
+            } else {
+              r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              ir = rsqrt((double)r2);
+              r = r2 * ir;
+              double sd, cd;
+              sincos(A.kappa * (double)r, &sd, &cd);
+              cph = cd;
+              sph = sd;
+              dn_x = d0 * tn[k][0] + d1 * tn[k][1] + d2 * tn[k][2];
+              dn_y = d0 * y.ny[0] + d1 * y.ny[1] + d2 * y.ny[2];
+            }
+            const T f = ir * inv4pi;
+            const T kr = kappa * r;
+            const T g2 = f * ir * ir;
+            // G = e f;  G'(r)/r = e (-1 + i kappa r) f / r^2
+            const C2<T> G = c2(cph * f, sph * f);
+            const C2<T> dG = c2((-cph - sph * kr) * g2, (-sph + cph * kr) * g2);
+            if (!HARD) {
+              const T w1 = y.ay * dn_x, w2 = ta[k] * y.ay * eta;
+              // ks = dG w1 - i eta a_x a_y G
+              const C2<T> ks = c2(dG.x * w1 + G.y * w2, dG.y * w1 - G.x * w2);
+              for (int c = 0; c < NCR; ++c) part[c] = fma2(ks, xs[b * NCR + c], part[c]);
+            } else {
+              const T w1 = -ta[k] * dn_y;  // a_x (y-x).n~y
+              const C2<T> kk2 = c2(dG.x * w1, dG.y * w1);
+              for (int c = 0; c < NCR; ++c) {
+                const int ch = (cr0 + c) / A.R;
+                part[c] = fma2(ch == 0 ? kk2 : G, xs[b * NCR + c], part[c]);
+              }
             }
           }
+          for (int c = 0; c < NCR; ++c) acc[c] = add(acc[c], part[c]);
         }
-        for (int c = 0; c < NCR; ++c) acc[c] = add(acc[c], part[c]);
+        for (int c = 0; c < NCR; ++c) tot[k][c] = fma2(e0, acc[c], tot[k][c]);
       }
-      for (int c = 0; c < NCR; ++c) tot[k][c] = fma2(e0, acc[c], tot[k][c]);
     }
-  }
-  // reduce over the warps (the staging area is reused)
-  __syncthreads();
-  for (int k = 0; k < 2; ++k)
-    for (int c = 0; c < NCR; ++c) {
-      int a = lane + 32 * k;
-      red[(warp * 64 + a) * NCR + c] = make_double2((double)tot[k][c].x, (double)tot[k][c].y);
+    // reduce over the warps (the staging area is reused)
+    __syncthreads();
+    for (int k = 0; k < 2; ++k)
+      for (int c = 0; c < NCR; ++c) {
+        int a = lane + 32 * k;
+        red[(warp * 64 + a) * NCR + c] = make_double2((double)tot[k][c].x, (double)tot[k][c].y);
+      }
+    __syncthreads();
+    const int na = min(64, Q - a0);
+    for (int o = threadIdx.x; o < na * ncr; o += blockDim.x) {
+      int a = o / ncr, c = o % ncr;
+      double2 sum = make_double2(0, 0);
+      for (int w = 0; w < M2L_WARPS; ++w) {
+        double2 v = red[(w * 64 + a) * NCR + c];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      L.yhat[((long)t * Q + a0 + a) * A.CR + cr0 + c] = sum;
     }
-  __syncthreads();
-  for (int o = threadIdx.x; o < Q * ncr; o += blockDim.x) {
-    int a = o / ncr, c = o % ncr;
-    double2 s = make_double2(0, 0);
-    for (int w = 0; w < M2L_WARPS; ++w) {
-      double2 v = red[(w * 64 + a) * NCR + c];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    L.yhat[((long)t * Q + a) * A.CR + cr0 + c] = s;
+    __syncthreads();  // the reduction area is the staging area of the next chunk
   }
 }
 
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(M2LArgs A, int Wc) {
   while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
   const M2LLevel &L = A.lev[li];
   const int t = blockIdx.x - L.first;
-  const int Q = A.Q;
+  const int Q = L.Q;  // <= 64 (4 x 16 thread rows)
   const long NQ = (long)L.n * Q;
   const int cr0 = blockIdx.y * Wc, ch = cr0 / A.R;
   const int type = A.hard ? (ch == 0 ? 1 : 2) : 0;
@@ -352,10 +360,18 @@ __global__ void k_pair_consts(const int *__restrict__ far_ptr, const int *__rest
   o[7] = (float)exp2(12.0 - ceil(log2(bound)));
 }
 
+// shared memory of the row kernel: per warp QS source nodes and their NCR coefficients (or the
+// reduction area)
+size_t rows_smem(int QS, int ncr, bool fp32) {
+  const size_t node = fp32 ? sizeof(SrcNode<float>) : sizeof(SrcNode<double>);
+  const size_t coef = fp32 ? sizeof(C2<float>) : sizeof(C2<double>);
+  return std::max((size_t)M2L_WARPS * QS * node + (size_t)M2L_WARPS * QS * ncr * coef,
+                  (size_t)M2L_WARPS * 64 * ncr * sizeof(double2));
+}
+
 template <class T, int NCR, bool HARD>
 void launch_rows(const M2LArgs &A, int nblocks, cudaStream_t st) {
-  size_t smem = std::max((size_t)M2L_WARPS * 64 * sizeof(SrcNode<T>) + (size_t)M2L_WARPS * 64 * NCR * sizeof(C2<T>),
-                         (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
+  const size_t smem = rows_smem(A.QS, NCR, std::is_same<T, float>::value);
   auto kfn = k_m2l_rows<T, NCR, HARD>;
   IGA_CUDA(set_max_dynamic_smem(kfn, smem));
   for (int cr0 = 0; cr0 < A.CR; cr0 += NCR) {
@@ -372,8 +388,10 @@ void launch_typed(const M2LArgs &A, int nblocks, cudaStream_t st) {
     launch_rows<T, 1, false>(A, nblocks, st);
   } else if (A.CR == 2) {
     launch_rows<T, 2, false>(A, nblocks, st);
-  } else {
+  } else if (A.CR < 8 || !std::is_same<T, float>::value) {
     launch_rows<T, 4, false>(A, nblocks, st);
+  } else {
+    launch_rows<T, 8, false>(A, nblocks, st);
   }
 }
 
@@ -383,7 +401,7 @@ void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa
   for (int l = S.lmin; l <= S.L; ++l) {
     int n = S.lev[l].n;
     const long nfar = (long)S.lev[l].far_src.size();
-    k_cluster_extent<<<(n + 127) / 128, 128, 0, st>>>(d.nodes[l], d.centers[l], n, S.q * S.q,
+    k_cluster_extent<<<(n + 127) / 128, 128, 0, st>>>(d.nodes[l], d.centers[l], n, S.lev[l].q * S.lev[l].q,
                                                       reinterpret_cast<double2 *>(d.cext[l]));
     note_launch();
     if (nfar == 0) continue;
@@ -395,13 +413,21 @@ void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa
   IGA_CUDA(cudaGetLastError());
 }
 
-bool m2l_rows_supported(const HostSetup &S) { return S.q * S.q <= 64 && S.L - S.lmin + 1 <= 16; }
+bool m2l_rows_supported(const HostSetup &S, const igabem_options &o, int R) {
+  if (S.L - S.lmin + 1 > 16) return false;
+  int QS = 0;
+  for (int l = S.lmin; l <= S.L; ++l) QS = std::max(QS, S.lev[l].q * S.lev[l].q);
+  if (R > 1 && QS <= 64) return true;  // the multi-column kernel
+  const bool fp32 = o.precision != IGABEM_FP64;
+  const int CR = (S.hard ? 7 : 1) * R;
+  const int ncr = S.hard ? 7 : (CR == 1 ? 1 : CR == 2 ? 2 : (CR < 8 || !fp32) ? 4 : 8);
+  return rows_smem(QS, ncr, fp32) <= (size_t)max_optin_smem();
+}
 
 void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      bool fp32, cudaStream_t st) {
   M2LArgs A;
-  A.q = S.q;
-  A.Q = S.q * S.q;
+  A.QS = 0;
   A.R = R;
   A.CR = (S.hard ? 7 : 1) * R;
   A.kappa = o.kappa;
@@ -420,9 +446,12 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     L.yhat = reinterpret_cast<double2 *>(d.yhat[l]);
     L.n = S.lev[l].n;
     L.first = nblocks;
+    L.q = S.lev[l].q;
+    L.Q = L.q * L.q;
+    A.QS = std::max(A.QS, L.Q);
     nblocks += S.lev[l].n;
   }
-  if (R > 1) {
+  if (R > 1 && A.QS <= 64) {
     // column chunk: the largest divisor of R not above 64 (chunks never straddle two channels)
     int Wc = 1;
     for (int w = std::min(R, 64); w >= 1; --w)
@@ -431,7 +460,7 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
         break;
       }
     const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
-    size_t smem = (size_t)A.Q * A.Q * 2 * tsz + (size_t)A.Q * Wc * 2 * tsz + (size_t)A.Q * 16 * tsz;
+    size_t smem = (size_t)A.QS * A.QS * 2 * tsz + (size_t)A.QS * Wc * 2 * tsz + (size_t)A.QS * 16 * tsz;
     dim3 grid(nblocks, A.CR / Wc);
     if (fp32) {
       IGA_CUDA(set_max_dynamic_smem(k_m2l_gemm<float>, smem));

@@ -46,7 +46,9 @@ namespace igabem {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;                            // 16 warps: warp 0 issues, 15 generate
+constexpr int TC_NQW = TC_THREADS / 128;                   // warps per tensor-memory lane quadrant
+constexpr int TC_MAXC = 16 / TC_NQW;                       // 16-column accumulator chunks per thread
 constexpr int TC_NS = 64;                                  // columns of a slice (MMA N <= 64)
 constexpr int TC_MAX_SLOTS = 8;
 constexpr int TC_GROUP = 4;                                // slices per CTA (256 accumulator columns)
@@ -371,19 +373,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TCArgs A) {
   };
 
   // FP32 accumulators: TMEM lane 32 (warp % 4) + lane; chunk c of the thread holds the group's
-  // columns 16 (half + 2 c) .. 16 (half + 2 c) + 15 (half = warp / 4)
-  float acc[8][16];
+  // columns 16 (cq + NQW c) .. 16 (cq + NQW c) + 15 (cq = warp / 4, NQW warps per lane quadrant)
+  float acc[TC_MAXC][16];
 #pragma unroll
-  for (int c = 0; c < 8; ++c)
+  for (int c = 0; c < TC_MAXC; ++c)
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[c][i] = 0.f;
-  const int half = warp >> 2, nch = (W / 16 - half + 1) / 2;
+  const int cq = warp >> 2, nch = (W / 16 - cq + TC_NQW - 1) / TC_NQW;
   auto drain = [&](int p) {  // adds pair p's buffer, scaled back, to the accumulators
     const int kk = k0 + p;
     const float inv = 1.0f / (L.pc[8L * kk + 7] * L.bscale[L.far_src[kk]]);
-    const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((p & 1) * A.wmax + 16 * half);
+    const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((p & 1) * A.wmax + 16 * cq);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < TC_MAXC; ++c) {
       if (c < nch) {
         uint32_t r[16];
         asm volatile(
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TCArgs A) {
             "[%16];"
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(base + 32 * c));
+            : "r"(base + 16 * TC_NQW * c));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc[c][i] = fmaf(__uint_as_float(r[i]), inv, acc[c][i]);
@@ -463,8 +465,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TCArgs A) {
       __syncthreads();
       if (a < Q) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int col = 16 * (half + 2 * c) - w0;
+        for (int c = 0; c < TC_MAXC; ++c) {
+          const int col = 16 * (cq + TC_NQW * c) - w0;
           if (c < nch && col >= 0 && col < 128)
 #pragma unroll
             for (int i = 0; i < 16; ++i)
@@ -585,6 +587,8 @@ void launch_wait_selftest(int *status, double limit_s, cudaStream_t st) {
 bool m2l_tc_supported(const HostSetup &S, int R) {
   const int Q = S.q * S.q, CR = (S.hard ? 7 : 1) * R;
   if (Q > 64 || R % 16 != 0 || S.L - S.lmin + 1 > 16) return false;
+  for (int l = S.lmin; l <= S.L; ++l)
+    if (S.lev[l].q != S.q) return false;  // one operand layout per launch: the same q on every level
   // slice count: hard R <= 64 gives 1 + 6, soft CR <= 512 gives 8
   if ((S.hard && R > TC_NS) || (!S.hard && CR > TC_MAX_SLOTS * TC_NS)) return false;
   return tc_smem_bytes(tc_kh(Q)) <= (size_t)max_optin_smem();

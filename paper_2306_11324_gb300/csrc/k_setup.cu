@@ -611,12 +611,13 @@ void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStrea
   note_launch();
 }
 
-void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st) {
+void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st) {
   Phase ph(d.prof, IGABEM_PH_SETUP_TABLES, st);
   for (int l = 0; l <= S.L; ++l) {
-    long tot = (long)S.lev[l].n * S.q * S.q;
+    const int q = S.lev[l].q;
+    long tot = (long)S.lev[l].n * q * q;
     int grid = (int)std::min<long>((tot + 255) / 256, 152L * 16);
-    k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, cheb, d.centers[l], S.lev[l].n, l, S.q,
+    k_node_geometry<<<grid, 256, 0, st>>>(d.edeg, d.eoff, d.ebez, d.chebl[l], d.centers[l], S.lev[l].n, l, q,
                                           S.n1, d.nodes[l], d.nodes32[l]);
     note_launch();
   }

@@ -113,6 +113,112 @@ __global__ void k_farfield(RhsArgs A, const double2 *__restrict__ rho, long npts
   if (threadIdx.x == 0) uinf[(long)k * gridDim.y + r] = cscale(red[0], 0.25 / IGA_PI);
 }
 
+// Far field in the mixed precisions, for many directions: the Gauss points are taken in groups of
+// FE x FE elements with a reference point C (the group's first Gauss point, FP64); the phase
+// kappa x^.y = kappa x^.C + kappa x^.(y - C) splits into a per-(direction, group) factor exp(-i kappa
+// x^.C) in FP64 and per-point exponentials of the small offsets in FP32, summed in FP32 per group and
+// direction, scaled by the FP64 factor and added over the groups in FP64.  Block: one group and 64
+// directions, 4 point lanes per direction, up to 8 right-hand sides per pass.
+constexpr int FF_DIRS = 64, FF_LANES = 4, FF_COLS = 8, FF_CHUNK = 256;
+
+__global__ void __launch_bounds__(256) k_farfield32(RhsArgs A, const double2 *__restrict__ rho, int fe, int n_dir,
+                                                    const double *__restrict__ xhat, double2 *__restrict__ uinf) {
+  __shared__ float4 pts[FF_CHUNK];               // y - C (3), a
+  __shared__ float4 nrm[FF_CHUNK];               // n~ (3)
+  __shared__ float2 rs[FF_CHUNK * FF_COLS];      // weighted density (FP32)
+  __shared__ float2 red[FF_LANES][FF_DIRS][FF_COLS];
+  const int nq = A.ng * A.ng, ge = 1 << fe, ngr1 = A.n1 >> fe;
+  const int g = blockIdx.x, j = g / (ngr1 * ngr1), gx = (g / ngr1) % ngr1, gy = g % ngr1;
+  const int npts = ge * ge * nq;
+  const int dl = threadIdx.x % FF_DIRS, lane = threadIdx.x / FF_DIRS;
+  const int k = blockIdx.y * FF_DIRS + dl;
+  const bool kv = k < n_dir;
+  // reference point: the first Gauss point of the group
+  const long e0 = ((long)j * A.n1 + gx * ge) * A.n1 + gy * ge;
+  const double C0 = A.gpx[e0 * nq], C1 = A.gpx[A.gst + e0 * nq], C2v = A.gpx[2 * A.gst + e0 * nq];
+  double xh[3] = {0.0, 0.0, 1.0};
+  if (kv) {
+    xh[0] = xhat[3 * k];
+    xh[1] = xhat[3 * k + 1];
+    xh[2] = xhat[3 * k + 2];
+  }
+  const float kx0 = (float)(-A.kappa * xh[0]), kx1 = (float)(-A.kappa * xh[1]), kx2 = (float)(-A.kappa * xh[2]);
+  for (int c0 = 0; c0 < A.R; c0 += FF_COLS) {
+    const int nc = min(FF_COLS, A.R - c0);
+    float2 acc[FF_COLS];
+#pragma unroll
+    for (int c = 0; c < FF_COLS; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int p0 = 0; p0 < npts; p0 += FF_CHUNK) {
+      const int np = min(FF_CHUNK, npts - p0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int pi = p0 + i, el = pi / nq, q = pi % nq;
+        const long e = ((long)j * A.n1 + gx * ge + el / ge) * A.n1 + gy * ge + el % ge;
+        const long iq = e * nq + q;
+        pts[i] = make_float4((float)(A.gpx[iq] - C0), (float)(A.gpx[A.gst + iq] - C1),
+                             (float)(A.gpx[2 * A.gst + iq] - C2v), (float)A.gpa[iq]);
+        nrm[i] = make_float4((float)A.gpn[iq], (float)A.gpn[A.gst + iq], (float)A.gpn[2 * A.gst + iq], 0.f);
+      }
+      for (int i = threadIdx.x; i < np * FF_COLS; i += blockDim.x) {
+        const int pi = i / FF_COLS, c = i % FF_COLS;
+        const int el = (p0 + pi) / nq, q = (p0 + pi) % nq;
+        const long e = ((long)j * A.n1 + gx * ge + el / ge) * A.n1 + gy * ge + el % ge;
+        float2 v = make_float2(0.f, 0.f);
+        if (c < nc) {
+          const double2 r = rho[(e * nq + q) * A.R + c0 + c];
+          v = make_float2((float)r.x, (float)r.y);
+        }
+        rs[i] = v;
+      }
+      __syncthreads();
+      if (kv) {
+        for (int i = lane; i < np; i += FF_LANES) {
+          const float4 y = pts[i];
+          float ph = fmaf(kx0, y.x, fmaf(kx1, y.y, kx2 * y.z));
+          const float kq = rintf(ph * 0.15915494309189535f);
+          ph = fmaf(-kq, 6.28318548202514648f, ph);
+          ph = fmaf(-kq, -1.7484556e-07f, ph);
+          float s, c;
+          __sincosf(ph, &s, &c);
+          float2 E;
+          if (A.hard) {  // -i kappa (x^.n~) e
+            const float4 n = nrm[i];
+            const float xn = -fmaf(kx0, n.x, fmaf(kx1, n.y, kx2 * n.z));  // kappa x^.n~
+            E = make_float2(xn * s, -xn * c);
+          } else {       // -a e
+            E = make_float2(-y.w * c, -y.w * s);
+          }
+#pragma unroll
+          for (int cc = 0; cc < FF_COLS; ++cc) {
+            const float2 r = rs[i * FF_COLS + cc];
+            acc[cc].x = fmaf(E.x, r.x, fmaf(-E.y, r.y, acc[cc].x));
+            acc[cc].y = fmaf(E.x, r.y, fmaf(E.y, r.x, acc[cc].y));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < FF_COLS; ++c) red[lane][dl][c] = acc[c];
+    __syncthreads();
+    for (int i = threadIdx.x; i < FF_DIRS * FF_COLS; i += blockDim.x) {
+      const int d = i / FF_COLS, c = i % FF_COLS, kk = blockIdx.y * FF_DIRS + d;
+      if (kk >= n_dir || c >= nc) continue;
+      double sx = 0.0, sy = 0.0;
+      for (int l = 0; l < FF_LANES; ++l) {
+        sx += (double)red[l][d][c].x;
+        sy += (double)red[l][d][c].y;
+      }
+      // the group factor exp(-i kappa x^.C) of direction kk (recomputed by this thread)
+      double s2, c2;
+      sincos(-A.kappa * (xhat[3 * kk] * C0 + xhat[3 * kk + 1] * C1 + xhat[3 * kk + 2] * C2v), &s2, &c2);
+      const double vx = (c2 * sx - s2 * sy) * (0.25 / IGA_PI), vy = (c2 * sy + s2 * sx) * (0.25 / IGA_PI);
+      atomicAdd(&uinf[(long)kk * A.R + c0 + c].x, vx);
+      atomicAdd(&uinf[(long)kk * A.R + c0 + c].y, vy);
+    }
+    __syncthreads();
+  }
+}
+
 // ----------------------------------------------------------------------------------------------
 // GMRES vector kernels; vectors are [N][R] complex, V_i = V + i N R
 
@@ -174,6 +280,163 @@ __global__ void k_sqrt_re(const double2 *__restrict__ h, double *__restrict__ nr
   if (r < R) nrm[r] = sqrt(fmax(h[r].x, 0.0));
 }
 
+// ---- device-side GMRES iteration: the Arnoldi index j lives on the device, so one captured graph
+// serves every iteration of a cycle (the kernels read j; grids are sized for the whole cycle) ----
+
+// partial sums of h[i][r] = sum_n conj(V_i[n][r]) w[n][r] for i <= j (blocks of i > j return)
+__global__ void k_multidot_partial_dev(const double2 *__restrict__ V, const int *__restrict__ jdev,
+                                       const double2 *__restrict__ w, long N, int R, double2 *__restrict__ red) {
+  extern __shared__ double2 shd[];
+  const int i = blockIdx.y, g = blockIdx.x, G = gridDim.x;
+  if (i > *jdev) return;
+  const int nthr = (blockDim.x / R) * R;
+  const double2 *Vi = V + (size_t)i * N * R;
+  long chunk = (N + G - 1) / G, n0 = g * chunk, n1 = min(N, n0 + chunk);
+  double2 acc = cmk(0, 0);
+  if (threadIdx.x < nthr) {
+    for (long idx = n0 * R + threadIdx.x; idx < n1 * R; idx += nthr) acc = cadd(acc, cconjmul(Vi[idx], w[idx]));
+  }
+  shd[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < R) {
+    double2 sum = cmk(0, 0);
+    for (int t = threadIdx.x; t < nthr; t += R) sum = cadd(sum, shd[t]);
+    red[((size_t)i * G + g) * R + threadIdx.x] = sum;
+  }
+}
+
+// h[i][r] for i <= j (zero above j), from the partial sums
+__global__ void k_multidot_final_dev(const double2 *__restrict__ red, const int *__restrict__ jdev, int nmax, int G,
+                                     int R, double2 *__restrict__ h) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nmax * R) return;
+  int i = o / R, r = o % R;
+  double2 sum = cmk(0, 0);
+  if (i <= *jdev)
+    for (int g = 0; g < G; ++g) sum = cadd(sum, red[((size_t)i * G + g) * R + r]);
+  h[o] = sum;
+}
+
+// w[n][r] -= sum_{i <= j} V_i[n][r] h[i][r]
+__global__ void k_multiaxpy_dev(const double2 *__restrict__ V, const int *__restrict__ jdev,
+                                const double2 *__restrict__ h, double2 *__restrict__ w, long N, int R) {
+  const int nv = *jdev + 1;
+  GRID_STRIDE(o, N * R) {
+    int r = int(o % R);
+    double2 acc = w[o];
+    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(V[(size_t)i * N * R + o], h[i * R + r]));
+    w[o] = acc;
+  }
+}
+
+// dst = V_j
+__global__ void k_copy_vj(const double2 *__restrict__ V, const int *__restrict__ jdev, double2 *__restrict__ dst,
+                          long NR) {
+  const double2 *src = V + (size_t)(*jdev) * NR;
+  GRID_STRIDE(o, NR) dst[o] = src[o];
+}
+
+// V_{j} = s w for the (already advanced) index j
+__global__ void k_scale_vj(const double2 *__restrict__ w, const double *__restrict__ s, double2 *__restrict__ V,
+                           const int *__restrict__ jdev, long N, int R) {
+  double2 *dst = V + (size_t)(*jdev) * N * R;
+  GRID_STRIDE(o, N * R) dst[o] = cscale(w[o], s[o % R]);
+}
+
+// cycle start: H, rotations and g cleared, g_0 = beta for the active columns, s = 1 / beta, j = 0
+__global__ void k_gm_init(GmDev G, const double *__restrict__ beta, const int *__restrict__ active) {
+  const int R = G.R, m = G.m;
+  GRID_STRIDE(o, (long)(m + 1) * m * R) G.H[o] = cmk(0, 0);
+  GRID_STRIDE(o, (long)m * R) {
+    G.cs[o] = cmk(1, 0);
+    G.sn[o] = cmk(0, 0);
+  }
+  GRID_STRIDE(o, (long)(m + 1) * R) G.g[o] = o < R && active[o] ? cmk(beta[o], 0) : cmk(0, 0);
+  GRID_STRIDE(o, (long)R) {
+    G.done[o] = active[o] ? 0 : 1;
+    G.k[o] = 0;
+    G.s[o] = active[o] ? 1.0 / beta[o] : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *G.j = 0;
+    G.flags[0] = 0;
+    G.flags[1] = 0;
+  }
+}
+
+// Arnoldi column j of every active right-hand side: h = hA + hB (the two Gram-Schmidt passes), the
+// new column of H rotated by the previous Givens rotations, the new rotation, g updated, the
+// convergence test |g_{j+1}| <= tol ||b||; s = 1 / h_{j+1,j} for the next basis vector (0 for finished
+// columns); then j advances.  One block; flags[0] = every column finished, flags[1] = non-finite met.
+__global__ void k_gm_arnoldi(GmDev G) {
+  const int R = G.R, m = G.m, j = *G.j;
+  __shared__ int all_done, bad;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    if (G.done[r]) {
+      G.s[r] = 0.0;
+      continue;
+    }
+    const double hn = G.nrm[r];
+    double2 *Hc = G.H + (size_t)r;  // H[i][jj][r] at ((i * m) + jj) * R + r
+    for (int i = 0; i <= j; ++i) Hc[((size_t)i * m + j) * R] = cadd(G.hA[i * R + r], G.hB[i * R + r]);
+    Hc[((size_t)(j + 1) * m + j) * R] = cmk(hn, 0);
+    for (int i = 0; i < j; ++i) {
+      const double2 c = G.cs[i * R + r], sv = G.sn[i * R + r];
+      const double2 a = Hc[((size_t)i * m + j) * R], b = Hc[((size_t)(i + 1) * m + j) * R];
+      // [c, s; -conj(s), conj(c)] (a, b)
+      Hc[((size_t)i * m + j) * R] = cadd(cmul(c, a), cmul(sv, b));
+      Hc[((size_t)(i + 1) * m + j) * R] = cadd(cmul(cmk(-sv.x, sv.y), a), cmul(cmk(c.x, -c.y), b));
+    }
+    const double2 a = Hc[((size_t)j * m + j) * R], b = Hc[((size_t)(j + 1) * m + j) * R];
+    const double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+    const double2 c = den > 0 ? cmk(a.x / den, -a.y / den) : cmk(1, 0);
+    const double2 sv = den > 0 ? cmk(b.x / den, -b.y / den) : cmk(0, 0);
+    G.cs[j * R + r] = c;
+    G.sn[j * R + r] = sv;
+    Hc[((size_t)j * m + j) * R] = cmk(den, 0);
+    Hc[((size_t)(j + 1) * m + j) * R] = cmk(0, 0);
+    const double2 gj = G.g[j * R + r];
+    G.g[(j + 1) * R + r] = cmul(cmk(-sv.x, sv.y), gj);
+    G.g[j * R + r] = cmul(c, gj);
+    G.k[r] = j + 1;
+    const int its = ++G.its[r];
+    const double2 gn = G.g[(j + 1) * R + r];
+    const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
+    if (!isfinite(res) || !isfinite(hn)) atomicExch(&bad, 1);
+    const bool done = res <= G.tol * G.bn[r] || its >= G.maxit || hn == 0.0 || j + 1 >= m;
+    G.done[r] = done ? 1 : 0;
+    G.s[r] = (!done && hn > 0) ? 1.0 / hn : 0.0;
+    if (!done) atomicExch(&all_done, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    G.flags[0] = all_done;
+    G.flags[1] = bad;
+    *G.j = j + 1;
+  }
+}
+
+// y = H^-1 g per column over its Krylov dimension k (zero beyond)
+__global__ void k_gm_solve(GmDev G) {
+  const int R = G.R, m = G.m;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    const int kc = G.k[r];
+    for (int i = m; i >= 0; --i) G.y[i * R + r] = cmk(0, 0);
+    for (int i = kc - 1; i >= 0; --i) {
+      double2 acc = G.g[i * R + r];
+      for (int q = i + 1; q < kc; ++q) acc = csub(acc, cmul(G.H[((size_t)i * m + q) * R + r], G.y[q * R + r]));
+      const double2 d = G.H[((size_t)i * m + i) * R + r];
+      const double dd = d.x * d.x + d.y * d.y;
+      G.y[i * R + r] = dd > 0 ? cmk((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd) : cmk(0, 0);
+    }
+  }
+}
+
 RhsArgs rhs_args(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R) {
   RhsArgs A;
   A.gpx = d.gpx; A.gpn = d.gpn; A.gpa = d.gpa; A.phi1 = d.phi1; A.gw = d.gw;
@@ -206,6 +469,16 @@ void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_op
   double2 *rho = reinterpret_cast<double2 *>(scratch);  // E nq R complex values
   k_density<<<grid_for(npts * R), 256, 0, st>>>(A, d.x2g, reinterpret_cast<const double2 *>(dens), S.E, rho);
   note_launch();
+  if (o.precision != IGABEM_FP64) {
+    const int fe = std::min(S.m, 4);
+    const long ngroups = (long)S.np << (2 * (S.m - fe));
+    IGA_CUDA(cudaMemsetAsync(uinf, 0, sizeof(double2) * (size_t)n_dir * R, st));
+    dim3 g32((unsigned)ngroups, (unsigned)((n_dir + FF_DIRS - 1) / FF_DIRS));
+    k_farfield32<<<g32, 256, 0, st>>>(A, rho, fe, n_dir, xhat_dev, reinterpret_cast<double2 *>(uinf));
+    note_launch();
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   dim3 grid(n_dir, R);
   k_farfield<<<grid, 256, 0, st>>>(A, rho, npts, xhat_dev, reinterpret_cast<double2 *>(uinf));
   note_launch();
@@ -224,6 +497,48 @@ void launch_multidot(const double *V, int nv, const double *w, long N, int R, do
                                                          RED_BLOCKS, R, reinterpret_cast<double2 *>(h));
   note_launch();
   IGA_CUDA(cudaGetLastError());
+}
+
+void launch_gm_iteration_tail(const GmDev &G, double *red, long N, cudaStream_t st) {
+  // two classical Gram-Schmidt passes against V_0..V_j, the norm, the Arnoldi update, the next basis vector
+  const int R = G.R, threads = std::max(R, (256 / R) * R);
+  for (int pass = 0; pass < 2; ++pass) {
+    double2 *h = pass ? G.hB : G.hA;
+    dim3 grid(RED_BLOCKS, G.m + 1);
+    k_multidot_partial_dev<<<grid, threads, threads * sizeof(double2), st>>>(
+        reinterpret_cast<const double2 *>(G.V), G.j, reinterpret_cast<const double2 *>(G.w), N, R,
+        reinterpret_cast<double2 *>(red));
+    note_launch();
+    k_multidot_final_dev<<<((G.m + 1) * R + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2 *>(red), G.j,
+                                                                     G.m + 1, RED_BLOCKS, R, h);
+    note_launch();
+    k_multiaxpy_dev<<<grid_for(N * R), 256, 0, st>>>(reinterpret_cast<const double2 *>(G.V), G.j, h,
+                                                      reinterpret_cast<double2 *>(G.w), N, R);
+    note_launch();
+  }
+  launch_norms(G.w, N, R, red, G.nrm, st);
+  k_gm_arnoldi<<<1, 1024, 0, st>>>(G);
+  note_launch();
+  k_scale_vj<<<grid_for(N * R), 256, 0, st>>>(reinterpret_cast<const double2 *>(G.w), G.s,
+                                               reinterpret_cast<double2 *>(G.V), G.j, N, R);
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
+void launch_copy_vj(const GmDev &G, double *dst, long N, cudaStream_t st) {
+  k_copy_vj<<<grid_for(N * G.R), 256, 0, st>>>(reinterpret_cast<const double2 *>(G.V), G.j,
+                                                 reinterpret_cast<double2 *>(dst), N * G.R);
+  note_launch();
+}
+
+void launch_gm_init(const GmDev &G, const double *beta, const int *active, cudaStream_t st) {
+  k_gm_init<<<grid_for((long)(G.m + 1) * G.m * G.R), 256, 0, st>>>(G, beta, active);
+  note_launch();
+}
+
+void launch_gm_solve(const GmDev &G, cudaStream_t st) {
+  k_gm_solve<<<(G.R + 127) / 128, 128, 0, st>>>(G);
+  note_launch();
 }
 
 void launch_multiaxpy(const double *V, int nv, const double *h, double *w, long N, int R, cudaStream_t st) {

@@ -7,9 +7,9 @@ namespace igabem {
 
 // set-up (k_setup.cu)
 void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
-void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, double *cheb, cudaStream_t st);
+void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
 void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, double eta, cudaStream_t st);
-bool m2l_rows_supported(const HostSetup &S);
+bool m2l_rows_supported(const HostSetup &S, const igabem_options &o, int R);
 void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      bool fp32, cudaStream_t st);
 // tensor-core M2L for R right-hand sides (k_m2l_tc.cu); yhat from xhat through d.tc_bimg
@@ -69,5 +69,31 @@ void launch_norms(const double *w, long N, int R, double *red, double *nrm, cuda
 void launch_scale(const double *w, const double *s, double *dst, long N, int R, cudaStream_t st);
 // r = b - y
 void launch_sub(const double *b, const double *y, double *r, long n, cudaStream_t st);
+
+// Device-side state of GMRES(m) for R columns (all device memory): the Arnoldi index j of the cycle,
+// the rotated Hessenberg matrices, Givens rotations, g, the per-column Krylov dimension, iteration count
+// and finished flag.
+struct GmDev {
+  int m, R, maxit;
+  double tol;
+  int *j;                     // Arnoldi index
+  int *k, *its, *done;        // [R]
+  int *flags;                 // [2]: every column finished; non-finite value met
+  double2 *H;                 // [(m+1)][m][R]
+  double2 *cs, *sn;           // [m][R]
+  double2 *g, *y;             // [(m+1)][R]
+  double2 *hA, *hB;           // [(m+1)][R]: the two Gram-Schmidt passes
+  double *nrm, *s, *bn;       // [R]
+  double *V, *w;              // basis [(m+1)][N][R] and the new vector [N][R]
+};
+// after the matrix-vector product w = A V_j: two CGS passes, the norm, the Arnoldi / Givens update
+// (k_gm_arnoldi), V_{j+1} = w / h_{j+1,j}; j advances on the device
+void launch_gm_iteration_tail(const GmDev &G, double *red, long N, cudaStream_t st);
+// dst = V_j (j read on the device)
+void launch_copy_vj(const GmDev &G, double *dst, long N, cudaStream_t st);
+// cycle start from beta [R] and the active flags [R] (device)
+void launch_gm_init(const GmDev &G, const double *beta, const int *active, cudaStream_t st);
+// y = H^-1 g per column
+void launch_gm_solve(const GmDev &G, cudaStream_t st);
 
 }  // namespace igabem

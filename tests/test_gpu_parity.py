@@ -251,3 +251,56 @@ def test_preconditioned_solve_matches_lu(hard, n_dirs):
         B.igabem_problem_destroy(prob)
     if not hard:                   # second-kind equation: the local blocks capture it well
         assert its[1] < its[0]
+
+
+@functools.lru_cache(maxsize=None)
+def _adaptive_rows():
+    """Oracle rows of the mode-B product with level-adaptive q: unit sphere m = 3, kappa = 16,
+    cheb_q = 4, cap 2, q_max = 10, element leaves: far blocks on level 2 with 10 x 10 points and on
+    level 3 with 6 x 6 (three columns)."""
+    sp = C.sphere_space(3, 1)
+    x = inputs.random_complex(sp.N, seed=93, cols=3)
+    tree = fmm.ClusterTree(sp.mesh, 3, 0.5, 4, 16.0, kappa_cap=2.0, q_max=10)
+    rows = np.array([0, 123, sp.N // 2, sp.N - 1])
+    return tree, rows, fmm.cfie_rows(sp, 16.0, 16.0, False, x, rows, tree=tree)
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED_FP32])
+def test_level_adaptive_interpolation_matches_oracle(prec):
+    """Level-adaptive q (NEXT-4): the per-level q and far-pair counts equal the oracle tree's; the
+    product with 10 x 10 nodes on level 2 (more than 64 per cluster: row chunks in the M2L), formed
+    from and evaluated at the Gauss points there (its children use 6 x 6), against the oracle rows,
+    for one column and three columns."""
+    prob, info = G.problem(level_m=3, degree_p=1, kappa=16.0, eta_cfie=16.0, cheb_q=4, kappa_cap=2.0, q_max=10,
+                           leaf_offset=0, eta_adm=0.5, precision=prec)
+    tree, rows, ref3 = _adaptive_rows()
+    assert info["level_q"][2:] == tree.ql[2:] == [10, 6]
+    assert info["level_far"] == [len(f) for f in tree.far]
+    sp = C.sphere_space(3, 1)
+    x = inputs.random_complex(sp.N, seed=93, cols=3)
+    tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
+    y3 = B.igabem_matvec(prob, x)
+    for col in range(3):
+        ref = ref3[:, col]
+        y1 = B.igabem_matvec(prob, np.ascontiguousarray(x[:, col]))
+        assert np.abs(y1[rows] - ref).max() / np.abs(ref).max() < tol
+        assert np.abs(y3[rows, col] - ref).max() / np.abs(ref).max() < tol
+    B.igabem_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("pc", [0, 1])
+def test_graph_captured_gmres_equals_eager_launches(pc):
+    """The GMRES iteration captured once as a CUDA graph (state on the device, flags read one iteration
+    behind) gives the same iterates as the same kernels launched one by one: equal iteration counts and
+    densities equal to rounding, for three directions that converge at different iterations."""
+    d = inputs.fibonacci_directions(3)
+    out = {}
+    for ng in (0, 1):
+        prob, info = G.problem(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, cheb_q=5, leaf_offset=1, eta_adm=0.5,
+                               tol=1e-9, gmres_restart=8, precond=pc, no_graph=ng)
+        x, sinfo = B.igabem_solve(prob, d, info["n_dofs"])
+        assert sinfo["rel_residual"] <= 1e-9
+        out[ng] = (x, sinfo)
+        B.igabem_problem_destroy(prob)
+    assert out[0][1]["iterations"] == out[1][1]["iterations"] > 8     # more than one restart cycle
+    assert G.rel(out[0][0], out[1][0]) < 1e-12

@@ -220,7 +220,10 @@ int igabem_farfield(igabem_problem *prob, int n_rhs, const void *density, int n_
  * requests already running; a request that arrives while others run starts as soon as a slot and
  * memory are free.  Each request runs the whole path (set-up, right-hand sides for its incident
  * directions, GMRES, far field at its directions) with its own options; its result does not depend
- * on what else runs.
+ * on what else runs.  Requests for the same problem (same geometry handle and identical options) are
+ * batched: those waiting together are merged into one multi-column GMRES solve (shared matrix-vector
+ * products), and a finished problem stays resident (tree, near-field blocks) for later requests with
+ * the same key, in a least-recently-used cache that counts against the memory budget.
  * ------------------------------------------------------------------------------------------------ */
 typedef struct igabem_server igabem_server;
 typedef struct igabem_request igabem_request;
@@ -229,9 +232,12 @@ typedef struct {
   long submitted, completed, failed;
   double p50_ms, p99_ms, mean_ms; /* latency from submission to completion of completed requests */
   double solves_per_s;            /* completed requests / (last completion - first submission) */
-  size_t peak_bytes;              /* largest admitted device memory at one time */
+  size_t peak_bytes;              /* largest admitted device memory at one time (resident problems included) */
   size_t budget_bytes;
   int peak_active;                /* largest number of requests running at one time */
+  long merged;                    /* requests that joined another request's solve (same problem) */
+  long cache_hits;                /* requests served by a resident problem (no set-up) */
+  long resident;                  /* problems resident now */
 } igabem_server_stats;
 
 /* Starts a server with max_active worker threads (1..64) on the context's device.  memory_budget in

@@ -57,7 +57,8 @@ class igabem_profile(ctypes.Structure):
 class igabem_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_long), ("completed", c_long), ("failed", c_long), ("p50_ms", c_double),
                 ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
-                ("peak_bytes", c_size_t), ("budget_bytes", c_size_t), ("peak_active", c_int)]
+                ("peak_bytes", c_size_t), ("budget_bytes", c_size_t), ("peak_active", c_int),
+                ("merged", c_long), ("cache_hits", c_long), ("resident", c_long)]
 
 
 class igabem_peaks(ctypes.Structure):

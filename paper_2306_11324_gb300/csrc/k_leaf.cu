@@ -185,6 +185,141 @@ __global__ void __launch_bounds__(256) k_near_mrhs(LeafArgs A, const int *__rest
     }
 }
 
+// Near-field SpMV for up to 16 columns per block: one thread block per (target leaf, column chunk),
+// one thread per (local function i, CPT adjacent columns).  The near blocks of the target's list are
+// staged in shared memory by asynchronous copies (cp.async), double buffered: block k + 1 is in flight
+// while block k is multiplied, one barrier per block; the source coefficients (converted to the block
+// precision) go through registers.  One block's sum is formed in the storage precision, the blocks
+// are summed in FP64 (as in k_near_spmv2).
+template <int BYTES>
+__device__ inline void cp_async(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <class BT, int CPT>
+__global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__restrict__ near_ptr,
+                                                   const int *__restrict__ near_src, const BT *__restrict__ blk,
+                                                   const double2 *__restrict__ xX, double2 *__restrict__ yleaf,
+                                                   int nL, int Rc) {
+  using RT = decltype(BT::x);
+  extern __shared__ __align__(16) unsigned char smk[];
+  BT *Bs = reinterpret_cast<BT *>(smk);              // [2][nL * nL] (block column-major: [j][i])
+  BT *Xs = Bs + 2 * nL * nL;                         // [2][nL][Rc]
+  const int t = blockIdx.x, r0 = blockIdx.y * Rc, rc = min(Rc, A.R - r0);
+  const int nlL = 1 << A.L, e1 = 1 << A.b;
+  const int nthr = blockDim.x, nB = nL * nL, nX = nL * Rc;
+  const int i = threadIdx.x % nL, cg = threadIdx.x / nL, c0 = cg * CPT;
+  const bool active = cg * CPT < Rc;
+  const int kb = near_ptr[t], ke = near_ptr[t + 1];
+  BT rx[2];
+  auto issue_block = [&](int k, int buf) {  // asynchronous copy of near block k into buffer buf
+    const BT *Bk = blk + (size_t)k * nB;
+    BT *dst = Bs + buf * nB;
+    for (int e = threadIdx.x; e < nB; e += nthr) cp_async<sizeof(BT)>(dst + e, Bk + e);
+    cp_async_commit();
+  };
+  auto fetch_x = [&](int k) {  // this thread's share of block k's source coefficients
+    const int s = near_src[k];
+    const int js = s / (nlL * nlL), cx = (s / nlL) % nlL, cy = s % nlL;
+    const long base = ((long)js * A.nb + cx * e1) * A.nb + cy * e1;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = threadIdx.x + u * nthr;
+      rx[u].x = 0;
+      rx[u].y = 0;
+      if (e < nX) {
+        const int jj = e / Rc, c = e % Rc, al = jj / A.nL1, be = jj % A.nL1;
+        if (c < rc) {
+          const double2 xd = xX[(base + (long)al * A.nb + be) * A.R + r0 + c];
+          rx[u].x = (RT)xd.x;
+          rx[u].y = (RT)xd.y;
+        }
+      }
+    }
+  };
+  auto store_x = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = threadIdx.x + u * nthr;
+      if (e < nX) Xs[buf * nX + e] = rx[u];
+    }
+  };
+  double2 acc[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) acc[c] = make_double2(0.0, 0.0);
+  if (kb < ke) {
+    issue_block(kb, 0);
+    fetch_x(kb);
+    store_x(0);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  if (kb + 1 < ke) {
+    issue_block(kb + 1, 1);
+    fetch_x(kb + 1);
+  }
+  for (int k = kb; k < ke; ++k) {
+    const int cur = (k - kb) & 1;
+    if (active) {
+      RT px[CPT], py[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) px[c] = py[c] = 0;
+      const BT *B = Bs + cur * nB + i;
+      const BT *X = Xs + cur * nX + c0;
+      for (int jj = 0; jj < nL; ++jj) {
+        const BT bv = B[jj * nL];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          if (c0 + c >= Rc) break;  // odd chunk width: the last thread of a row has one column
+          const BT xv = X[jj * Rc + c];
+          px[c] += bv.x * xv.x - bv.y * xv.y;
+          py[c] += bv.x * xv.y + bv.y * xv.x;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        acc[c].x += (double)px[c];
+        acc[c].y += (double)py[c];
+      }
+    }
+    if (k + 1 < ke) store_x(cur ^ 1);  // coefficients of block k + 1
+    cp_async_wait_all();                // block k + 1 has landed
+    __syncthreads();                    // ... for every thread; buffer cur is free
+    if (k + 2 < ke) {
+      issue_block(k + 2, cur);
+      fetch_x(k + 2);
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (c0 + c < rc) yleaf[((size_t)t * nL + i) * A.R + r0 + c0 + c] = acc[c];
+  }
+}
+
+// launch of k_near_cols: columns per thread 2 (1 for a single column), chunks of up to 16 columns
+template <class BT>
+bool launch_near_cols(const LeafArgs &A, const int *near_ptr, const int *near_src, const BT *blk, const double2 *xX,
+                      double2 *yleaf, int nleaf, int nL, int R, cudaStream_t st) {
+  const int Rc = std::min(R, 16), cpt = Rc >= 2 ? 2 : 1;
+  const int threads = ((nL * ((Rc + cpt - 1) / cpt) + 31) / 32) * 32;
+  if (threads > 576 || (size_t)nL * Rc > 2 * (size_t)threads) return false;
+  const size_t smem = sizeof(BT) * 2 * ((size_t)nL * nL + (size_t)nL * Rc);
+  dim3 grid(nleaf, (R + Rc - 1) / Rc);
+  if (cpt == 2) {
+    IGA_CUDA(set_max_dynamic_smem(k_near_cols<BT, 2>, smem));
+    k_near_cols<BT, 2><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, yleaf, nL, Rc);
+  } else {
+    IGA_CUDA(set_max_dynamic_smem(k_near_cols<BT, 1>, smem));
+    k_near_cols<BT, 1><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, yleaf, nL, Rc);
+  }
+  note_launch();
+  return true;
+}
+
 // P2M for the columns [r0, r0 + Rc) of every channel.
 // shared: X[nL1][nL1][Rc], U[nG][nL1][Rc] (and dU), f[nG][nG][C][Rc], T[q][nG][C][Rc]
 __global__ void k_p2m2(LeafArgs A, const double2 *__restrict__ xX, double2 *__restrict__ xhat, int r0, int Rc) {
@@ -420,22 +555,23 @@ template <> struct CT<float> { using type = float2; };
 template <> struct CT<double> { using type = double2; };
 
 // P2M for many columns: xhat_t[a C + c][r] = sum_k M_t[k][a C + c] x_t[k][r], one thread block per
-// (leaf, chunk of 64 columns), 64-row chunks of the output with a 4 x 4 register tile per thread.
-template <class T>
+// (leaf, chunk of 16 NN columns), 64-row chunks of the output with a 4 x NN register tile per thread.
+template <class T, int NN>
 __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ xX,
                                                   double2 *__restrict__ xhat) {
   using V = typename CT<T>::type;
+  constexpr int NC = 16 * NN;
   extern __shared__ __align__(16) unsigned char smp[];
   const int nL1 = A.nL1, nL = nL1 * nL1, QC = A.q * A.q * A.C;
-  V *Xs = reinterpret_cast<V *>(smp);        // [nL][64]
-  T *Ms = reinterpret_cast<T *>(Xs + nL * 64);  // [nL][64]
-  const int t = blockIdx.x, r0 = blockIdx.y * 64, Rc = min(64, A.R - r0);
+  V *Xs = reinterpret_cast<V *>(smp);        // [nL][NC]
+  T *Ms = reinterpret_cast<T *>(Xs + nL * NC);  // [nL][64]
+  const int t = blockIdx.x, r0 = blockIdx.y * NC, Rc = min(NC, A.R - r0);
   const int nlL = 1 << A.L, e1 = 1 << A.b;
   const int j = t / (nlL * nlL), cx = (t / nlL) % nlL, cy = t % nlL;
   const long base = ((long)j * A.nb + cx * e1) * A.nb + cy * e1;
   const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
-  for (int e = threadIdx.x; e < nL * 64; e += blockDim.x) {
-    const int k = e / 64, c = e % 64, al = k / nL1, be = k % nL1;
+  for (int e = threadIdx.x; e < nL * NC; e += blockDim.x) {
+    const int k = e / NC, c = e % NC, al = k / nL1, be = k % nL1;
     V v;
     v.x = 0;
     v.y = 0;
@@ -453,26 +589,26 @@ __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restric
       Ms[e] = i < QC ? M[((size_t)t * nL + k) * QC + i] : (T)0;
     }
     __syncthreads();
-    T px[4][4], py[4][4];
+    T px[4][NN], py[4][NN];
     for (int m = 0; m < 4; ++m)
-      for (int n = 0; n < 4; ++n) px[m][n] = py[m][n] = 0;
+      for (int n = 0; n < NN; ++n) px[m][n] = py[m][n] = 0;
     for (int k = 0; k < nL; ++k) {
       T mv[4];
-      V xv[4];
+      V xv[NN];
 #pragma unroll
       for (int m = 0; m < 4; ++m) mv[m] = Ms[k * 64 + ti + 16 * m];
 #pragma unroll
-      for (int n = 0; n < 4; ++n) xv[n] = Xs[k * 64 + tr + 16 * n];
+      for (int n = 0; n < NN; ++n) xv[n] = Xs[k * NC + tr + 16 * n];
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
+        for (int n = 0; n < NN; ++n) {
           px[m][n] += mv[m] * xv[n].x;
           py[m][n] += mv[m] * xv[n].y;
         }
     }
     for (int m = 0; m < 4; ++m)
-      for (int n = 0; n < 4; ++n) {
+      for (int n = 0; n < NN; ++n) {
         const int i = i0 + ti + 16 * m, c = tr + 16 * n;
         if (i < QC && c < Rc) xhat[((size_t)t * QC + i) * A.R + r0 + c] = make_double2((double)px[m][n], (double)py[m][n]);
       }
@@ -482,24 +618,26 @@ __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restric
 // L2P for many columns: y_leaf[t][k][r] += sum_{a, c} M_t[k][a C + c] sigma_c yhat_t[a C + c][r] with the
 // channel factors of the tested operator: soft sigma_0 = 1; hard sigma_0 = -1 (the -K part),
 // sigma_{1..3} = -i eta (curl test of -i eta W), sigma_{4..6} = i eta kappa^2 (its normal part).
-template <class T>
+// One thread block per (leaf, chunk of 16 NN columns), a 4 x NN register tile per thread.
+template <class T, int NN>
 __global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ yhat,
                                                   double2 *__restrict__ yleaf) {
   using V = typename CT<T>::type;
+  constexpr int NC = 16 * NN;
   extern __shared__ __align__(16) unsigned char smq[];
   const int nL1 = A.nL1, nL = nL1 * nL1, C = A.C, QC = A.q * A.q * C;
-  V *Ys = reinterpret_cast<V *>(smq);           // [64 rows a C + c][64]
-  T *Ms = reinterpret_cast<T *>(Ys + 64 * 64);  // [nL][64 rows]
-  const int t = blockIdx.x, r0 = blockIdx.y * 64, Rc = min(64, A.R - r0);
+  V *Ys = reinterpret_cast<V *>(smq);           // [64 rows a C + c][NC]
+  T *Ms = reinterpret_cast<T *>(Ys + 64 * NC);  // [nL][64 rows]
+  const int t = blockIdx.x, r0 = blockIdx.y * NC, Rc = min(NC, A.R - r0);
   const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
   const double k2e = A.kappa * A.kappa * A.eta;
-  T px[4][4], py[4][4];
+  T px[4][NN], py[4][NN];
   for (int m = 0; m < 4; ++m)
-    for (int n = 0; n < 4; ++n) px[m][n] = py[m][n] = 0;
+    for (int n = 0; n < NN; ++n) px[m][n] = py[m][n] = 0;
   for (int i0 = 0; i0 < QC; i0 += 64) {
     __syncthreads();
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-      const int i = i0 + e / 64, c = e % 64;
+    for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
+      const int i = i0 + e / NC, c = e % NC;
       double2 y = make_double2(0.0, 0.0);
       if (i < QC && c < Rc) {
         const double2 yv = yhat[((size_t)t * QC + i) * A.R + r0 + c];
@@ -522,25 +660,25 @@ __global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restric
     const int iw = min(64, QC - i0);
     for (int i = 0; i < iw; ++i) {
       T mv[4];
-      V yv[4];
+      V yv[NN];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int k = ti + 16 * m;
         mv[m] = k < nL ? Ms[k * 64 + i] : (T)0;
       }
 #pragma unroll
-      for (int n = 0; n < 4; ++n) yv[n] = Ys[i * 64 + tr + 16 * n];
+      for (int n = 0; n < NN; ++n) yv[n] = Ys[i * NC + tr + 16 * n];
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
+        for (int n = 0; n < NN; ++n) {
           px[m][n] += mv[m] * yv[n].x;
           py[m][n] += mv[m] * yv[n].y;
         }
     }
   }
   for (int m = 0; m < 4; ++m)
-    for (int n = 0; n < 4; ++n) {
+    for (int n = 0; n < NN; ++n) {
       const int k = ti + 16 * m, c = tr + 16 * n;
       if (k < nL && c < Rc) {
         double2 *dst = yleaf + ((size_t)t * nL + k) * A.R + r0 + c;
@@ -744,6 +882,12 @@ void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem
                         cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
+  if (R <= 16 && launch_near_cols<double2>(A, d.ident_ptr, d.ident_src, reinterpret_cast<const double2 *>(d.binv),
+                                           reinterpret_cast<const double2 *>(d.xX),
+                                           reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st)) {
+    IGA_CUDA(cudaGetLastError());
+    return;
+  }
   if (R >= 8 && S.nL <= 64) {
     dim3 grid(nleaf, (R + NM_COLS - 1) / NM_COLS);
     const size_t smem = sizeof(double2) * ((size_t)S.nL * S.nL + (size_t)S.nL * NM_COLS);
@@ -775,6 +919,18 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
                       cudaStream_t st) {
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
+  if (R <= 16) {  // staged, double-buffered blocks with one thread per (function, column pair)
+    const bool ok = d.blk32 ? launch_near_cols<float2>(A, d.near_ptr, d.near_src, reinterpret_cast<const float2 *>(d.blk32),
+                                                       reinterpret_cast<const double2 *>(d.xX),
+                                                       reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st)
+                            : launch_near_cols<double2>(A, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
+                                                        reinterpret_cast<const double2 *>(d.xX),
+                                                        reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st);
+    if (ok) {
+      IGA_CUDA(cudaGetLastError());
+      return;
+    }
+  }
   if (R >= 8 && S.nL <= 64) {
     dim3 grid(nleaf, (R + NM_COLS - 1) / NM_COLS);
     if (d.blk32) {
@@ -846,18 +1002,22 @@ void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n;
   if (R >= 8 && (d.lm32 || d.lm64)) {
-    dim3 grid(nleaf, (R + 63) / 64);
-    const size_t nl = (size_t)S.nL1 * S.nL1 * 64;
+    const int nn = R <= 16 ? 1 : 4, nc = 16 * nn;
+    dim3 grid(nleaf, (R + nc - 1) / nc);
+    const size_t nl = (size_t)S.nL1 * S.nL1;
+    auto go = [&](auto kfn, const auto *M, size_t smem) {
+      IGA_CUDA(set_max_dynamic_smem(kfn, smem));
+      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.xX),
+                                   reinterpret_cast<double2 *>(d.xhat[S.L]));
+    };
     if (d.lm32) {
-      const size_t smem = nl * (sizeof(float2) + sizeof(float));
-      IGA_CUDA(set_max_dynamic_smem(k_p2m_mrhs<float>, smem));
-      k_p2m_mrhs<float><<<grid, 256, smem, st>>>(A, d.lm32, reinterpret_cast<const double2 *>(d.xX),
-                                                 reinterpret_cast<double2 *>(d.xhat[S.L]));
+      const size_t smem = nl * nc * sizeof(float2) + nl * 64 * sizeof(float);
+      if (nn == 1) go(k_p2m_mrhs<float, 1>, d.lm32, smem);
+      else go(k_p2m_mrhs<float, 4>, d.lm32, smem);
     } else {
-      const size_t smem = nl * (sizeof(double2) + sizeof(double));
-      IGA_CUDA(set_max_dynamic_smem(k_p2m_mrhs<double>, smem));
-      k_p2m_mrhs<double><<<grid, 256, smem, st>>>(A, d.lm64, reinterpret_cast<const double2 *>(d.xX),
-                                                  reinterpret_cast<double2 *>(d.xhat[S.L]));
+      const size_t smem = nl * nc * sizeof(double2) + nl * 64 * sizeof(double);
+      if (nn == 1) go(k_p2m_mrhs<double, 1>, d.lm64, smem);
+      else go(k_p2m_mrhs<double, 4>, d.lm64, smem);
     }
     note_launch();
     IGA_CUDA(cudaGetLastError());
@@ -878,18 +1038,22 @@ void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n;
   if (R >= 8 && (d.lm32 || d.lm64)) {
-    dim3 grid(nleaf, (R + 63) / 64);
+    const int nn = R <= 16 ? 1 : 4, nc = 16 * nn;
+    dim3 grid(nleaf, (R + nc - 1) / nc);
     const size_t nl = (size_t)S.nL1 * S.nL1 * 64;
+    auto go = [&](auto kfn, const auto *M, size_t smem) {
+      IGA_CUDA(set_max_dynamic_smem(kfn, smem));
+      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.yhat[S.L]),
+                                   reinterpret_cast<double2 *>(d.yleaf));
+    };
     if (d.lm32) {
-      const size_t smem = 64 * 64 * sizeof(float2) + nl * sizeof(float);
-      IGA_CUDA(set_max_dynamic_smem(k_l2p_mrhs<float>, smem));
-      k_l2p_mrhs<float><<<grid, 256, smem, st>>>(A, d.lm32, reinterpret_cast<const double2 *>(d.yhat[S.L]),
-                                                 reinterpret_cast<double2 *>(d.yleaf));
+      const size_t smem = 64 * (size_t)nc * sizeof(float2) + nl * sizeof(float);
+      if (nn == 1) go(k_l2p_mrhs<float, 1>, d.lm32, smem);
+      else go(k_l2p_mrhs<float, 4>, d.lm32, smem);
     } else {
-      const size_t smem = 64 * 64 * sizeof(double2) + nl * sizeof(double);
-      IGA_CUDA(set_max_dynamic_smem(k_l2p_mrhs<double>, smem));
-      k_l2p_mrhs<double><<<grid, 256, smem, st>>>(A, d.lm64, reinterpret_cast<const double2 *>(d.yhat[S.L]),
-                                                  reinterpret_cast<double2 *>(d.yleaf));
+      const size_t smem = 64 * (size_t)nc * sizeof(double2) + nl * sizeof(double);
+      if (nn == 1) go(k_l2p_mrhs<double, 1>, d.lm64, smem);
+      else go(k_l2p_mrhs<double, 4>, d.lm64, smem);
     }
     note_launch();
     IGA_CUDA(cudaGetLastError());

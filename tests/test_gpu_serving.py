@@ -91,3 +91,34 @@ def test_wait_times_out_and_poll_reports_progress():
     assert rc == 0 and np.isfinite(u).all() and info["solve_ms"] > 0
     B.igabem_request_destroy(r)
     B.igabem_server_destroy(srv)
+
+
+def test_requests_for_one_problem_are_merged_and_the_problem_stays_resident():
+    """Three requests for the same problem that wait together are solved as one multi-column GMRES
+    run (shared matrix-vector products); a later request for it reuses the resident set-up.  Each
+    request's far field equals the same request solved alone."""
+    srv = B.igabem_server_create(G.ctx(), 0, 1)        # one slot: the requests queue behind the first
+    first = B.igabem_submit(srv, G.geometry("deformed"),
+                            B.igabem_default_options(level_m=4, degree_p=2, kappa=3.0, eta_cfie=3.0, leaf_offset=2),
+                            [[0.0, 0.0, 1.0]], XH)
+    kw = dict(level_m=3, degree_p=2, kappa=4.0, eta_cfie=4.0, bc=0, cheb_q=6, leaf_offset=1)
+    opt = B.igabem_default_options(tol=1e-8, **kw)
+    dirs = inputs.fibonacci_directions(6)
+    parts = [dirs[0:1], dirs[1:3], dirs[3:6]]
+    reqs = [B.igabem_submit(srv, G.geometry("sphere"), opt, d, XH) for d in parts]
+    for r in [first] + reqs:
+        B.igabem_wait(r, 600.0)
+    late = B.igabem_submit(srv, G.geometry("sphere"), opt, dirs[4:5], XH)
+    B.igabem_wait(late, 600.0)
+    stats = B.igabem_server_get_stats(srv)
+    out = [B.igabem_result(r) for r in reqs + [late]]
+    for r in [first] + reqs + [late]:
+        B.igabem_request_destroy(r)
+    B.igabem_server_destroy(srv)
+    assert stats["merged"] >= 2 and stats["cache_hits"] >= 1 and stats["failed"] == 0
+    prob, info = G.problem("sphere", tol=1e-8, **kw)
+    for d, (u, sinfo, rc) in zip(parts + [dirs[4:5]], out):
+        x, _ = B.igabem_solve(prob, d, info["n_dofs"])
+        ref = B.igabem_farfield(prob, x, XH)
+        assert rc == 0 and G.rel(u, ref) < 1e-7, G.rel(u, ref)
+    B.igabem_problem_destroy(prob)

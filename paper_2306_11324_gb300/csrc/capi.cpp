@@ -108,6 +108,11 @@ size_t problem_work_bytes(const HostSetup &S, int R, int gmres_m, int precision)
     add((size_t)S.lev[l].n * Q * C * R * cz);
     add((size_t)S.lev[l].n * Q * C * R * cz);
   }
+  if (precision != IGABEM_FP64) {  // FP32 copies of the input vector and of the expansions
+    add(S.NX * R * sizeof(float2));
+    for (int l = S.lmin; l <= S.L; ++l) add((size_t)S.lev[l].n * S.lev[l].q * S.lev[l].q * C * R * sizeof(float2));
+    add((size_t)S.lev[S.L].n * S.q * S.q * C * R * sizeof(float2));
+  }
   if (precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
     for (int l = S.lmin; l <= S.L; ++l) {
       add(m2l_tc_image_bytes(S, l, R));
@@ -153,6 +158,8 @@ struct ProblemWork {
   std::vector<void *> xhat, yhat;
   std::vector<uint8_t *> tc_bimg;
   std::vector<float *> tc_bscale;
+  std::vector<float2 *> xhat32;      // mixed precisions: FP32 copies of the expansions, the input vector
+  float2 *xX32 = nullptr, *y32 = nullptr;  // and the leaf-level local expansions
   // GMRES
   double *V, *w, *x, *b, *r, *t, *u, *vj;
   GmDev G{};
@@ -215,6 +222,14 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
     W.xhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
     W.yhat[l] = W.arena.get<double>((size_t)S.lev[l].n * Q * C * R * 2);
   }
+  W.xhat32.assign(S.L + 1, nullptr);
+  W.xX32 = W.y32 = nullptr;
+  if (P->opt.precision != IGABEM_FP64) {
+    W.xX32 = W.arena.get<float2>(S.NX * R);
+    for (int l = S.lmin; l <= S.L; ++l)
+      W.xhat32[l] = W.arena.get<float2>((size_t)S.lev[l].n * S.lev[l].q * S.lev[l].q * C * R);
+    W.y32 = W.arena.get<float2>((size_t)S.lev[S.L].n * S.q * S.q * C * R);
+  }
   W.tc_bimg.assign(S.L + 1, nullptr);
   W.tc_bscale.assign(S.L + 1, nullptr);
   if (P->opt.precision == IGABEM_MIXED_TC && S.n_far > 0 && m2l_tc_supported(S, R))
@@ -269,6 +284,9 @@ void ensure_work(igabem_problem *P, int R, bool with_gmres) {
   d.yhat = W.yhat;
   d.tc_bimg = W.tc_bimg;
   d.tc_bscale = W.tc_bscale;
+  d.xhat32 = W.xhat32;
+  d.xX32 = W.xX32;
+  d.y32 = W.y32;
 }
 
 // the device status word: a kernel whose bounded wait ran out has set it (the stream is synchronised)

@@ -231,6 +231,10 @@ struct DeviceProblem {
   double *yleaf = nullptr;                   // leaf-local outputs [n_leaf][nL][R] complex
   double *gq = nullptr;                      // channel values at Gauss points [E][nq][C][R]
   std::vector<void *> xhat, yhat;            // expansions per level [n][q*q][C][R]
+  // mixed precisions: FP32 copies made once per product for the kernels that compute in FP32 (the
+  // expansions after the upward pass, the input vector, the leaf-level local expansions)
+  std::vector<float2 *> xhat32;
+  float2 *xX32 = nullptr, *y32 = nullptr;
   double *xin = nullptr, *yout = nullptr;    // device staging of caller vectors [N][R]
   double *red = nullptr;                     // reduction scratch
 };

@@ -607,6 +607,21 @@ size_t band_smem(int n1d, int q, bool fp32, bool l2p) {
   return lg + 2 * ts * BAND_COLS * (l2p ? ((size_t)q * q + q) : ((size_t)n1d + q));
 }
 
+// FP32 copy of a complex FP64 vector (the mixed precisions: one conversion per product instead of one
+// per use inside the FP32 kernels; GB300 converts on its FP64 pipe)
+__global__ void k_to_f32(const double2 *__restrict__ src, float2 *__restrict__ dst, long n) {
+  GRID_STRIDE(i, n) {
+    const double2 v = src[i];
+    dst[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void to_f32(const void *src, float2 *dst, long n, cudaStream_t st) {
+  if (n <= 0 || !dst) return;
+  k_to_f32<<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(src), dst, n);
+  note_launch();
+}
+
 // y[i][r] = sum_{X in g2x(i)} sum_{leaves t containing X} y_leaf[t][local(X)][r]
 __global__ void k_gather_out(Dims D, const int *__restrict__ g2x_ptr, const int *__restrict__ g2x_idx,
                              const double2 *__restrict__ yleaf, double2 *__restrict__ y) {
@@ -656,6 +671,7 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     k_gather_in<<<grid_for(D.NX * R), 256, 0, st>>>(D, d.x2g, reinterpret_cast<const double2 *>(x),
                                                      reinterpret_cast<double2 *>(d.xX));
     note_launch();
+    if (o.precision != IGABEM_FP64) to_f32(d.xX, d.xX32, D.NX * R, st);
   }
   const bool leafk = leaf_kernels_supported(S);
   {
@@ -724,7 +740,7 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         }
         const Dims Dl = level_dims(l);  // the children have the same q
         long n = (long)S.lev[l].n * Dl.Q * D.CR;
-        const bool sep = D.CR >= 16 && Dl.q <= 16 && Dl.Q * SEP_COLS <= 256 * 8;
+        const bool sep = (D.CR >= 16 || (f32 && D.CR >= 4)) && Dl.q <= 16 && Dl.Q * SEP_COLS <= 256 * 8;
         const size_t smem = (size_t)2 * Dl.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
         if (sep) {
           IGA_CUDA(f32 ? set_max_dynamic_smem(k_m2m_sep<float>, smem) : set_max_dynamic_smem(k_m2m_sep<double>, smem));
@@ -739,12 +755,17 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         note_launch();
       }
     }
+    const bool tc = o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() && d.tc_bimg[S.L];
     if (m2l_rows_supported(S, o, R)) {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
-      if (o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() && d.tc_bimg[S.L])
+      if (tc) {
         launch_m2l_tc(d, S, o, R, st);
-      else
+      } else {
+        if (f32)  // the expansions of the upward pass in FP32 for the FP32 M2L
+          for (int l = S.lmin; l <= S.L; ++l)
+            to_f32(d.xhat[l], d.xhat32[l], (long)S.lev[l].n * S.lev[l].q * S.lev[l].q * D.CR, st);
         launch_m2l_rows(d, S, o, R, f32, st);
+      }
     } else {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       for (int l = S.lmin; l <= S.L; ++l) {
@@ -768,7 +789,7 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         }
         const Dims Dl = level_dims(l);
         long n = (long)S.lev[l + 1].n * Dl.Q * D.CR;
-        const bool sep = D.CR >= 16 && Dl.q <= 16;
+        const bool sep = (D.CR >= 16 || (f32 && D.CR >= 4)) && Dl.q <= 16;
         const size_t smem = (size_t)3 * Dl.Q * SEP_COLS * (f32 ? sizeof(float2) : sizeof(double2));
         if (sep && smem <= (size_t)max_optin_smem() - 4096) {
           IGA_CUDA(f32 ? set_max_dynamic_smem(k_l2l_sep<float>, smem) : set_max_dynamic_smem(k_l2l_sep<double>, smem));
@@ -785,6 +806,7 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     }
     {
       Phase ph(d.prof, IGABEM_PH_L2P, st);
+      if (f32) to_f32(d.yhat[S.L], d.y32, (long)nleaf * D.Q * D.CR, st);
       if (bands) {  // the band bottoms' fields at the Gauss points, tested (before gq is reused below)
         k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, gq, reinterpret_cast<double2 *>(d.yleaf));
         note_launch();

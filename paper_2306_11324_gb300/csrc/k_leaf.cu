@@ -202,8 +202,8 @@ __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0
 template <class BT, int CPT>
 __global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__restrict__ near_ptr,
                                                    const int *__restrict__ near_src, const BT *__restrict__ blk,
-                                                   const double2 *__restrict__ xX, double2 *__restrict__ yleaf,
-                                                   int nL, int Rc) {
+                                                   const double2 *__restrict__ xX, const float2 *__restrict__ x32,
+                                                   double2 *__restrict__ yleaf, int nL, int Rc) {
   using RT = decltype(BT::x);
   extern __shared__ __align__(16) unsigned char smk[];
   BT *Bs = reinterpret_cast<BT *>(smk);              // [2][nL * nL] (block column-major: [j][i])
@@ -233,9 +233,16 @@ __global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__rest
       if (e < nX) {
         const int jj = e / Rc, c = e % Rc, al = jj / A.nL1, be = jj % A.nL1;
         if (c < rc) {
-          const double2 xd = xX[(base + (long)al * A.nb + be) * A.R + r0 + c];
-          rx[u].x = (RT)xd.x;
-          rx[u].y = (RT)xd.y;
+          const long ix = (base + (long)al * A.nb + be) * A.R + r0 + c;
+          if constexpr (sizeof(RT) == 4) {  // FP32 blocks: the FP32 copy of the input
+            const float2 xf = x32[ix];
+            rx[u].x = xf.x;
+            rx[u].y = xf.y;
+          } else {
+            const double2 xd = xX[ix];
+            rx[u].x = xd.x;
+            rx[u].y = xd.y;
+          }
         }
       }
     }
@@ -247,9 +254,20 @@ __global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__rest
       if (e < nX) Xs[buf * nX + e] = rx[u];
     }
   };
+  // the blocks' sums: FP64 for FP64 blocks; for FP32 blocks an FP32 sum with a compensation term
+  // (Neumaier), as accurate as an FP64 sum here without FP64 arithmetic
   double2 acc[CPT];
+  float2 sh[CPT], sl[CPT];
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = make_double2(0.0, 0.0);
+  for (int c = 0; c < CPT; ++c) {
+    acc[c] = make_double2(0.0, 0.0);
+    sh[c] = sl[c] = make_float2(0.f, 0.f);
+  }
+  auto nsum = [](float &hi, float &lo, float v) {
+    const float t = hi + v;
+    lo += fabsf(hi) >= fabsf(v) ? (hi - t) + v : (v - t) + hi;
+    hi = t;
+  };
   if (kb < ke) {
     issue_block(kb, 0);
     fetch_x(kb);
@@ -281,8 +299,13 @@ __global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__rest
       }
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        acc[c].x += (double)px[c];
-        acc[c].y += (double)py[c];
+        if constexpr (sizeof(RT) == 4) {
+          nsum(sh[c].x, sl[c].x, (float)px[c]);
+          nsum(sh[c].y, sl[c].y, (float)py[c]);
+        } else {
+          acc[c].x += (double)px[c];
+          acc[c].y += (double)py[c];
+        }
       }
     }
     if (k + 1 < ke) store_x(cur ^ 1);  // coefficients of block k + 1
@@ -295,15 +318,17 @@ __global__ void __launch_bounds__(576) k_near_cols(LeafArgs A, const int *__rest
   }
   if (active) {
 #pragma unroll
-    for (int c = 0; c < CPT; ++c)
+    for (int c = 0; c < CPT; ++c) {
+      if (sizeof(RT) == 4) acc[c] = make_double2((double)sh[c].x + (double)sl[c].x, (double)sh[c].y + (double)sl[c].y);
       if (c0 + c < rc) yleaf[((size_t)t * nL + i) * A.R + r0 + c0 + c] = acc[c];
+    }
   }
 }
 
 // launch of k_near_cols: columns per thread 2 (1 for a single column), chunks of up to 16 columns
 template <class BT>
 bool launch_near_cols(const LeafArgs &A, const int *near_ptr, const int *near_src, const BT *blk, const double2 *xX,
-                      double2 *yleaf, int nleaf, int nL, int R, cudaStream_t st) {
+                      const float2 *x32, double2 *yleaf, int nleaf, int nL, int R, cudaStream_t st) {
   const int Rc = std::min(R, 16), cpt = Rc >= 2 ? 2 : 1;
   const int threads = ((nL * ((Rc + cpt - 1) / cpt) + 31) / 32) * 32;
   if (threads > 576 || (size_t)nL * Rc > 2 * (size_t)threads) return false;
@@ -311,10 +336,10 @@ bool launch_near_cols(const LeafArgs &A, const int *near_ptr, const int *near_sr
   dim3 grid(nleaf, (R + Rc - 1) / Rc);
   if (cpt == 2) {
     IGA_CUDA(set_max_dynamic_smem(k_near_cols<BT, 2>, smem));
-    k_near_cols<BT, 2><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, yleaf, nL, Rc);
+    k_near_cols<BT, 2><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, x32, yleaf, nL, Rc);
   } else {
     IGA_CUDA(set_max_dynamic_smem(k_near_cols<BT, 1>, smem));
-    k_near_cols<BT, 1><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, yleaf, nL, Rc);
+    k_near_cols<BT, 1><<<grid, threads, smem, st>>>(A, near_ptr, near_src, blk, xX, x32, yleaf, nL, Rc);
   }
   note_launch();
   return true;
@@ -558,7 +583,7 @@ template <> struct CT<double> { using type = double2; };
 // (leaf, chunk of 16 NN columns), 64-row chunks of the output with a 4 x NN register tile per thread.
 template <class T, int NN>
 __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ xX,
-                                                  double2 *__restrict__ xhat) {
+                                                  const float2 *__restrict__ x32, double2 *__restrict__ xhat) {
   using V = typename CT<T>::type;
   constexpr int NC = 16 * NN;
   extern __shared__ __align__(16) unsigned char smp[];
@@ -576,9 +601,16 @@ __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restric
     v.x = 0;
     v.y = 0;
     if (c < Rc) {
-      const double2 xd = xX[(base + (long)al * A.nb + be) * A.R + r0 + c];
-      v.x = (T)xd.x;
-      v.y = (T)xd.y;
+      const long ix = (base + (long)al * A.nb + be) * A.R + r0 + c;
+      if constexpr (sizeof(T) == 4) {
+        const float2 xf = x32[ix];
+        v.x = xf.x;
+        v.y = xf.y;
+      } else {
+        const double2 xd = xX[ix];
+        v.x = xd.x;
+        v.y = xd.y;
+      }
     }
     Xs[e] = v;
   }
@@ -621,7 +653,7 @@ __global__ void __launch_bounds__(256) k_p2m_mrhs(LeafArgs A, const T *__restric
 // One thread block per (leaf, chunk of 16 NN columns), a 4 x NN register tile per thread.
 template <class T, int NN>
 __global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restrict__ M, const double2 *__restrict__ yhat,
-                                                  double2 *__restrict__ yleaf) {
+                                                  const float2 *__restrict__ y32, double2 *__restrict__ yleaf) {
   using V = typename CT<T>::type;
   constexpr int NC = 16 * NN;
   extern __shared__ __align__(16) unsigned char smq[];
@@ -630,7 +662,7 @@ __global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restric
   T *Ms = reinterpret_cast<T *>(Ys + 64 * NC);  // [nL][64 rows]
   const int t = blockIdx.x, r0 = blockIdx.y * NC, Rc = min(NC, A.R - r0);
   const int ti = threadIdx.x >> 4, tr = threadIdx.x & 15;
-  const double k2e = A.kappa * A.kappa * A.eta;
+  const T k2e = (T)(A.kappa * A.kappa * A.eta), eta = (T)A.eta;
   T px[4][NN], py[4][NN];
   for (int m = 0; m < 4; ++m)
     for (int n = 0; n < NN; ++n) px[m][n] = py[m][n] = 0;
@@ -638,18 +670,35 @@ __global__ void __launch_bounds__(256) k_l2p_mrhs(LeafArgs A, const T *__restric
     __syncthreads();
     for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
       const int i = i0 + e / NC, c = e % NC;
-      double2 y = make_double2(0.0, 0.0);
-      if (i < QC && c < Rc) {
-        const double2 yv = yhat[((size_t)t * QC + i) * A.R + r0 + c];
-        const int ch = i % C;
-        if (!A.hard) y = yv;
-        else if (ch == 0) y = make_double2(-yv.x, -yv.y);
-        else if (ch <= 3) y = make_double2(A.eta * yv.y, -A.eta * yv.x);
-        else y = make_double2(-k2e * yv.y, k2e * yv.x);
-      }
       V v;
-      v.x = (T)y.x;
-      v.y = (T)y.y;
+      v.x = 0;
+      v.y = 0;
+      if (i < QC && c < Rc) {
+        const size_t iy = ((size_t)t * QC + i) * A.R + r0 + c;
+        V yv;
+        if constexpr (sizeof(T) == 4) {
+          const float2 f = y32[iy];
+          yv.x = f.x;
+          yv.y = f.y;
+        } else {
+          const double2 f = yhat[iy];
+          yv.x = f.x;
+          yv.y = f.y;
+        }
+        const int ch = i % C;
+        if (!A.hard) {
+          v = yv;
+        } else if (ch == 0) {
+          v.x = -yv.x;
+          v.y = -yv.y;
+        } else if (ch <= 3) {
+          v.x = eta * yv.y;
+          v.y = -eta * yv.x;
+        } else {
+          v.x = -k2e * yv.y;
+          v.y = k2e * yv.x;
+        }
+      }
       Ys[e] = v;
     }
     for (int e = threadIdx.x; e < nL * 64; e += blockDim.x) {
@@ -883,7 +932,7 @@ void launch_block_apply(const DeviceProblem &d, const HostSetup &S, const igabem
   LeafArgs A = leaf_args(d, S, o, R);
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
   if (R <= 16 && launch_near_cols<double2>(A, d.ident_ptr, d.ident_src, reinterpret_cast<const double2 *>(d.binv),
-                                           reinterpret_cast<const double2 *>(d.xX),
+                                           reinterpret_cast<const double2 *>(d.xX), nullptr,
                                            reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st)) {
     IGA_CUDA(cudaGetLastError());
     return;
@@ -921,10 +970,10 @@ void launch_near_spmv(const DeviceProblem &d, const HostSetup &S, const igabem_o
   const int nleaf = S.lev[S.L].n, nout = S.nL * R, threads = 256;
   if (R <= 16) {  // staged, double-buffered blocks with one thread per (function, column pair)
     const bool ok = d.blk32 ? launch_near_cols<float2>(A, d.near_ptr, d.near_src, reinterpret_cast<const float2 *>(d.blk32),
-                                                       reinterpret_cast<const double2 *>(d.xX),
+                                                       reinterpret_cast<const double2 *>(d.xX), d.xX32,
                                                        reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st)
                             : launch_near_cols<double2>(A, d.near_ptr, d.near_src, reinterpret_cast<const double2 *>(d.blk),
-                                                        reinterpret_cast<const double2 *>(d.xX),
+                                                        reinterpret_cast<const double2 *>(d.xX), nullptr,
                                                         reinterpret_cast<double2 *>(d.yleaf), nleaf, S.nL, R, st);
     if (ok) {
       IGA_CUDA(cudaGetLastError());
@@ -1007,7 +1056,7 @@ void launch_p2m(const DeviceProblem &d, const HostSetup &S, const igabem_options
     const size_t nl = (size_t)S.nL1 * S.nL1;
     auto go = [&](auto kfn, const auto *M, size_t smem) {
       IGA_CUDA(set_max_dynamic_smem(kfn, smem));
-      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.xX),
+      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.xX), d.xX32,
                                    reinterpret_cast<double2 *>(d.xhat[S.L]));
     };
     if (d.lm32) {
@@ -1043,7 +1092,7 @@ void launch_l2p(const DeviceProblem &d, const HostSetup &S, const igabem_options
     const size_t nl = (size_t)S.nL1 * S.nL1 * 64;
     auto go = [&](auto kfn, const auto *M, size_t smem) {
       IGA_CUDA(set_max_dynamic_smem(kfn, smem));
-      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.yhat[S.L]),
+      kfn<<<grid, 256, smem, st>>>(A, M, reinterpret_cast<const double2 *>(d.yhat[S.L]), d.y32,
                                    reinterpret_cast<double2 *>(d.yleaf));
     };
     if (d.lm32) {

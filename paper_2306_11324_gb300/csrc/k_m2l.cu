@@ -36,6 +36,7 @@ struct M2LLevel {
   const float *nodes32;  // FP32 [7][n q^2]: x - c, n~, a
   const float *pc;       // FP32 pair constants [n_far][8]: D, |D|, |D|^2, cos, sin of kappa|D| (FP32 path)
   const double2 *xhat;
+  const float2 *xhat32;  // FP32 copy of xhat (the FP32 kernels read it)
   double2 *yhat;
   int n;                 // clusters on the level
   int first;             // first block index of the level in the flattened grid
@@ -123,8 +124,13 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_rows(M2LArgs A, int cr0)
         sn.Dny = D[0] * sn.ny[0] + D[1] * sn.ny[1] + D[2] * sn.ny[2];
         src[b] = sn;
         for (int c = 0; c < ncr; ++c) {
-          double2 v = L.xhat[ib * A.CR + cr0 + c];
-          xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+          if constexpr (F32) {
+            const float2 v = L.xhat32[ib * A.CR + cr0 + c];
+            xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+          } else {
+            const double2 v = L.xhat[ib * A.CR + cr0 + c];
+            xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+          }
         }
       }
       __syncwarp();
@@ -270,9 +276,15 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(M2LArgs A, int Wc) {
     }
     for (int i = threadIdx.x; i < Q * Wc; i += blockDim.x) {
       int b = i / Wc, c = i % Wc;
-      double2 v = L.xhat[((long)s * Q + b) * A.CR + cr0 + c];
+      C2<T> xv;
+      if constexpr (F32) {
+        const float2 v = L.xhat32[((long)s * Q + b) * A.CR + cr0 + c];
+        xv = c2((T)v.x, (T)v.y);
+      } else {
+        const double2 v = L.xhat[((long)s * Q + b) * A.CR + cr0 + c];
+        xv = c2((T)v.x, (T)v.y);
+      }
       // the pair factor exp(i kappa |D|) is folded into the source coefficients
-      C2<T> xv = c2((T)v.x, (T)v.y);
       Xs[i] = F32 ? mul(e0, xv) : xv;
     }
     __syncthreads();
@@ -443,6 +455,7 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     L.nodes32 = d.nodes32[l];
     L.pc = d.pairc[l];
     L.xhat = reinterpret_cast<const double2 *>(d.xhat[l]);
+    L.xhat32 = d.xhat32.empty() ? nullptr : d.xhat32[l];
     L.yhat = reinterpret_cast<double2 *>(d.yhat[l]);
     L.n = S.lev[l].n;
     L.first = nblocks;

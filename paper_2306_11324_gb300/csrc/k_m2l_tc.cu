@@ -46,7 +46,7 @@ namespace igabem {
 
 namespace {
 
-constexpr int TC_THREADS = 512;                            // 16 warps: warp 0 issues, 15 generate
+constexpr int TC_THREADS = 256;                            // 8 warps: warp 0 issues, 7 generate
 constexpr int TC_NQW = TC_THREADS / 128;                   // warps per tensor-memory lane quadrant
 constexpr int TC_MAXC = 16 / TC_NQW;                       // 16-column accumulator chunks per thread
 constexpr int TC_NS = 64;                                  // columns of a slice (MMA N <= 64)

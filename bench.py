@@ -65,6 +65,7 @@ WORKLOADS = {
                                                     tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=2048,
                                                     n_rhs=8, restart=30, precond={"fp64": 1, "mixed": 1, "tc": 1},
                                                     precision="mixed", step="sweep", eta="kappa",
+                                                    m2l_stored={"fp64": 0, "mixed": 1, "tc": 1},
                                                     kappas=[50.0 + 10.0 * i / 15 for i in range(16)],
                                                     solve_max_iter=2000),
 }
@@ -135,7 +136,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["serving_stream"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + ["serving_stream", "torus_convergence"])
     ap.add_argument("--requests", type=int, default=64, help="serving_stream: requests in the stream")
     ap.add_argument("--rate", type=float, default=2.0, help="serving_stream: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving_stream: concurrent requests")
@@ -508,6 +509,51 @@ def run_matvec_steps(args, wl, B, inputs, geom, options, stream, flush, local, w
         dist.destroy_process_group()
 
 
+def run_torus_convergence(args):
+    """The convergence study of Sec. 5.2 on its geometry: the torus R = 2, r = 0.5 as 16 exact rational
+    patches, kappa = 2.5, plane wave d = x^, far field at 100 directions, FP64 with level-adaptive
+    interpolation (cheb_q 8, cap 2, up to 14 points), GMRES(30) with the block preconditioner to 1e-11;
+    for p = 1, 2 (sound-soft) and p = 1 (sound-hard) the error at m = 1..4 against m = 5 and the
+    observed orders in h (expected 2p + 2 for sound-soft, 2p + 1 for sound-hard).  The paper's own
+    reference solutions and data logs are not available; the finest level stands in for them."""
+    import torch
+    from paper_2306_11324_gb300 import binding as B
+    from paper_2306_11324_gb300 import inputs
+    torch.cuda.set_device(0)
+    ctx = B.igabem_create(0, torch.cuda.current_stream().cuda_stream)
+    geom = B.igabem_geometry_create(ctx, inputs.torus_patches(2.0, 0.5))
+    xh = inputs.fibonacci_directions(100)
+    d = np.array([[1.0, 0.0, 0.0]])
+    table, orders = [], {}
+    for p, hard in ((1, False), (2, False), (1, True)):
+        u, info_m = {}, {}
+        for m in (1, 2, 3, 4, 5):
+            opt = B.igabem_default_options(level_m=m, degree_p=p, kappa=2.5, eta_cfie=(1 / 2.5) if hard else 2.5,
+                                           bc=int(hard), cheb_q=8, kappa_cap=2.0, q_max=14, leaf_offset=min(m, 1),
+                                           eta_adm=0.5, tol=1e-11, precond=0 if hard else 1,
+                                           gmres_restart=300 if hard else 30, max_iter=3000)
+            t0 = time.perf_counter()
+            prob = B.igabem_problem_create(geom, opt)
+            info = B.igabem_problem_info(prob)
+            x, sinfo = B.igabem_solve(prob, d, info["n_dofs"], raise_on_not_converged=False)
+            u[m] = B.igabem_farfield(prob, x, xh)[:, 0]
+            B.igabem_problem_destroy(prob)
+            info_m[m] = (info["n_dofs"], sinfo["iterations"], sinfo["rel_residual"], time.perf_counter() - t0)
+        errs = {m: float(np.abs(u[m] - u[5]).max() / np.abs(u[5]).max()) for m in (1, 2, 3, 4)}
+        for m in (1, 2, 3, 4):
+            order = float(np.log2(errs[m - 1] / errs[m])) if m > 1 else None
+            table.append({"p": p, "bc": "hard" if hard else "soft", "m": m, "n_dofs": info_m[m][0],
+                          "gmres_iterations": info_m[m][1], "rel_residual": info_m[m][2], "seconds": info_m[m][3],
+                          "farfield_err_vs_m5": errs[m], "order": order})
+        orders[f"p{p}_{'hard' if hard else 'soft'}"] = float(np.log2(errs[2] / errs[3]))
+    print(json.dumps({"metric": "far-field self-convergence on the torus (Sec. 5.2)", "value": orders["p1_soft"],
+                      "unit": "observed order in h (m = 2 -> 3, against m = 5)", "n_gpus": 1, "steps": 1, "warmup": 0,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic (exact torus, plane wave d = x^)",
+                      "config": {"workload": "torus_convergence", "kappa": 2.5, "R": 2.0, "r": 0.5,
+                                 "expected_orders": {"p1_soft": 4, "p2_soft": 6, "p1_hard": 3}},
+                      "orders": orders, "table": table}))
+
+
 def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, world, rank, dist, peaks, ctx):
     """The frequency-sweep workload: a step is one kappa of the sweep (set-up, GMRES for all incident
     directions at once, far field); solves/s counts every incident direction.  Beside the timed steps:
@@ -526,7 +572,8 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                  q_max=wl["q_max"], eta_adm=wl["eta_adm"], leaf_offset=wl["leaf_offset"][precision],
                  tol=wl["tol"][precision], kappa_cap=wl["kappa_cap"], gmres_restart=wl["restart"],
                  max_iter=wl["solve_max_iter"], precond=wl["precond"][precision],
-                 precision=PRECISIONS[precision], profile=1)
+                 precision=PRECISIONS[precision], profile=1,
+                 m2l_stored=wl.get("m2l_stored", {}).get(precision, 0))
         o.update(kw)
         return B.igabem_default_options(**o)
 
@@ -665,6 +712,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                       "kappa_cap": wl["kappa_cap"], "leaf_offset": wl["leaf_offset"][args.precision],
                       "gmres_restart": wl["restart"], "tol": wl["tol"][args.precision],
                       "precond": wl["precond"][args.precision], "n_far_pairs": info["n_far_pairs"],
+                      "m2l_stored": wl.get("m2l_stored", {}).get(args.precision, 0),
                       "parallelism": f"replicas x{world}",
                       "l2": "working set far above L2 (and a 256 MB write before each step)"},
            "steps_detail": steps_rec,
@@ -694,6 +742,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving_stream":
         return run_serving(args)
+    if args.workload == "torus_convergence":
+        return run_torus_convergence(args)
     import torch
     from paper_2306_11324_gb300 import binding as B
     from paper_2306_11324_gb300 import inputs

@@ -93,6 +93,12 @@ typedef struct {
                           kappa max(2r) <= cap_l, eps(q_l, cap_l / 2) = eps_ref (kappa_cap where q_l =
                           cheb_q).  Expansions of a level whose q differs from its children's are formed
                           from and evaluated at the Gauss points directly. */
+  int m2l_stored;      /* 0: M2L coupling blocks generated on the fly in every product (default);
+                          1: generated once at set-up and kept in device memory (each far pair's q^2 x q^2
+                          block per kernel type, FP32 in the mixed precisions, FP64 otherwise, with the
+                          pair phase factor folded in), streamed by every product: the paper's H^2
+                          storage of the compressed operator (Sec. 5.1), reused across iterations and
+                          right-hand sides; igabem_problem_info reports the bytes */
   int no_graph;        /* 0: each GMRES iteration (matrix-vector product, Gram-Schmidt, Givens update, next
                           basis vector) is captured once as a CUDA graph with its state on the device and
                           replayed, the host only reading the finished flags one iteration behind;
@@ -204,6 +210,16 @@ int igabem_matvec(igabem_problem *prob, int n_rhs, const void *x, void *y);
    written) if a right-hand side missed the tolerance within max_iter iterations. */
 int igabem_solve(igabem_problem *prob, int n_rhs, const double *dirs, void *density,
                  igabem_solve_info *info);
+
+/* As igabem_solve for incident spherical waves from point sources, u_inc(x) = G(x, z_r) =
+   exp(i kappa |x - z_r|) / (4 pi |x - z_r|) at the points z ([n_rhs][3], host, outside the scatterer:
+   the direct formulation of Sec. 2 needs an incident field that solves the Helmholtz equation inside
+   it), instead of plane waves: the right-hand sides of Sec. 4.1 with these u_inc, grad u_inc =
+   G (i kappa r - 1) / r^2 (x - z). */
+int igabem_solve_sources(igabem_problem *prob, int n_rhs, const double *z, void *density,
+                         igabem_solve_info *info);
+/* Right-hand sides of igabem_solve_sources: b = [N][n_rhs] complex. */
+int igabem_rhs_sources(igabem_problem *prob, int n_rhs, const double *z, void *b);
 
 /* Far-field pattern (Sec. 1) of n_rhs densities at n_dir unit directions xhat ([n_dir][3], host):
      sound-soft u_inf(x^) = -1/(4 pi) int exp(-i kappa x^.y) t(y) dsigma_y,

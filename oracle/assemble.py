@@ -268,6 +268,28 @@ def cfie_matrix(space, kappa, eta, hard: bool, ops=None):
     return P.T @ AX @ P
 
 
+def rhs_point_sources(space, kappa, eta, z, hard: bool, rules: ElementRules | None = None):
+    """Load vectors (N, R) of the CFIE systems (Sec. 4.1) for the incident fields u_inc = G(., z_r) of
+    point sources at the rows of z (R, 3): sound-soft <du_inc/dn - i eta u_inc, psi_i>, sound-hard
+    <u_inc - i eta du_inc/dn, psi_i>, with du_inc/dn = G'(r)/r (x - z).n, 4x4 Gauss per element."""
+    rules = rules or ElementRules(space)
+    Z = np.atleast_2d(np.asarray(z, float))
+    pts = rules.pts
+    wq = np.tile(rules.w, space.mesh.E)
+    out = np.zeros((space.N, Z.shape[0]), dtype=complex)
+    for r, zr in enumerate(Z):
+        v = pts.x - zr
+        dist = np.linalg.norm(v, axis=1)
+        G = np.exp(1j * kappa * dist) / (4.0 * np.pi * dist)
+        dn = G * (1j * kappa * dist - 1.0) / dist ** 2 * np.sum(v * pts.n, axis=1)   # a du_inc/dn
+        f = (G * pts.a - 1j * eta * dn) if hard else (dn - 1j * eta * pts.a * G)
+        vals = (wq * f)[:, None] * pts.phi
+        bX = np.zeros(space.NX, dtype=complex)
+        np.add.at(bX, space.l2x[pts.e], vals)
+        np.add.at(out[:, r], space.x2g, bX)
+    return out
+
+
 def rhs(space, kappa, eta, d, hard: bool, rules: ElementRules | None = None):
     """Load vector(s) for incident directions d (3,) or (R, 3): (N,) or (N, R).
 

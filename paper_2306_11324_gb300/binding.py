@@ -29,7 +29,7 @@ class igabem_options(ctypes.Structure):
                 ("kappa_cap", c_double), ("gauss_regular", c_int), ("gauss_singular", c_int),
                 ("precision", c_int), ("gmres_restart", c_int), ("max_iter", c_int), ("tol", c_double),
                 ("no_fmm", c_int), ("profile", c_int), ("precond", c_int), ("q_max", c_int),
-                ("no_graph", c_int)]
+                ("m2l_stored", c_int), ("no_graph", c_int)]
 
 
 class igabem_info(ctypes.Structure):
@@ -96,6 +96,8 @@ SIGNATURES = {
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_wait_selftest": (c_int, [c_void_p, ctypes.c_double]),
     "igabem_measure_peaks": (c_int, [c_void_p, ctypes.POINTER(igabem_peaks)]),
+    "igabem_solve_sources": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
+    "igabem_rhs_sources": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_server_create": (c_int, [c_void_p, c_size_t, c_int, ctypes.POINTER(c_void_p)]),
     "igabem_server_destroy": (c_int, [c_void_p]),
     "igabem_submit": (c_int, [c_void_p, c_void_p, ctypes.POINTER(igabem_options), c_int, c_void_p, c_int,
@@ -242,6 +244,26 @@ def igabem_solve(prob, dirs, n_dofs: int, density=None, raise_on_not_converged=T
     if rc != IGABEM_OK and (raise_on_not_converged or rc != -4):
         _check(rc)
     return density, {k: getattr(info, k) for k, _ in igabem_solve_info._fields_}
+
+
+def igabem_solve_sources(prob, z, n_dofs: int, density=None, raise_on_not_converged=True):
+    """Solve for incident point sources G(x, z_r) at the points z [n][3]."""
+    zz = _host(z, np.float64).reshape(-1, 3)
+    R = zz.shape[0]
+    density = np.empty((n_dofs, R), np.complex128) if density is None else density
+    info = igabem_solve_info()
+    rc = lib().igabem_solve_sources(prob, R, _ptr(zz), _ptr(density), ctypes.byref(info))
+    if rc != IGABEM_OK and (raise_on_not_converged or rc != -4):
+        _check(rc)
+    return density, {k: getattr(info, k) for k, _ in igabem_solve_info._fields_}
+
+
+def igabem_rhs_sources(prob, z, n_dofs: int, out=None):
+    zz = _host(z, np.float64).reshape(-1, 3)
+    R = zz.shape[0]
+    out = np.empty((n_dofs, R), np.complex128) if out is None else out
+    _check(lib().igabem_rhs_sources(prob, R, _ptr(zz), _ptr(out)))
+    return out
 
 
 def igabem_farfield(prob, density, xhat, out=None):

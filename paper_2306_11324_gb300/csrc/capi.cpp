@@ -378,6 +378,9 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     }
     total += 256;  // status word
     total += bytes_of(S.nbr);
+    if (opt->m2l_stored && S.n_far > 0)
+      for (int l = S.lmin; l <= S.L; ++l)
+        total += (m2l_stored_entries(S, l) * (mixed ? sizeof(float2) : sizeof(double2)) + 255) & ~size_t(255);
     if (S.n_far > 0 && leaf_moments_supported(S))
       total += ((leaf_moment_entries(S) * (mixed ? sizeof(float) : sizeof(double))) + 255) & ~size_t(255);
     P->arena_bytes = total + 4096;
@@ -492,6 +495,13 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   if (S.n_far > 0) {
     Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
     launch_pair_consts(d, S, opt->kappa, opt->eta_cfie, st);
+  }
+  d.m2ls.assign(S.L + 1, nullptr);
+  if (opt->m2l_stored && S.n_far > 0) {
+    for (int l = S.lmin; l <= S.L; ++l)
+      d.m2ls[l] = A.get<double>(m2l_stored_entries(S, l) * (mixed ? 1 : 2));
+    Phase ph(&P->prof, IGABEM_PH_SETUP_TABLES, st);
+    launch_m2l_fill(d, S, *opt, st);
   }
   launch_near_field(d, S, *opt, st);
   if (opt->precond) {
@@ -769,7 +779,40 @@ int igabem_matvec(igabem_problem *P, int n_rhs, const void *x, void *y) {
   });
 }
 
+namespace {
+int solve_impl(igabem_problem *P, int n_rhs, const double *dirs, int kind, void *density, igabem_solve_info *info);
+}
+
 int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density, igabem_solve_info *info) {
+  return solve_impl(P, n_rhs, dirs, 0, density, info);
+}
+
+int igabem_solve_sources(igabem_problem *P, int n_rhs, const double *z, void *density, igabem_solve_info *info) {
+  return solve_impl(P, n_rhs, z, 1, density, info);
+}
+
+int igabem_rhs_sources(igabem_problem *P, int n_rhs, const double *z, void *b) {
+  return guarded([&] {
+    if (!P || !z || !b || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid rhs arguments");
+    IGA_CUDA(cudaSetDevice(P->geom->ctx->device));
+    ensure_work(P, n_rhs, false);
+    cudaStream_t st = P->stream;
+    ProblemWork &W = ext(P)->work;
+    IGA_CUDA(cudaMemcpyAsync(W.red, z, 3 * sizeof(double) * n_rhs, cudaMemcpyHostToDevice, st));
+    bool dev = is_device_ptr(b);
+    double *out = dev ? static_cast<double *>(b) : W.yout;
+    launch_rhs(P->d, P->S, P->opt, n_rhs, W.red, out, st, 1);
+    if (!dev)
+      IGA_CUDA(cudaMemcpyAsync(b, out, P->S.N * n_rhs * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+    P->prof.flush();
+  });
+}
+
+}  // extern "C"
+
+namespace {
+int solve_impl(igabem_problem *P, int n_rhs, const double *dirs, int kind, void *density, igabem_solve_info *info) {
   int status = IGABEM_OK;
   int rc = guarded([&] {
     if (!P || !dirs || !density || n_rhs <= 0) fail(IGABEM_EINVAL, "invalid solve arguments");
@@ -789,7 +832,7 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
     G.maxit = maxit;
     G.tol = tol;
     IGA_CUDA(cudaMemcpyAsync(W.red, dirs, 3 * sizeof(double) * R, cudaMemcpyHostToDevice, st));
-    launch_rhs(P->d, S, P->opt, R, W.red, W.b, st);
+    launch_rhs(P->d, S, P->opt, R, W.red, W.b, st, kind);
     std::vector<double> bn(R), beta(R);
     std::vector<int> its(R, 0), act(R);
     auto norms = [&](const double *v, std::vector<double> &out, double *dev_copy) {
@@ -949,6 +992,9 @@ int igabem_solve(igabem_problem *P, int n_rhs, const double *dirs, void *density
   });
   return rc != IGABEM_OK ? rc : status;
 }
+}  // namespace
+
+extern "C" {
 
 int igabem_farfield(igabem_problem *P, int n_rhs, const void *density, int n_dir, const double *xhat,
                     void *uinf) {

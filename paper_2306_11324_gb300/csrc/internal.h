@@ -212,6 +212,8 @@ struct DeviceProblem {
   std::vector<double *> cext;                // per level: [n][2] node extent and largest Jacobian
   std::vector<double *> chebl;               // per level: its q Chebyshev points on [0,1]
   std::vector<double *> T1l;                 // per level: [2][q][q] transfer to the children (same q)
+  std::vector<double *> m2ls;                // stored M2L blocks per level (m2l_stored): [n_far][types][q^2 b][q^2 a]
+                                             // complex, FP32 (mixed) or FP64, pair phase factor folded in
   std::vector<double *> LGl;                 // per band-bottom level: [2^(m-l)][ng][q] Lagrange at Gauss points
   std::vector<uint8_t *> tc_bimg;            // per level: tensor-core M2L operands of the sources
   std::vector<float *> tc_bscale;            // per level: power-of-two scale of each cluster's operand

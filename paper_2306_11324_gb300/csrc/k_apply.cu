@@ -731,6 +731,9 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         note_launch();
       }
     }
+    const bool stored = !d.m2ls.empty() && d.m2ls[S.lmin];
+    const bool tc = !stored && o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() &&
+                    d.tc_bimg[S.L];
     {
       Phase ph(d.prof, IGABEM_PH_M2M, st);
       for (int l = S.L - 1; l >= S.lmin; --l) {
@@ -754,18 +757,14 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         }
         note_launch();
       }
+      if (f32 && !tc)  // the upward pass's expansions in FP32 for the FP32 M2L kernels
+        for (int l = S.lmin; l <= S.L; ++l)
+          to_f32(d.xhat[l], d.xhat32[l], (long)S.lev[l].n * S.lev[l].q * S.lev[l].q * D.CR, st);
     }
-    const bool tc = o.precision == IGABEM_MIXED_TC && m2l_tc_supported(S, R) && !d.tc_bimg.empty() && d.tc_bimg[S.L];
     if (m2l_rows_supported(S, o, R)) {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
-      if (tc) {
-        launch_m2l_tc(d, S, o, R, st);
-      } else {
-        if (f32)  // the expansions of the upward pass in FP32 for the FP32 M2L
-          for (int l = S.lmin; l <= S.L; ++l)
-            to_f32(d.xhat[l], d.xhat32[l], (long)S.lev[l].n * S.lev[l].q * S.lev[l].q * D.CR, st);
-        launch_m2l_rows(d, S, o, R, f32, st);
-      }
+      if (tc) launch_m2l_tc(d, S, o, R, st);
+      else launch_m2l_rows(d, S, o, R, f32, st);
     } else {
       Phase ph(d.prof, IGABEM_PH_M2L, st);
       for (int l = S.lmin; l <= S.L; ++l) {

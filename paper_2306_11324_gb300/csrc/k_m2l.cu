@@ -37,6 +37,7 @@ struct M2LLevel {
   const float *pc;       // FP32 pair constants [n_far][8]: D, |D|, |D|^2, cos, sin of kappa|D| (FP32 path)
   const double2 *xhat;
   const float2 *xhat32;  // FP32 copy of xhat (the FP32 kernels read it)
+  const void *stored;    // stored coupling blocks of the level (m2l_stored) or nullptr
   double2 *yhat;
   int n;                 // clusters on the level
   int first;             // first block index of the level in the flattened grid
@@ -227,6 +228,129 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_rows(M2LArgs A, int cr0)
   }
 }
 
+// ---- stored coupling blocks (m2l_stored): the same kernel samples (node_sample, the samples of the
+// multi-column M2L) generated once per problem, then streamed by every product ----
+
+// one thread block per admissible pair k of a level: every entry S_k[type][b][a] (column-major: the
+// target node a runs fastest) with the pair factor exp(i kappa |D|) folded in (FP32 path)
+template <class T>
+__global__ void __launch_bounds__(256) k_m2l_fill(M2LLevel L, bool hard, double kappa, double eta,
+                                                  C2<T> *__restrict__ out) {
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const long kk = blockIdx.x;
+  const int Q = L.Q, ntype = hard ? 2 : 1;
+  const long NQ = (long)L.n * Q;
+  int lo = 0, hi = L.n;  // target t with far_ptr[t] <= kk < far_ptr[t + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (L.far_ptr[mid] <= kk) lo = mid;
+    else hi = mid;
+  }
+  const int t = lo, s = L.far_src[kk];
+  T D[3] = {0, 0, 0}, Dn = 0, D2 = 0;
+  C2<T> e0 = c2((T)1, (T)0);
+  if constexpr (F32) {
+    const float *pc = L.pc + 8 * kk;
+    D[0] = pc[0]; D[1] = pc[1]; D[2] = pc[2]; Dn = pc[3]; D2 = pc[4];
+    e0 = c2(pc[5], pc[6]);
+  }
+  C2<T> *S = out + kk * (long)ntype * Q * Q;
+  for (int o = threadIdx.x; o < ntype * Q * Q; o += blockDim.x) {
+    const int ty = o / (Q * Q), b = (o / Q) % Q, a = o % Q;
+    T X[7], Y[7];
+    for (int c = 0; c < 7; ++c) {
+      X[c] = F32 ? (T)L.nodes32[c * NQ + (long)t * Q + a] : (T)L.nodes[c * NQ + (long)t * Q + a];
+      Y[c] = F32 ? (T)L.nodes32[c * NQ + (long)s * Q + b] : (T)L.nodes[c * NQ + (long)s * Q + b];
+    }
+    const int type = hard ? (ty == 0 ? 1 : 2) : 0;
+    const C2<T> v = node_sample<T>(type, X, X + 3, X[6], Y, Y + 3, Y[6], D, Dn, D2, (T)kappa, (T)eta);
+    S[o] = F32 ? mul(e0, v) : v;
+  }
+}
+
+// M2L from the stored blocks: the row kernel's layout (one block per target cluster, warps over the
+// interaction list, lane rows a0 + lane, a0 + lane + 32) with the samples read from the stored block
+// (coalesced: consecutive lanes read consecutive target nodes) instead of generated.
+template <class T, int NCR, bool HARD>
+__global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_stored(M2LArgs A, int cr0) {
+  extern __shared__ __align__(16) unsigned char smst[];
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int li = 0;
+  while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
+  const M2LLevel &L = A.lev[li];
+  const int t = blockIdx.x - L.first;
+  const int Q = L.Q, q = L.q, QS = A.QS, ntype = HARD ? 2 : 1;
+  const int ncr = min(NCR, A.CR - cr0);
+  C2<T> *xs = reinterpret_cast<C2<T> *>(smst) + warp * QS * NCR;
+  double2 *red = reinterpret_cast<double2 *>(smst);
+  const C2<T> *Sall = reinterpret_cast<const C2<T> *>(L.stored);
+  for (int a0 = 0; a0 < Q; a0 += 64) {
+    C2<T> tot[2][NCR];
+    for (int k = 0; k < 2; ++k)
+      for (int c = 0; c < NCR; ++c) tot[k][c] = c2((T)0, (T)0);
+    for (int kk = L.far_ptr[t] + warp; kk < L.far_ptr[t + 1]; kk += M2L_WARPS) {
+      const int s = L.far_src[kk];
+      __syncwarp();
+      for (int b = lane; b < Q; b += 32) {
+        const long ib = (long)s * Q + b;
+        for (int c = 0; c < ncr; ++c) {
+          if constexpr (F32) {
+            const float2 v = L.xhat32[ib * A.CR + cr0 + c];
+            xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+          } else {
+            const double2 v = L.xhat[ib * A.CR + cr0 + c];
+            xs[b * NCR + c] = c2((T)v.x, (T)v.y);
+          }
+        }
+      }
+      __syncwarp();
+      const C2<T> *Sk = Sall + (long)kk * ntype * Q * Q;
+      for (int k = 0; k < 2; ++k) {
+        const int a = a0 + lane + 32 * k;
+        if (a >= Q) continue;
+        C2<T> acc[NCR];
+        for (int c = 0; c < NCR; ++c) acc[c] = c2((T)0, (T)0);
+        for (int b1 = 0; b1 < q; ++b1) {
+          C2<T> part[NCR];
+          for (int c = 0; c < NCR; ++c) part[c] = c2((T)0, (T)0);
+          for (int b2 = 0; b2 < q; ++b2) {
+            const int b = b1 * q + b2;
+            const C2<T> s0 = Sk[(long)b * Q + a];
+            if (!HARD) {
+              for (int c = 0; c < NCR; ++c) part[c] = fma2(s0, xs[b * NCR + c], part[c]);
+            } else {
+              const C2<T> s1 = Sk[(long)(Q + b) * Q + a];
+              for (int c = 0; c < NCR; ++c) part[c] = fma2((cr0 + c) / A.R == 0 ? s0 : s1, xs[b * NCR + c], part[c]);
+            }
+          }
+          for (int c = 0; c < NCR; ++c) acc[c] = add(acc[c], part[c]);
+        }
+        for (int c = 0; c < NCR; ++c) tot[k][c] = add(tot[k][c], acc[c]);
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < 2; ++k)
+      for (int c = 0; c < NCR; ++c) {
+        const int a = lane + 32 * k;
+        red[(warp * 64 + a) * NCR + c] = make_double2((double)tot[k][c].x, (double)tot[k][c].y);
+      }
+    __syncthreads();
+    const int na = min(64, Q - a0);
+    for (int o = threadIdx.x; o < na * ncr; o += blockDim.x) {
+      const int a = o / ncr, c = o % ncr;
+      double2 sum = make_double2(0, 0);
+      for (int w = 0; w < M2L_WARPS; ++w) {
+        const double2 v = red[(w * 64 + a) * NCR + c];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      L.yhat[((long)t * Q + a0 + a) * A.CR + cr0 + c] = sum;
+    }
+    __syncthreads();
+  }
+}
+
 // Multi-column M2L: per target cluster and column chunk, every coupling block S_ts (q^2 x q^2) is
 // generated once into shared memory and applied to the chunk's columns of xhat_s with a register
 // tiled product (4 x 4 complex outputs per thread).  A chunk lies within one channel, so one kernel
@@ -392,6 +516,26 @@ void launch_rows(const M2LArgs &A, int nblocks, cudaStream_t st) {
   }
 }
 
+template <class T, int NCR, bool HARD>
+void launch_stored(const M2LArgs &A, int nblocks, cudaStream_t st) {
+  const size_t smem = std::max((size_t)M2L_WARPS * A.QS * NCR * sizeof(C2<T>), (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
+  auto kfn = k_m2l_stored<T, NCR, HARD>;
+  IGA_CUDA(set_max_dynamic_smem(kfn, smem));
+  for (int cr0 = 0; cr0 < A.CR; cr0 += NCR) {
+    kfn<<<nblocks, 32 * M2L_WARPS, smem, st>>>(A, cr0);
+    note_launch();
+  }
+}
+
+template <class T>
+void launch_stored_typed(const M2LArgs &A, int nblocks, cudaStream_t st) {
+  if (A.hard) launch_stored<T, 7, true>(A, nblocks, st);
+  else if (A.CR == 1) launch_stored<T, 1, false>(A, nblocks, st);
+  else if (A.CR == 2) launch_stored<T, 2, false>(A, nblocks, st);
+  else if (A.CR < 8) launch_stored<T, 4, false>(A, nblocks, st);
+  else launch_stored<T, 8, false>(A, nblocks, st);
+}
+
 template <class T>
 void launch_typed(const M2LArgs &A, int nblocks, cudaStream_t st) {
   if (A.hard) {
@@ -420,6 +564,36 @@ void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa
     k_pair_consts<<<(int)((nfar + 255) / 256), 256, 0, st>>>(d.far_ptr[l], d.far_src[l], d.centers[l],
                                                              reinterpret_cast<const double2 *>(d.cext[l]), n, nfar,
                                                              kappa, eta, d.pairc[l]);
+    note_launch();
+  }
+  IGA_CUDA(cudaGetLastError());
+}
+
+size_t m2l_stored_entries(const HostSetup &S, int l) {
+  const size_t Q = (size_t)S.lev[l].q * S.lev[l].q;
+  return S.lev[l].far_src.size() * Q * Q * (S.hard ? 2 : 1);
+}
+
+void launch_m2l_fill(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, cudaStream_t st) {
+  const bool fp32 = o.precision != IGABEM_FP64;
+  for (int l = S.lmin; l <= S.L; ++l) {
+    const long nfar = (long)S.lev[l].far_src.size();
+    if (nfar == 0) continue;
+    M2LLevel L{};
+    L.far_ptr = d.far_ptr[l];
+    L.far_src = d.far_src[l];
+    L.nodes = d.nodes[l];
+    L.nodes32 = d.nodes32[l];
+    L.pc = d.pairc[l];
+    L.n = S.lev[l].n;
+    L.q = S.lev[l].q;
+    L.Q = L.q * L.q;
+    if (fp32)
+      k_m2l_fill<float><<<(unsigned)nfar, 256, 0, st>>>(L, S.hard, o.kappa, o.eta_cfie,
+                                                        reinterpret_cast<C2<float> *>(d.m2ls[l]));
+    else
+      k_m2l_fill<double><<<(unsigned)nfar, 256, 0, st>>>(L, S.hard, o.kappa, o.eta_cfie,
+                                                         reinterpret_cast<C2<double> *>(d.m2ls[l]));
     note_launch();
   }
   IGA_CUDA(cudaGetLastError());
@@ -456,6 +630,7 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     L.pc = d.pairc[l];
     L.xhat = reinterpret_cast<const double2 *>(d.xhat[l]);
     L.xhat32 = d.xhat32.empty() ? nullptr : d.xhat32[l];
+    L.stored = d.m2ls.empty() ? nullptr : d.m2ls[l];
     L.yhat = reinterpret_cast<double2 *>(d.yhat[l]);
     L.n = S.lev[l].n;
     L.first = nblocks;
@@ -464,7 +639,10 @@ void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_op
     A.QS = std::max(A.QS, L.Q);
     nblocks += S.lev[l].n;
   }
-  if (R > 1 && A.QS <= 64) {
+  if (A.nlev > 0 && A.lev[0].stored) {  // stored coupling blocks: stream them
+    if (fp32) launch_stored_typed<float>(A, nblocks, st);
+    else launch_stored_typed<double>(A, nblocks, st);
+  } else if (R > 1 && A.QS <= 64) {
     // column chunk: the largest divisor of R not above 64 (chunks never straddle two channels)
     int Wc = 1;
     for (int w = std::min(R, 64); w >= 1; --w)

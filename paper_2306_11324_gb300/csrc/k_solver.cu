@@ -19,16 +19,19 @@ inline int grid_for(long n, int block = 256) {
 struct RhsArgs {
   const double *gpx, *gpn, *gpa, *phi1, *gw;
   const int *g2x_ptr, *g2x_idx;
-  const double *dirs;
+  const double *dirs;     // per right-hand side: the direction d (plane wave) or the source point z
   long gst, N;
   int n1, nb, p, ng, R;
   double h, kappa, eta;
   bool hard;
+  int kind;               // 0 plane waves exp(i kappa d.x); 1 point sources G(x, z)
 };
 
 // b[i][r] = sum over the elements of the supports of psi_i of sum_q w_q h^2 psi(q) f_r(q),
-//   soft: f = (i kappa d.n~ - i eta a) exp(i kappa d.x)   (a (du_inc/dn - i eta u_inc))
-//   hard: f = (a + eta kappa d.n~) exp(i kappa d.x)         (a (u_inc - i eta du_inc/dn))
+//   soft: f = grad u_inc . n~ - i eta a u_inc        (a (du_inc/dn - i eta u_inc))
+//   hard: f = a u_inc - i eta grad u_inc . n~        (a (u_inc - i eta du_inc/dn))
+// with u_inc = exp(i kappa d.x), grad u_inc = i kappa d u_inc (plane wave), or u_inc = G(x, z),
+// grad u_inc = G (i kappa r - 1) / r^2 (x - z), r = |x - z| (point source at z).
 __global__ void k_rhs(RhsArgs A, double2 *__restrict__ b) {
   const int p1 = A.p + 1, nq = A.ng * A.ng;
   GRID_STRIDE(o, A.N * A.R) {
@@ -48,13 +51,26 @@ __global__ void k_rhs(RhsArgs A, double2 *__restrict__ b) {
               long iq = e * nq + q1 * A.ng + q2;
               double x[3] = {A.gpx[iq], A.gpx[A.gst + iq], A.gpx[2 * A.gst + iq]};
               double n[3] = {A.gpn[iq], A.gpn[A.gst + iq], A.gpn[2 * A.gst + iq]};
-              double dx = d[0] * x[0] + d[1] * x[1] + d[2] * x[2];
-              double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
-              double s, c;
-              sincos(A.kappa * dx, &s, &c);
-              double2 f = A.hard ? cmk(A.gpa[iq] + A.eta * A.kappa * dn, 0.0)
-                                 : cmk(0.0, A.kappa * dn - A.eta * A.gpa[iq]);
-              f = cmul(f, cmk(c, s));
+              double2 f;
+              if (A.kind == 0) {
+                double dx = d[0] * x[0] + d[1] * x[1] + d[2] * x[2];
+                double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+                double s, c;
+                sincos(A.kappa * dx, &s, &c);
+                f = A.hard ? cmk(A.gpa[iq] + A.eta * A.kappa * dn, 0.0) : cmk(0.0, A.kappa * dn - A.eta * A.gpa[iq]);
+                f = cmul(f, cmk(c, s));
+              } else {
+                const double v[3] = {x[0] - d[0], x[1] - d[1], x[2] - d[2]};
+                const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                double s, c;
+                sincos(A.kappa * r, &s, &c);
+                const double2 u = cmk(c / (4.0 * IGA_PI * r), s / (4.0 * IGA_PI * r));
+                const double vn = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / (r * r);
+                const double2 gn = cscale(cmul(u, cmk(-1.0, A.kappa * r)), vn);   // grad u_inc . n~
+                const double2 ie_gn = cmk(A.eta * gn.y, -A.eta * gn.x);         // i eta grad u . n~
+                const double2 ie_u = cmk(-A.eta * u.y * A.gpa[iq], A.eta * u.x * A.gpa[iq]);  // i eta a u
+                f = A.hard ? csub(cscale(u, A.gpa[iq]), ie_gn) : csub(gn, ie_u);
+              }
               double w = A.gw[q1] * A.gw[q2] * A.h * A.h *
                          A.phi1[(ix * A.ng + q1) * p1 + ka] * A.phi1[(iy * A.ng + q2) * p1 + kb];
               acc = cadd(acc, cscale(f, w));
@@ -444,16 +460,18 @@ RhsArgs rhs_args(const DeviceProblem &d, const HostSetup &S, const igabem_option
   A.gst = (long)S.E * S.ng * S.ng; A.N = S.N;
   A.n1 = S.n1; A.nb = S.nb; A.p = S.p; A.ng = S.ng; A.R = R;
   A.h = S.h; A.kappa = o.kappa; A.eta = o.eta_cfie; A.hard = S.hard;
+  A.kind = 0;
   return A;
 }
 
 }  // namespace
 
 void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
-                const double *dirs_dev, double *b, cudaStream_t st) {
+                const double *dirs_dev, double *b, cudaStream_t st, int kind) {
   Phase ph(d.prof, IGABEM_PH_RHS, st);
   RhsArgs A = rhs_args(d, S, o, R);
   A.dirs = dirs_dev;
+  A.kind = kind;
   k_rhs<<<grid_for(S.N * R), 256, 0, st>>>(A, reinterpret_cast<double2 *>(b));
   note_launch();
   IGA_CUDA(cudaGetLastError());

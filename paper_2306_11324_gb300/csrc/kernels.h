@@ -10,6 +10,9 @@ void launch_gauss_geometry(const DeviceProblem &d, const HostSetup &S, cudaStrea
 void launch_node_geometry(const DeviceProblem &d, const HostSetup &S, cudaStream_t st);
 void launch_pair_consts(const DeviceProblem &d, const HostSetup &S, double kappa, double eta, cudaStream_t st);
 bool m2l_rows_supported(const HostSetup &S, const igabem_options &o, int R);
+// stored M2L coupling blocks (m2l_stored): complex entries of level l, and their generation at set-up
+size_t m2l_stored_entries(const HostSetup &S, int l);
+void launch_m2l_fill(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, cudaStream_t st);
 void launch_m2l_rows(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      bool fp32, cudaStream_t st);
 // tensor-core M2L for R right-hand sides (k_m2l_tc.cu); yhat from xhat through d.tc_bimg
@@ -46,8 +49,9 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
                    const double *x, double *y, cudaStream_t st);
 
 // right-hand sides and far field (k_solver.cu)
+// kind 0: plane waves with directions dirs; kind 1: point sources at the points dirs
 void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
-                const double *dirs_dev, double *b, cudaStream_t st);
+                const double *dirs_dev, double *b, cudaStream_t st, int kind = 0);
 // scratch: device space for E ng^2 R complex values (the weighted density at the Gauss points)
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      const double *dens, int n_dir, const double *xhat_dev, double *uinf, double *scratch,

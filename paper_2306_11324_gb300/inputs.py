@@ -225,6 +225,42 @@ def patches_to_arrays(patches: list[NurbsPatch]):
     return deg, cnt, knots, ctrl, w
 
 
+def torus_patches(R: float = 2.0, r: float = 0.5) -> list[NurbsPatch]:
+    """The torus with major radius R and minor radius r as 16 exact rational biquadratic patches:
+    a surface of revolution whose profile (the minor circle) and sweep (the major circle) are each
+    four rational quadratic quarter-circle arcs (control points on the arc ends and at the corner of
+    their tangents, middle weight 1/sqrt(2)); patch (i, j) covers the quarter i of the major circle
+    and the quarter j of the minor circle, so neighbouring patches share edge parametrisations.  The
+    parameter s runs along the major circle and t along the minor one, which makes d_s F x d_t F
+    point out of the enclosed volume."""
+    h = 1.0 / np.sqrt(2.0)
+    w3 = np.array([1.0, h, 1.0])
+
+    def arc(k):   # unit-circle quarter arc k (angles k pi/2 .. (k+1) pi/2): 2-D control points
+        a0, a1 = k * np.pi / 2, (k + 1) * np.pi / 2
+        p0 = np.array([np.cos(a0), np.sin(a0)])
+        p2 = np.array([np.cos(a1), np.sin(a1)])
+        return np.stack([p0, p0 + p2, p2])   # the corner of the two tangents is p0 + p2 for a quarter arc
+
+    knots = np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    patches = []
+    for i in range(4):          # major circle (sweep), parameter t
+        C = arc(i)
+        for j in range(4):      # minor circle (profile), parameter s
+            Dm = arc(j)
+            ctrl = np.zeros((3, 3, 3))
+            wts = np.zeros((3, 3))
+            for a in range(3):      # s index (profile)
+                for b in range(3):  # t index (sweep)
+                    rho = R + r * Dm[a, 0]     # distance of the profile control point from the axis
+                    ctrl[a, b] = [rho * C[b, 0], rho * C[b, 1], r * Dm[a, 1]]
+                    wts[a, b] = w3[a] * w3[b]
+            # first parameter along the sweep: d_s F x d_t F then points outward
+            patches.append(NurbsPatch(2, 2, knots.copy(), knots.copy(), ctrl.transpose(1, 0, 2).copy(),
+                                      wts.T.copy()))
+    return patches
+
+
 def polyhedral_torus_patches(R: float = 2.0, r: float = 0.5, n_major: int = 4, n_minor: int = 4):
     """A closed genus-1 surface of n_major x n_minor flat bilinear patches whose corners lie on the
     torus with radii (R, r); used where a closed surface with Euler characteristic 0 is needed."""

@@ -23,15 +23,16 @@ def _prec(name):
     return {"fp64": B.FP64, "mixed": B.MIXED_FP32, "tc": B.MIXED_TC}[name]
 
 
-def _problem(c, prec):
+def _problem(c, prec, stored=0):
     return G.problem(c["geometry"], level_m=c["m"], degree_p=c["p"], kappa=c["kappa"], eta_cfie=c["eta"],
                      bc=int(c["hard"]), cheb_q=c["q"], leaf_offset=c["m"] - c["leaf"], eta_adm=0.5,
-                     kappa_cap=0.0 if not np.isfinite(c["cap"]) else c["cap"], precision=_prec(prec))
+                     kappa_cap=0.0 if not np.isfinite(c["cap"]) else c["cap"], precision=_prec(prec),
+                     m2l_stored=stored)
 
 
-def _check(name, prec, single_column=True):
+def _check(name, prec, single_column=True, stored=0):
     c, rows, ref, N, n_far = golden.load(name)
-    prob, info = _problem(c, prec)
+    prob, info = _problem(c, prec, stored)
     assert info["n_dofs"] == N and info["n_far_pairs"] == n_far
     x = inputs.random_complex(N, seed=c["seed"], cols=c["cols"])
     y = B.igabem_matvec(prob, x if c["cols"] > 1 else x[:, 0])
@@ -59,11 +60,12 @@ def test_deformed_multispan_sound_hard_p2_q7_capped(prec):
     _check("deformed_hard_m4_p2_q7_b2_k8_cap6", prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_default_workload_matvec_against_oracle_rows(prec):
-    """The default workload's operator (6936 unknowns, kappa = 8) on a seeded vector: the plain FP64
-    GPU matvec and the mixed-precision one against the oracle's rows."""
-    _check("sphere_soft_6x32x32_p2_k8", prec)
+@pytest.mark.parametrize("prec,stored", [("fp64", 0), ("mixed", 0), ("fp64", 1), ("mixed", 1)])
+def test_6x32x32_workload_matvec_against_oracle_rows(prec, stored):
+    """The 32 x 32-element workload's operator (6936 unknowns, kappa = 8) on a seeded vector: the plain
+    FP64 GPU matvec and the mixed-precision one, with the coupling blocks generated on the fly and
+    stored, against the oracle's rows."""
+    _check("sphere_soft_6x32x32_p2_k8", prec, stored=stored)
 
 
 @pytest.mark.parametrize("prec", ["tc", "mixed"])

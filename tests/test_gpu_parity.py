@@ -304,3 +304,39 @@ def test_graph_captured_gmres_equals_eager_launches(pc):
         B.igabem_problem_destroy(prob)
     assert out[0][1]["iterations"] == out[1][1]["iterations"] > 8     # more than one restart cycle
     assert G.rel(out[0][0], out[1][0]) < 1e-12
+
+
+@pytest.mark.parametrize("prec,hard,R", [(B.FP64, False, 1), (B.FP64, True, 3), (B.MIXED_FP32, False, 4),
+                                         (B.MIXED_FP32, True, 1), (B.MIXED_TC, False, 16)])
+def test_stored_coupling_blocks_match_oracle(prec, hard, R):
+    """NEXT-2: the M2L coupling blocks generated once at set-up and streamed by every product (the
+    paper's stored H^2 operator) give the oracle's mode-B product, and the same product as the
+    blocks generated on the fly."""
+    m, p, leaf, q, kappa = 2, 1, 2, 5, 3.0
+    kw = dict(level_m=m, degree_p=p, kappa=kappa, eta_cfie=kappa, bc=int(hard), cheb_q=q, leaf_offset=m - leaf,
+              eta_adm=0.5, precision=prec)
+    prob, info = G.problem(m2l_stored=1, **kw)
+    fly, _ = G.problem(**kw)
+    sp = C.sphere_space(m, p, hard)
+    Amat = C.cfie(m, p, kappa, kappa, hard, mode_b=(leaf, 0.5, q))
+    x = inputs.random_complex(sp.N, seed=95, cols=R)
+    y = B.igabem_matvec(prob, x)
+    tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
+    assert G.rel(y, Amat @ x) < tol
+    assert G.rel(y, B.igabem_matvec(fly, x)) < (1e-12 if prec == B.FP64 else MIXED_MATVEC_TOL)
+    B.igabem_problem_destroy(prob)
+    B.igabem_problem_destroy(fly)
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED_FP32])
+def test_stored_coupling_blocks_with_level_adaptive_q(prec):
+    """Stored blocks of 10 x 10 and 6 x 6 nodes (level-adaptive q) against the oracle's mode-B rows."""
+    prob, info = G.problem(level_m=3, degree_p=1, kappa=16.0, eta_cfie=16.0, cheb_q=4, kappa_cap=2.0, q_max=10,
+                           leaf_offset=0, eta_adm=0.5, precision=prec, m2l_stored=1)
+    tree, rows, ref3 = _adaptive_rows()
+    sp = C.sphere_space(3, 1)
+    x = inputs.random_complex(sp.N, seed=93, cols=3)
+    y3 = B.igabem_matvec(prob, x)
+    tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
+    assert np.abs(y3[rows] - ref3).max() / np.abs(ref3).max() < tol
+    B.igabem_problem_destroy(prob)

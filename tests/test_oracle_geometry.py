@@ -149,3 +149,31 @@ def test_continuous_space_traces_agree_across_interfaces():
     from scipy.spatial import cKDTree
     for a, b in cKDTree(pts).query_pairs(1e-11):
         assert abs(vals[a] - vals[b]) < 1e-12
+
+
+def test_exact_torus_lies_on_the_torus_conforms_and_points_outward():
+    """The 16 rational biquadratic patches of the convergence workload (Sec. 5.2: torus R = 2, r = 0.5):
+    every point satisfies (rho - R)^2 + z^2 = r^2, shared edges carry equal parametrisations, the
+    normals point out (int x . n = 3 vol = 6 pi^2 R r^2) and S^0 has dimension 16 (2^m+p-1)^2 (Euler
+    characteristic 0)."""
+    patches = inputs.torus_patches(2.0, 0.5)
+    rng = np.random.default_rng(3)
+    for p in patches:
+        s, t = rng.uniform(0, 1, 300), rng.uniform(0, 1, 300)
+        F, _, _ = bspline.nurbs_eval(p, s, t)
+        rho = np.hypot(F[:, 0], F[:, 1])
+        assert np.abs((rho - 2.0) ** 2 + F[:, 2] ** 2 - 0.25).max() < 1e-13
+    edges = [e for p in patches for e in _edge_samples(p)]
+    for i, a in enumerate(edges):
+        partners = [b for j, b in enumerate(edges) if j // 4 != i // 4 and
+                    (np.allclose(a, b, atol=1e-13) or np.allclose(a, b[::-1], atol=1e-13))]
+        assert len(partners) == 1
+    u, v, w = Q.tensor_rule(14)
+    total = 0.0
+    for p in patches:
+        F, Fs, Ft = bspline.nurbs_eval(p, u, v)
+        total += np.sum(w * np.sum(F * np.cross(Fs, Ft), axis=1))
+    assert abs(total - 6 * np.pi ** 2 * 2.0 * 0.25) < 1e-9
+    for m, p in ((1, 1), (2, 2)):
+        mesh = S.Mesh(patches, m)
+        assert S.Space(mesh, p, continuous=True).N == 16 * (2 ** m + p - 1) ** 2

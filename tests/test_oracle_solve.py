@@ -73,3 +73,20 @@ def test_mie_limits_and_optical_theorem():
             assert abs(4 * np.pi * np.mean(np.abs(u) ** 2) / (4 * np.pi / kappa * u0.imag) - 1) < 2e-3
     # sound-hard, kappa -> 0: no monopole; u_inf = O(kappa^2)
     assert np.abs(mie.mie_far_field(1e-3, xh[:5], D, True)).max() < 1e-5
+
+
+def test_point_source_right_hand_side_tends_to_the_plane_wave_one():
+    """A point source far away in the direction -d is a plane wave of direction d times
+    G(|z|) = exp(i kappa |z|)/(4 pi |z|), up to O(1/|z|): the point-source load vectors divided by G(|z|)
+    approach the plane-wave ones at that rate (sound-soft and sound-hard)."""
+    d = np.array([0.0, 0.6, 0.8])
+    k = 2.0
+    for hard in (False, True):
+        sp = C.sphere_space(1, 1, hard)
+        ref = A.rhs(sp, k, k, d, hard)
+        errs = []
+        for Rz in (1e3, 1e5):
+            b = A.rhs_point_sources(sp, k, k, -Rz * d, hard)[:, 0]
+            g = np.exp(1j * k * Rz) / (4 * np.pi * Rz)
+            errs.append(np.abs(b / g - ref).max() / np.abs(ref).max())
+        assert errs[0] < 10.0 / 1e3 and 50 < errs[0] / errs[1] < 200

@@ -307,6 +307,26 @@ int igabem_farfield_noalloc(igabem_problem *prob, int n_rhs, const void *density
    completed, IGABEM_EINVAL for a bad limit, IGABEM_ECUDA on a CUDA error.  The context stays usable. */
 int igabem_wait_selftest(igabem_ctx *ctx, double limit_s);
 
+/* Autotuner of the problem layout (the paper has no counterpart; it tunes this library's own
+   parameters).  For the geometry, options and n_rhs columns it sets up and times every candidate
+   layout that fits 60 % of the free device memory -- leaf_offset b in 1..min(level_m, 3) (leaves of
+   2^b x 2^b elements) with the M2L coupling blocks generated on the fly or stored -- scoring set-up time
+   + matvecs_per_setup x the time of one product (CUDA events, 3 products after a warm-up), and writes
+   the caller's options with the best leaf_offset and m2l_stored into *out.  Choices are cached in
+   memory and, when cache_path is not NULL, appended to that text file (one line per key: discretisation,
+   wavenumber, precision, column count, geometry fingerprint) and read from it on later calls, so a
+   later call with the same key returns at once (info->from_cache = 1).  Allocates device memory for the
+   candidates while it runs; IGABEM_ENOMEM if no candidate fits. */
+typedef struct {
+  int leaf_offset, m2l_stored;  /* the choice */
+  double setup_ms, matvec_ms;   /* measured for the choice (0 when taken from the cache) */
+  double score_ms;              /* setup_ms + matvecs_per_setup x matvec_ms */
+  int candidates;               /* layouts timed */
+  int from_cache;               /* 1: the choice came from the cache */
+} igabem_tune_info;
+int igabem_autotune(igabem_geom *geom, const igabem_options *opt, int n_rhs, int matvecs_per_setup,
+                    const char *cache_path, igabem_options *out, igabem_tune_info *info);
+
 /* Measured arithmetic rates of the context's device (the paper has no counterpart: these are the
    denominators against which the library's benchmark quotes the roofline fractions of its ALU-bound
    kernels).  Each rate is timed with CUDA events on the context's stream, best of five launches after

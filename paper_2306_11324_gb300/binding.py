@@ -67,6 +67,11 @@ class igabem_peaks(ctypes.Structure):
                 ("sm_clock_mhz_attr", c_double)]
 
 
+class igabem_tune_info(ctypes.Structure):
+    _fields_ = [("leaf_offset", c_int), ("m2l_stored", c_int), ("setup_ms", c_double), ("matvec_ms", c_double),
+                ("score_ms", c_double), ("candidates", c_int), ("from_cache", c_int)]
+
+
 class IgabemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -96,6 +101,8 @@ SIGNATURES = {
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_wait_selftest": (c_int, [c_void_p, ctypes.c_double]),
     "igabem_measure_peaks": (c_int, [c_void_p, ctypes.POINTER(igabem_peaks)]),
+    "igabem_autotune": (c_int, [c_void_p, ctypes.POINTER(igabem_options), c_int, c_int, ctypes.c_char_p,
+                                ctypes.POINTER(igabem_options), ctypes.POINTER(igabem_tune_info)]),
     "igabem_solve_sources": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
     "igabem_rhs_sources": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_server_create": (c_int, [c_void_p, c_size_t, c_int, ctypes.POINTER(c_void_p)]),
@@ -342,6 +349,16 @@ def igabem_farfield_noalloc(prob, density, xhat, uinf):
     R = _ncols(density)
     _check(lib().igabem_farfield_noalloc(prob, R, _ptr(density), int(xhat.shape[0]), _ptr(xhat), _ptr(uinf)))
     return uinf
+
+
+def igabem_autotune(geom, opt: igabem_options, n_rhs: int, matvecs_per_setup: int = 30, cache_path=None):
+    """(tuned options, info dict): the fastest leaf size / M2L storage for this geometry and options."""
+    out = igabem_options()
+    info = igabem_tune_info()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().igabem_autotune(geom, ctypes.byref(opt), int(n_rhs), int(matvecs_per_setup), path,
+                                 ctypes.byref(out), ctypes.byref(info)))
+    return out, {k: getattr(info, k) for k, _ in igabem_tune_info._fields_}
 
 
 def igabem_measure_peaks(ctx) -> dict:

@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 
 def test_autotune_picks_a_candidate_caches_it_and_keeps_the_operator(tmp_path):
-    kw = dict(level_m=4, degree_p=2, kappa=6.0, eta_cfie=6.0, cheb_q=6, eta_adm=0.5, precision=B.MIXED_FP32,
-              leaf_offset=2)
+    kw = dict(level_m=4, degree_p=2, kappa=6.0, eta_cfie=6.0, cheb_q=7, kappa_cap=4.0, eta_adm=0.5,
+              precision=B.MIXED_FP32, leaf_offset=2)
     opt = B.igabem_default_options(**kw)
     path = str(tmp_path / "tune.txt")
     tuned, info = B.igabem_autotune(G.geometry("sphere"), opt, 4, 30, path)

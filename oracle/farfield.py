@@ -38,3 +38,27 @@ def far_field(space, kappa, coeff, xhat, hard: bool, rules: ElementRules | None 
     if hard:
         return (-1j * kappa / (4 * np.pi)) * (ph * (xhat @ pts.n.T)) @ (wq * dens)
     return (-1.0 / (4 * np.pi)) * ph @ (wq * pts.a * dens)
+
+
+def potential(space, kappa, coeff, points, hard: bool, rules: ElementRules | None = None):
+    """The scattered field at points outside the scatterer (the representations of Sec. 2, Sec. 5.3's
+    potential evaluation), summed directly over the 4x4 Gauss points of every element:
+        sound-soft:  u_s(x) = -SL(t)(x) = -int G(x, y) t(y) dsigma_y
+        sound-hard:  u_s(x) =  DL(u)(x) =  int dG/dn_y(x, y) u(y) dsigma_y,
+    dG/dn_y = G'(r)/r (y - x).n_y, G'(r)/r = G (i kappa r - 1)/r^2; coeff (N,) -> (n_points,)."""
+    rules = rules or ElementRules(space)
+    pts = rules.pts
+    wq = np.tile(rules.w, space.mesh.E)
+    dens = density_at_points(space, coeff, rules)
+    X = np.atleast_2d(np.asarray(points, float))
+    out = np.zeros(X.shape[0], dtype=complex)
+    for i, x in enumerate(X):
+        v = pts.x - x                                   # y - x
+        r = np.linalg.norm(v, axis=1)
+        G = np.exp(1j * kappa * r) / (4 * np.pi * r)
+        if hard:
+            dGn = G * (1j * kappa * r - 1.0) / r ** 2 * np.sum(v * pts.n, axis=1)   # a dG/dn_y
+            out[i] = np.sum(wq * dGn * dens)
+        else:
+            out[i] = -np.sum(wq * pts.a * G * dens)
+    return out

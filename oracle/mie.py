@@ -29,3 +29,26 @@ def mie_far_field(kappa, xhat, d=(0.0, 0.0, 1.0), hard=False):
             h = j + 1j * spherical_yn(n, kappa)
         out += (2 * n + 1) * (j / h) * eval_legendre(n, c)
     return 1j / kappa * out
+
+
+def mie_scattered_field(kappa, x, d=(0.0, 0.0, 1.0), hard=False):
+    """Scattered field u_s at points x (n, 3) outside the unit sphere, for the plane wave of direction d:
+    with theta = angle(x, d) and r = |x|,
+        sound-soft:  u_s = -sum_n (2n+1) i^n [j_n(kappa) / h_n(kappa)] h_n(kappa r) P_n(cos theta)
+        sound-hard:  u_s = -sum_n (2n+1) i^n [j_n'(kappa) / h_n'(kappa)] h_n(kappa r) P_n(cos theta)
+    (the expansion of the incident wave in spherical waves, u_inc = sum (2n+1) i^n j_n(kappa r) P_n)."""
+    x = np.atleast_2d(np.asarray(x, float))
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    r = np.linalg.norm(x, axis=1)
+    c = np.clip((x @ d) / r, -1.0, 1.0)
+    nmax = int(kappa * r.max() + 4 * (kappa * r.max()) ** (1 / 3) + 20)
+    out = np.zeros(r.shape, dtype=complex)
+    for n in range(nmax + 1):
+        if hard:
+            a = spherical_jn(n, kappa, derivative=True) / (spherical_jn(n, kappa, derivative=True)
+                                                           + 1j * spherical_yn(n, kappa, derivative=True))
+        else:
+            a = spherical_jn(n, kappa) / (spherical_jn(n, kappa) + 1j * spherical_yn(n, kappa))
+        hn = spherical_jn(n, kappa * r) + 1j * spherical_yn(n, kappa * r)
+        out -= (2 * n + 1) * (1j ** n) * a * hn * eval_legendre(n, c)
+    return out

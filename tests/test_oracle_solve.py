@@ -90,3 +90,20 @@ def test_point_source_right_hand_side_tends_to_the_plane_wave_one():
             g = np.exp(1j * k * Rz) / (4 * np.pi * Rz)
             errs.append(np.abs(b / g - ref).max() / np.abs(ref).max())
         assert errs[0] < 10.0 / 1e3 and 50 < errs[0] / errs[1] < 200
+
+
+@pytest.mark.parametrize("hard", [False, True])
+def test_potential_matches_the_mie_near_field(hard):
+    """The scattered field at points off the unit sphere (Sec. 5.3's potential evaluation) from the
+    oracle's LU density, against the Mie series near field (r = 1.5 .. 5); the error shrinks under
+    refinement like the far field's."""
+    rng = np.random.default_rng(4)
+    P = rng.standard_normal((12, 3))
+    P *= (rng.uniform(1.5, 5.0, 12) / np.linalg.norm(P, axis=1))[:, None]
+    ref = mie.mie_scattered_field(1.0, P, D, hard)
+    errs = []
+    for m in (1, 2):
+        sp, Amat, b, x = _solve(m, 1, 1.0, hard)
+        u = farfield.potential(sp, 1.0, x, P, hard)
+        errs.append(np.abs(u - ref).max() / np.abs(ref).max())
+    assert errs[1] < 2e-3 and errs[1] < errs[0] / 4

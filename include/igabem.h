@@ -221,6 +221,18 @@ int igabem_solve_sources(igabem_problem *prob, int n_rhs, const double *z, void 
 /* Right-hand sides of igabem_solve_sources: b = [N][n_rhs] complex. */
 int igabem_rhs_sources(igabem_problem *prob, int n_rhs, const double *z, void *b);
 
+/* The scattered field at n_pts points outside the scatterer (pts [n_pts][3], host or device) for n_rhs
+   <= 8 densities ([N][n_rhs] complex, host or device): sound-soft u_s = -SL(t), sound-hard u_s = DL(u)
+   (the representations of Sec. 2), summed over the regular Gauss rule of every element, by an
+   interpolation fast multipole method in physical space (Sec. 4.4, last part, and Sec. 5.3): an octree
+   over the sources and points (leaves of at most 64 Gauss points), min(cheb_q, 10)^3 Chebyshev nodes
+   per box, eta_adm and kappa_cap as for the surface tree, kernel samples generated on the fly (FP32 in
+   the mixed precisions, FP64 otherwise), the near field summed directly; no_fmm = 1 sums everything
+   directly.  u = [n_pts][n_rhs] complex (host or device).  Allocates its octree and expansions for the
+   duration of the call. */
+int igabem_potential(igabem_problem *prob, int n_rhs, const void *density, int n_pts, const double *pts,
+                     void *u);
+
 /* Far-field pattern (Sec. 1) of n_rhs densities at n_dir unit directions xhat ([n_dir][3], host):
      sound-soft u_inf(x^) = -1/(4 pi) int exp(-i kappa x^.y) t(y) dsigma_y,
      sound-hard u_inf(x^) = -i kappa/(4 pi) int (x^.n_y) exp(-i kappa x^.y) u(y) dsigma_y,

@@ -101,6 +101,7 @@ SIGNATURES = {
     "igabem_farfield_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_wait_selftest": (c_int, [c_void_p, ctypes.c_double]),
     "igabem_measure_peaks": (c_int, [c_void_p, ctypes.POINTER(igabem_peaks)]),
+    "igabem_potential": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "igabem_autotune": (c_int, [c_void_p, ctypes.POINTER(igabem_options), c_int, c_int, ctypes.c_char_p,
                                 ctypes.POINTER(igabem_options), ctypes.POINTER(igabem_tune_info)]),
     "igabem_solve_sources": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(igabem_solve_info)]),
@@ -270,6 +271,18 @@ def igabem_rhs_sources(prob, z, n_dofs: int, out=None):
     R = zz.shape[0]
     out = np.empty((n_dofs, R), np.complex128) if out is None else out
     _check(lib().igabem_rhs_sources(prob, R, _ptr(zz), _ptr(out)))
+    return out
+
+
+def igabem_potential(prob, density, points, out=None):
+    """Scattered field [n_pts][R] at points [n_pts][3] (numpy or torch, host or CUDA)."""
+    R = _ncols(density)
+    pts = points if _is_torch(points) else _host(points, np.float64).reshape(-1, 3)
+    n = int(pts.shape[0])
+    if out is None:
+        out = np.empty((n, R), np.complex128)
+    dens = density if _is_torch(density) else _host(density, np.complex128)
+    _check(lib().igabem_potential(prob, R, _ptr(dens), n, _ptr(pts), _ptr(out)))
     return out
 
 

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libigabem.so")
-SOURCES = ["capi.cpp", "host_setup.cpp", "k_setup.cu", "k_apply.cu", "k_solver.cu", "k_m2l.cu", "k_m2l_tc.cu", "k_leaf.cu", "profile.cpp", "server.cpp", "k_noalloc.cu", "k_peaks.cu", "autotune.cpp"]
+SOURCES = ["capi.cpp", "host_setup.cpp", "k_setup.cu", "k_apply.cu", "k_solver.cu", "k_m2l.cu", "k_m2l_tc.cu", "k_leaf.cu", "profile.cpp", "server.cpp", "k_noalloc.cu", "k_peaks.cu", "autotune.cpp", "k_potential.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CSRC, "-I" + INCLUDE]
 

@@ -477,6 +477,16 @@ void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options
   IGA_CUDA(cudaGetLastError());
 }
 
+void launch_density(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, const double *dens,
+                    double *rho, cudaStream_t st) {
+  RhsArgs A = rhs_args(d, S, o, R);
+  const long npts = (long)S.E * S.ng * S.ng;
+  k_density<<<grid_for(npts * R), 256, 0, st>>>(A, d.x2g, reinterpret_cast<const double2 *>(dens), S.E,
+                                                 reinterpret_cast<double2 *>(rho));
+  note_launch();
+  IGA_CUDA(cudaGetLastError());
+}
+
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      const double *dens, int n_dir, const double *xhat_dev, double *uinf, double *scratch,
                      cudaStream_t st) {

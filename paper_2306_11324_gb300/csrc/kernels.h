@@ -52,6 +52,9 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
 // kind 0: plane waves with directions dirs; kind 1: point sources at the points dirs
 void launch_rhs(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                 const double *dirs_dev, double *b, cudaStream_t st, int kind = 0);
+// rho[e][q][r] = w_q h^2 sum_k psi_k(q) dens[.][r]: the weighted density at the Gauss points (complex)
+void launch_density(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R, const double *dens,
+                    double *rho, cudaStream_t st);
 // scratch: device space for E ng^2 R complex values (the weighted density at the Gauss points)
 void launch_farfield(const DeviceProblem &d, const HostSetup &S, const igabem_options &o, int R,
                      const double *dens, int n_dir, const double *xhat_dev, double *uinf, double *scratch,

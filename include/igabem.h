@@ -123,7 +123,8 @@ typedef struct {
   size_t device_bytes;       /* device memory held by the problem */
   double setup_ms;           /* wall time of igabem_problem_create */
   double host_setup_ms;      /* of which host-side set-up (tree, lists, tables) */
-  long n_singular_points;    /* 4-D quadrature points of the touching pairs (Sec. 4.3 rules) */
+  long n_singular_points;    /* 4-D quadrature points evaluated for the touching pairs (Sec. 4.3 rules;
+                                identical pairs take half of their rule, each point in both orientations) */
   int n_levels;              /* tree levels 0 .. m - b (at most 24 reported below) */
   int level_q[24];           /* interpolation points per direction on each level */
   long level_far[24];        /* admissible pairs on each level */

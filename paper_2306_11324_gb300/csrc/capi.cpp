@@ -543,7 +543,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   I.n_singular_points = 0;
   for (size_t i = 0; i + 6 < S.sing.size(); i += 7) {
     const int kind = S.sing[i + 2];
-    I.n_singular_points += kind == 0 ? (long)S.r_id.w.size() : (kind == 2 ? (long)S.r_edge.w.size() : (long)S.r_vert.w.size());
+    I.n_singular_points += kind == 0 ? (long)S.r_id.w.size() / 2 : (kind == 2 ? (long)S.r_edge.w.size() : (long)S.r_vert.w.size());
   }
   I.n_levels = S.L + 1;
   for (int l = 0; l <= S.L && l < 24; ++l) {

@@ -193,6 +193,9 @@ static std::vector<double> bernstein_collocation_inverse(int n) {
 // Regularising transforms for touching element pairs (same derivation as documented with the
 // device quadrature): identical 8 regions, common edge 6, common vertex 4; ns points per variable.
 
+// The regions are ordered with the sign s1 outermost: region (s1 = 1, 1 - s2, tri) is region (0, s2, tri)
+// with x and y exchanged, so the first half of the points (s1 = 0) and both orientations of each give
+// the whole rule (the singular kernel uses that).
 static void rule_identical(const std::vector<double> &gx, const std::vector<double> &gw, Rule4 &R) {
   int n = (int)gx.size();
   for (int s1 = 0; s1 < 2; ++s1)
@@ -769,7 +772,9 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   for (int i = 0; i < npt; ++i) {
     const int *t = &S.touch[5 * i];
     if (t[2] == 0) {
-      S.sing.insert(S.sing.end(), {t[0], t[1], 0, 0, 0, S.touch_blk[i], -1});
+      // identical pair: the rule's second half is the first with x and y exchanged, so its first half
+      // gives the block from both orientations of every point (block of (f, e) = the same block)
+      S.sing.insert(S.sing.end(), {t[0], t[1], 0, 0, 0, S.touch_blk[i], S.touch_blk[i]});
     } else if (t[0] < t[1]) {
       int back = S.touch_blk[touch_index(t[1], t[0])];
       S.sing.insert(S.sing.end(), {t[0], t[1], t[2], t[3], t[4], S.touch_blk[i], back});

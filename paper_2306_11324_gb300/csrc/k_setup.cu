@@ -495,6 +495,9 @@ __global__ void k_near_singular(SingArgs S) {
   const bool both = blk_fe >= 0;
   const int ri = kind == 0 ? 0 : (kind == 2 ? 1 : 2);
   const int npt = S.rule_n[ri];
+  // identical pairs: the first half of the rule with both orientations of every point (the second
+  // half is the first with x and y exchanged), accumulated into the same block
+  const int nuse = kind == 0 ? npt / 2 : npt;
   const double *R = S.rule[ri];
   const int n1 = A.n1;
   const int ixe = (e / n1) % n1, iye = e % n1, ixf = (f / n1) % n1, iyf = f % n1;
@@ -506,8 +509,8 @@ __global__ void k_near_singular(SingArgs S) {
   for (int i = threadIdx.x; i < 4 * (pe1 + 1) * (pe2 + 1); i += blockDim.x) net_e[i] = A.ebez[A.eoff[e] + i];
   for (int i = threadIdx.x; i < 4 * (pf1 + 1) * (pf2 + 1); i += blockDim.x) net_f[i] = A.ebez[A.eoff[f] + i];
   __syncthreads();
-  for (int c0 = 0; c0 < npt; c0 += SING_CHUNK) {
-    const int cn = min(SING_CHUNK, npt - c0);
+  for (int c0 = 0; c0 < nuse; c0 += SING_CHUNK) {
+    const int cn = min(SING_CHUNK, nuse - c0);
     for (int t = threadIdx.x; t < cn; t += blockDim.x) {
       const int ip = c0 + t;
       double ue, ve, uf, vf;

@@ -67,7 +67,7 @@ __global__ void k_rhs(RhsArgs A, double2 *__restrict__ b) {
                 const double2 u = cmk(c / (4.0 * IGA_PI * r), s / (4.0 * IGA_PI * r));
                 const double vn = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / (r * r);
                 const double2 gn = cscale(cmul(u, cmk(-1.0, A.kappa * r)), vn);   // grad u_inc . n~
-                const double2 ie_gn = cmk(A.eta * gn.y, -A.eta * gn.x);         // i eta grad u . n~
+                const double2 ie_gn = cmk(-A.eta * gn.y, A.eta * gn.x);         // i eta grad u . n~
                 const double2 ie_u = cmk(-A.eta * u.y * A.gpa[iq], A.eta * u.x * A.gpa[iq]);  // i eta a u
                 f = A.hard ? csub(cscale(u, A.gpa[iq]), ie_gn) : csub(gn, ie_u);
               }

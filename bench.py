@@ -337,6 +337,18 @@ def serving_requests(n, seed=0):
     return out
 
 
+def _report_done(B, reqs, handles, reported, t0):
+    """Progress of the serving stream on stderr: one line per finished request."""
+    for i, h in enumerate(handles):
+        if i not in reported and B.igabem_poll(h):
+            reported.add(i)
+            _, info, rc = B.igabem_result(h, raise_errors=False)
+            r = reqs[i]
+            print(f"[{time.perf_counter() - t0:8.1f} s] request {i}: m={r['m']} kappa={r['kappa']:.1f} "
+                  f"bc={r['bc']} R={len(r['dirs'])} rc={rc} its={info['iterations']} "
+                  f"solve {info['solve_ms']:.0f} ms", file=sys.stderr, flush=True)
+
+
 def run_serving(args):
     """Continuous-batching serving run: Poisson arrivals into the library's server."""
     import torch
@@ -368,6 +380,7 @@ def run_serving(args):
     for r in reqs:
         geom(r["geom_seed"])
     srv = B.igabem_server_create(ctx, 0, args.slots)
+    reported = set()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
         handles, t_next = [], t0
@@ -376,8 +389,10 @@ def run_serving(args):
             while time.perf_counter() < t_next:
                 time.sleep(min(0.005, max(0.0, t_next - time.perf_counter())))
             handles.append(B.igabem_submit(srv, geom(r["geom_seed"]), opt(r), r["dirs"], xhat))
-        for h in handles:
-            B.igabem_wait(h, -1.0)
+            _report_done(B, reqs, handles, reported, t0)
+        while len(reported) < len(handles):
+            time.sleep(0.05)
+            _report_done(B, reqs, handles, reported, t0)
         wall = time.perf_counter() - t0
     status = [B.igabem_result(h, raise_errors=False)[2] for h in handles]
     st = B.igabem_server_get_stats(srv)

@@ -129,7 +129,7 @@ extern "C" int igabem_autotune(igabem_geom *geom, const igabem_options *opt, int
           }
           problem_release(P);
           if (rc != IGABEM_OK) continue;
-          const double score = setup_ms + nmv * ms;
+          const double score = setup_ms + nmv * (double)ms;
           ++ti.candidates;
           if (score < best) {
             best = score;

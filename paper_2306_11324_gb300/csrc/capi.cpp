@@ -350,6 +350,7 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     total += 13 * ((gst * sizeof(double) + 255) & ~size_t(255));
     total += bytes_of(S.phi1) + bytes_of(S.dphi1) + bytes_of(S.ext1) + bytes_of(S.gx) + bytes_of(S.gw);
     total += 3 * 256 + 5 * nrule * sizeof(double);
+    for (const Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) total += (r->share.size() + 255) & ~size_t(255);
     total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.sing) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) +
              bytes_of(S.g2x_idx);
     total += bytes_of(S.near_ptr) + bytes_of(S.near_src) + bytes_of(dummy_tgt);
@@ -436,6 +437,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   for (int k = 0; k < 3; ++k) {
     d.rule[k] = upload(A, rules[k], st);
     d.rule_n[k] = (int)R4[k]->w.size();
+    d.share[k] = upload(A, R4[k]->share, st);
   }
   d.touch = upload(A, S.touch, st);
   d.touch_blk = upload(A, S.touch_blk, st);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <map>
 #include <numeric>
 #include <string>
 #include <unordered_map>
@@ -252,6 +253,49 @@ static void rule_vertex(const std::vector<double> &gx, const std::vector<double>
           }
 }
 
+// Sharing tables of a rule (Rule4::share).  In the tensor rules above each coordinate of a point
+// depends on three of the four Gauss indices at most, so inside a chunk of consecutive points (whole
+// groups of ns^2 points with the first two indices fixed) a coordinate takes few distinct values and
+// many points repeat one element's point: the singular kernel evaluates the geometry once per distinct
+// value / point of a chunk.
+static void share_tables(Rule4 &R, int ch, int &nv_max, int &nd_max) {
+  const int n = (int)R.w.size(), nch = (n + ch - 1) / ch, hdr = 6 + 6 * ch;
+  R.share.assign((size_t)nch * hdr + (size_t)n * 6, 0);
+  unsigned char *PI = R.share.data() + (size_t)nch * hdr;
+  for (int c = 0; c < nch; ++c) {
+    unsigned char *H = R.share.data() + (size_t)c * hdr;
+    const int p0 = c * ch, cn = std::min(ch, n - p0);
+    for (int side = 0; side < 2; ++side) {
+      const std::vector<double> &a = side ? R.y1 : R.x1, &b = side ? R.y2 : R.x2;
+      std::map<double, int> m1, m2;
+      std::map<std::pair<double, double>, int> md;
+      auto put = [&](auto &m, const auto &key, int list, int t) {
+        auto it = m.find(key);
+        int id;
+        if (it == m.end()) {
+          id = (int)m.size();
+          m.emplace(key, id);
+          H[6 + list * ch + id] = (unsigned char)t;
+        } else {
+          id = it->second;
+        }
+        PI[(size_t)(p0 + t) * 6 + list] = (unsigned char)id;
+      };
+      for (int t = 0; t < cn; ++t) {
+        const int p = p0 + t;
+        put(m1, a[p], 3 * side, t);
+        put(m2, b[p], 3 * side + 1, t);
+        put(md, std::make_pair(a[p], b[p]), 3 * side + 2, t);
+      }
+      H[3 * side] = (unsigned char)m1.size();
+      H[3 * side + 1] = (unsigned char)m2.size();
+      H[3 * side + 2] = (unsigned char)md.size();
+      nv_max = std::max(nv_max, (int)std::max(m1.size(), m2.size()));
+      nd_max = std::max(nd_max, (int)md.size());
+    }
+  }
+}
+
 // The eight symmetries of the unit square, in the order identity, rotations by 90/180/270
 // degrees, then these composed with the diagonal reflection; applied to corner coordinates.
 static void d4(int k, int u, int v, int &ou, int &ov) {
@@ -418,6 +462,9 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   rule_identical(sx, sw, S.r_id);
   rule_edge(sx, sw, S.r_edge);
   rule_vertex(sx, sw, S.r_vert);
+  S.sing_ch = S.ns * S.ns <= 128 ? S.ns * S.ns * (128 / (S.ns * S.ns)) : 128;
+  S.sing_nv = S.sing_nd = 0;
+  for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, S.sing_ch, S.sing_nv, S.sing_nd);
 
   // --- ansatz space: knot vector Xi_{p,m}, tables per element column ---
   std::vector<double> kn;

@@ -73,6 +73,10 @@ struct Arena {
 
 struct Rule4 {  // a rule on [0,1]^4 for touching element pairs, canonical position
   std::vector<double> x1, x2, y1, y2, w;
+  // Sharing tables over chunks of sing_ch consecutive points: per chunk 6 counts and 6 lists of
+  // sing_ch offsets (the first point of each distinct x1, x2, (x1, x2), y1, y2, (y1, y2) in the
+  // chunk), then per point its 6 indices into those lists.
+  std::vector<unsigned char> share;
 };
 
 struct TreeLevel {
@@ -102,6 +106,7 @@ struct HostSetup {
   std::vector<double> corners; // 4 corners x 3 per element, local (0,0),(1,0),(0,1),(1,1)
   // quadrature
   int ng = 4, ns = 5;
+  int sing_ch = 128, sing_nv = 0, sing_nd = 0;  // singular chunk; most distinct coordinates / points in one
   std::vector<double> gx, gw;          // Gauss rule on [0,1] (ng points)
   Rule4 r_id, r_edge, r_vert;
   // ansatz basis: per element column ix, Gauss point q, function a: value and d/ds
@@ -196,6 +201,7 @@ struct DeviceProblem {
   double *gpx, *gpn, *gpa, *gfs, *gft;    // Gauss-point geometry: [3][E*ng*ng] or [E*ng*ng]
   double *phi1, *dphi1, *ext1, *gx, *gw;
   double *rule[3];                          // singular rules (5 arrays each, SoA)
+  unsigned char *share[3];                  // their sharing tables (Rule4::share)
   int rule_n[3];
   double *corners;
   int *touch, *touch_blk, *sing;

@@ -400,7 +400,20 @@ struct SingArgs {
   const int *sing;        // 7 ints per unordered touching pair
   const double *rule[3];  // per kind: x1, x2, y1, y2, w arrays of n points, concatenated
   int rule_n[3];
+  const unsigned char *share[3];  // per kind: sharing tables over chunks of ch points
+  int ch, nv, nd, pg1;            // chunk; most distinct coordinates / points of a chunk; max degree + 1
 };
+
+// shared-memory doubles of k_near_singular: the per-point union (w k psi, curls; aliased by the column
+// partials of the geometry), the distinct points' geometry, the two element nets
+__host__ __device__ inline size_t sing_union_doubles(int ch, int nloc, bool hard, int nv, int pg1) {
+  const size_t pts = (size_t)ch * (2 + 5 * nloc + (hard ? 6 * nloc : 0));
+  const size_t col = (size_t)2 * nv * pg1 * 8;
+  return pts > col ? pts : col;
+}
+__host__ __device__ inline size_t sing_smem_doubles(int ch, int nloc, bool hard, int nv, int nd, int pg1) {
+  return sing_union_doubles(ch, nloc, hard, nv, pg1) + (size_t)2 * nd * 13 + 8 * 49;
+}
 
 // values of the nloc local functions at local point (u, v) of element column (ix, iy) (Bernstein
 // extraction) into val; with curl != nullptr also c_k = d_s psi_k d_t F - d_t psi_k d_s F
@@ -435,7 +448,6 @@ __device__ inline void basis_curl_at(const NearArgs &A, int ix, int iy, double u
     }
 }
 
-constexpr int SING_CHUNK = 128;  // one point per thread
 constexpr int SING_MAXACC = 19;  // (p+1)^4 / 128 rounded up for p <= 6
 
 // The nloc local functions at local point (u, v) of element column (ix, iy), each times the complex
@@ -483,13 +495,17 @@ template <int NSLOT>
 __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;
   extern __shared__ double smd[];
-  const int nloc = A.nloc, p1 = A.p + 1;
-  // shared: Ax[C][nloc], Bx[C][nloc] (complex: w k(x,y) psi_k(x) and w k(y,x) psi_k(x)), gc[C] (complex),
-  // phy[C][nloc], and for sound-hard cx[C][nloc][3], cy[C][nloc][3]
-  double2 *Ax = reinterpret_cast<double2 *>(smd), *Bx = Ax + SING_CHUNK * nloc, *gc = Bx + SING_CHUNK * nloc;
-  double *phy = reinterpret_cast<double *>(gc + SING_CHUNK);
-  double *cxs = phy + SING_CHUNK * nloc, *cys = cxs + (A.hard ? 3 * SING_CHUNK * nloc : 0);
-  double *net_e = cys + (A.hard ? 3 * SING_CHUNK * nloc : 0), *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
+  const int nloc = A.nloc, p1 = A.p + 1, ch = S.ch;
+  // shared: Ax[ch][nloc], Bx[ch][nloc] (complex: w k(x,y) psi_k(x) and w k(y,x) psi_k(x)), gc[ch] (complex),
+  // phy[ch][nloc], and for sound-hard cx[ch][nloc][3], cy[ch][nloc][3]; aliased by the column partials
+  // colp[2][nv][pg1][8] of the element geometries; then geo[2][nd][13] (x, d_s x, d_t x, n, |n| of the
+  // chunk's distinct points) and the two element nets
+  double2 *Ax = reinterpret_cast<double2 *>(smd), *Bx = Ax + ch * nloc, *gc = Bx + ch * nloc;
+  double *phy = reinterpret_cast<double *>(gc + ch);
+  double *cxs = phy + ch * nloc, *cys = cxs + (A.hard ? 3 * ch * nloc : 0);
+  double *colp = smd;
+  double *geo = smd + sing_union_doubles(ch, nloc, A.hard, S.nv, S.pg1);
+  double *net_e = geo + 2 * S.nd * 13, *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
   const int *W = S.sing + 7 * blockIdx.x;
   const int e = W[0], f = W[1], kind = W[2], te = W[3], tf = W[4], blk_ef = W[5], blk_fe = W[6];
   const bool both = blk_fe >= 0;
@@ -499,6 +515,9 @@ __global__ void k_near_singular(SingArgs S) {
   // half is the first with x and y exchanged), accumulated into the same block
   const int nuse = kind == 0 ? npt / 2 : npt;
   const double *R = S.rule[ri];
+  const unsigned char *SH = S.share[ri];
+  const int hdr = 6 + 6 * ch;
+  const unsigned char *PI = SH + (size_t)((npt + ch - 1) / ch) * hdr;
   const int n1 = A.n1;
   const int ixe = (e / n1) % n1, iye = e % n1, ixf = (f / n1) % n1, iyf = f % n1;
   const double h4 = A.h * A.h * A.h * A.h;
@@ -508,25 +527,106 @@ __global__ void k_near_singular(SingArgs S) {
   const int pe1 = A.edeg[2 * e], pe2 = A.edeg[2 * e + 1], pf1 = A.edeg[2 * f], pf2 = A.edeg[2 * f + 1];
   for (int i = threadIdx.x; i < 4 * (pe1 + 1) * (pe2 + 1); i += blockDim.x) net_e[i] = A.ebez[A.eoff[e] + i];
   for (int i = threadIdx.x; i < 4 * (pf1 + 1) * (pf2 + 1); i += blockDim.x) net_f[i] = A.ebez[A.eoff[f] + i];
+  // the rule coordinate (0: first, 1: second) that becomes an element's second local coordinate under
+  // its square symmetry (rotations by 90 / 270 degrees and the diagonal reflection exchange them)
+  const int vse = ((te & 1) != (te >= 4)) ? 0 : 1, vsf = ((tf & 1) != (tf >= 4)) ? 0 : 1;
   __syncthreads();
-  for (int c0 = 0; c0 < nuse; c0 += SING_CHUNK) {
-    const int cn = min(SING_CHUNK, nuse - c0);
+  for (int c0 = 0; c0 < nuse; c0 += ch) {
+    const int cn = min(ch, nuse - c0);
+    const unsigned char *H = SH + (size_t)(c0 / ch) * hdr;
+    // geometry, step 1: for each distinct second local coordinate v of the chunk and each row i of the
+    // net, the row contracted with the Bernstein polynomials of v and their derivatives
+    {
+      const int nve = H[vse], nvf = H[3 + vsf], re = pe1 + 1, rf = pf1 + 1;
+      for (int w = threadIdx.x; w < nve * re + nvf * rf; w += blockDim.x) {
+        const bool sf = w >= nve * re;
+        const int ww = sf ? w - nve * re : w, rr = sf ? rf : re;
+        const int k = ww / rr, i = ww % rr;
+        const int ip = c0 + H[6 + (sf ? 3 + vsf : vse) * ch + k];
+        double u, v;
+        if (sf) d4_apply(tf, R[2 * npt + ip], R[3 * npt + ip], u, v);
+        else d4_apply(te, R[ip], R[npt + ip], u, v);
+        const int q2 = sf ? pf2 : pe2;
+        double B2[8], dB2[8];
+        bernstein_all(q2, v, B2, dB2);
+        const double *c = (sf ? net_f : net_e) + i * (q2 + 1) * 4;
+        double r[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0};
+        for (int j = 0; j <= q2; ++j) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            r[kk] += B2[j] * c[4 * j + kk];
+            rv[kk] += dB2[j] * c[4 * j + kk];
+          }
+        }
+        double *o = colp + ((size_t)((sf ? S.nv : 0) + k) * S.pg1 + i) * 8;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          o[kk] = r[kk];
+          o[4 + kk] = rv[kk];
+        }
+      }
+    }
+    __syncthreads();
+    // geometry, step 2: each distinct point of the chunk (x, its tangents d_s x, d_t x, the normal
+    // n = d_s x ^ d_t x and |n|) from the column partials of its second coordinate
+    {
+      const int nde = H[2], ndf = H[5];
+      for (int w = threadIdx.x; w < nde + ndf; w += blockDim.x) {
+        const bool sf = w >= nde;
+        const int k = sf ? w - nde : w;
+        const int ip = c0 + H[6 + (sf ? 5 : 2) * ch + k];
+        double u, v;
+        if (sf) d4_apply(tf, R[2 * npt + ip], R[3 * npt + ip], u, v);
+        else d4_apply(te, R[ip], R[npt + ip], u, v);
+        const int kv = PI[(size_t)ip * 6 + (sf ? 3 + vsf : vse)];
+        const int q1 = sf ? pf1 : pe1;
+        double B1[8], dB1[8];
+        bernstein_all(q1, u, B1, dB1);
+        const double *cp = colp + (size_t)((sf ? S.nv : 0) + kv) * S.pg1 * 8;
+        double h[4] = {0, 0, 0, 0}, hu[4] = {0, 0, 0, 0}, hv[4] = {0, 0, 0, 0};
+        for (int i = 0; i <= q1; ++i) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            h[kk] += B1[i] * cp[i * 8 + kk];
+            hu[kk] += dB1[i] * cp[i * 8 + kk];
+            hv[kk] += B1[i] * cp[i * 8 + 4 + kk];
+          }
+        }
+        const double iw = 1.0 / h[3];
+        double *g = geo + (size_t)((sf ? S.nd : 0) + k) * 13;
+        double fs[3], ft[3], nn[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          const double F = h[kk] * iw;
+          g[kk] = F;
+          fs[kk] = (hu[kk] - F * hu[3]) * iw * n1;
+          ft[kk] = (hv[kk] - F * hv[3]) * iw * n1;
+          g[3 + kk] = fs[kk];
+          g[6 + kk] = ft[kk];
+        }
+        cross3(fs, ft, nn);
+        g[9] = nn[0];
+        g[10] = nn[1];
+        g[11] = nn[2];
+        g[12] = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      }
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < cn; t += blockDim.x) {
       const int ip = c0 + t;
       double ue, ve, uf, vf;
       d4_apply(te, R[ip], R[npt + ip], ue, ve);
       d4_apply(tf, R[2 * npt + ip], R[3 * npt + ip], uf, vf);
       const double w = R[4 * npt + ip] * h4;
-      double X[3], Xu[3], Xv[3], Y[3], Yu[3], Yv[3], fs[3], ft[3], gs[3], gt[3], nx[3], ny[3];
-      bez_eval_sep(net_e, pe1, pe2, ue, ve, X, Xu, Xv);
-      bez_eval_sep(net_f, pf1, pf2, uf, vf, Y, Yu, Yv);
+      const double *ge = geo + (size_t)PI[(size_t)ip * 6 + 2] * 13;
+      const double *gf = geo + (size_t)(S.nd + PI[(size_t)ip * 6 + 5]) * 13;
+      double X[3], Y[3], fs[3], ft[3], gs[3], gt[3], nx[3], ny[3];
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
-        fs[k] = Xu[k] * n1; ft[k] = Xv[k] * n1; gs[k] = Yu[k] * n1; gt[k] = Yv[k] * n1;
+        X[k] = ge[k]; fs[k] = ge[3 + k]; ft[k] = ge[6 + k]; nx[k] = ge[9 + k];
+        Y[k] = gf[k]; gs[k] = gf[3 + k]; gt[k] = gf[6 + k]; ny[k] = gf[9 + k];
       }
-      cross3(fs, ft, nx);
-      cross3(gs, gt, ny);
-      const double ax = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
-      const double ay = sqrt(ny[0] * ny[0] + ny[1] * ny[1] + ny[2] * ny[2]);
+      const double ax = ge[12], ay = gf[12];
       PairKernel pk;
       double2 kyx;
       cfie_kernel_both(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay, pk, kyx);
@@ -701,8 +801,15 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   }
   const int nsing = (int)S.sing.size() / 7;
   if (S.nloc * S.nloc > SING_MAXACC * 128) fail(IGABEM_EINVAL, "degree_p too large for the singular kernel");
-  const size_t smem =
-      ((size_t)SING_CHUNK * (2 + 5 * S.nloc + (S.hard ? 6 * S.nloc : 0)) + 8 * 49) * sizeof(double);
+  int pg1 = 1;
+  for (size_t i = 0; i < S.edeg.size(); ++i) pg1 = std::max(pg1, S.edeg[i] + 1);
+  SA.ch = S.sing_ch;
+  SA.nv = S.sing_nv;
+  SA.nd = S.sing_nd;
+  SA.pg1 = pg1;
+  for (int k = 0; k < 3; ++k) SA.share[k] = d.share[k];
+  const size_t smem = sing_smem_doubles(S.sing_ch, S.nloc, S.hard, S.sing_nv, S.sing_nd, pg1) * sizeof(double);
+  if (smem > 227 * 1024) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
   const int nslot = (S.nloc * S.nloc + 127) / 128;
   auto go = [&](auto kfn) {
     IGA_CUDA(set_max_dynamic_smem(kfn, smem));

@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the isogeometric CFIE solver on one GB300 (or N replicas of it under torchrun).
 
-Default workload (a step is one scattering request through the whole hot path: problem set-up with
-geometry tables, cluster tree and near-field Galerkin quadrature, right-hand side, GMRES with fast
-multipole matrix-vector products, far-field pattern at 100 Fibonacci directions): sound-soft unit
-sphere as 6 exact rational patches with 32 x 32 elements each (6144 elements), B-splines of degree 2
-(6936 unknowns), kappa = 8, eta = kappa, plane wave d = (0,0,1), 7 x 7 Chebyshev points per cluster,
-admissibility eta_adm = 0.5, GMRES(30) to 1e-6; timed in the mixed precision (FP32 far field, block
-preconditioner), the FP64 form timed beside it and the far fields of the two compared.
+Default workload, the large single scatterer: seeded deformed sphere (6 degree-4 patches with 4 knot
+spans per direction, control points displaced radially with amplitude 0.15), 256 x 256 elements per
+patch (393216 elements), B-splines of degree 2 (399384 unknowns), sound-soft, eta = kappa, a frequency
+sweep of 16 kappa in [50, 60] with 8 incident directions each and the far field at 2048 directions.
+A step is one kappa of the sweep through the whole hot path: problem set-up (geometry tables, cluster
+tree with level-adaptive Chebyshev orders 7 .. 12, stored FP32 coupling blocks, near-field Galerkin
+quadrature), right-hand sides, GMRES(30) with the block preconditioner to 1e-5 for the 8 directions at
+once, far field; solves/s counts every direction.  Timed in the mixed precision; the product is
+compared with the plain FP64 operator's on a seeded vector beside the steps.
 
+--workload sphere_soft_6x32x32_p2_k8: sound-soft unit sphere, 32 x 32 elements per patch (6936
+unknowns), kappa = 8, one plane wave; a step is one request (set-up, GMRES(30) to 1e-6, far field at 100
+directions), the FP64 form timed beside it and the far fields of the two compared.
 --workload deformed_hard_6x64x64_p2_k20_64dirs: sound-hard deformed sphere, 24576 elements, kappa = 20,
 64 incident directions; a step is one operator application to the 64 columns (tensor-core M2L by
 default), one full solve timed beside the steps, the product checked against the FP64 operator.
 --workload serving_stream: Poisson arrivals of mixed requests into the library's server.
+--workload torus_convergence: observed convergence orders on the exact torus.
 
 Prints one JSON line (see the keys below).  --impl reference times the CPU oracle instead.
 """
@@ -68,27 +74,42 @@ WORKLOADS = {
                                                     m2l_stored={"fp64": 0, "mixed": 1, "tc": 1},
                                                     kappas=[50.0 + 10.0 * i / 15 for i in range(16)],
                                                     solve_max_iter=2000),
+    # the same step at 32 x 32 elements per patch (6144 elements), kappa in [10, 12]: a small case of the
+    # large scatterer's kernels (profiling, quick checks)
+    "deformed_soft_6x32x32_p2_k10-12_8dirs": dict(geometry="deformed", level_m=5, degree_p=2, kappa=10.0, bc=0,
+                                                  cheb_q=7, q_max=12, eta_adm=0.5, kappa_cap=6.0,
+                                                  leaf_offset={"fp64": 2, "mixed": 2, "tc": 2},
+                                                  tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=2048,
+                                                  n_rhs=8, restart=30, precond={"fp64": 1, "mixed": 1, "tc": 1},
+                                                  precision="mixed", step="sweep", eta="kappa",
+                                                  m2l_stored={"fp64": 0, "mixed": 1, "tc": 1},
+                                                  kappas=[10.0 + 2.0 * i / 15 for i in range(16)],
+                                                  solve_max_iter=2000),
 }
-DEFAULT = "sphere_soft_6x32x32_p2_k8"
+DEFAULT = "deformed_soft_6x256x256_p2_k50-60_8dirs"
 PRECISIONS = {}                              # name -> igabem_precision (filled once the binding is loaded)
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic: soft 40 flops, hard 52 per pair of samples
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 
 
-def singular_flops_per_point(p, hard, pg=4):
-    """FP64 operations of one 4-D quadrature point of a touching pair (the model behind the roofline of
-    k_near_singular): both elements' rational Bezier geometry of degree pg (homogeneous rows with their
-    v-derivatives, then the columns with value, d/du, d/dv; normal and Jacobian), the kernel (distance,
-    sincos, G, G'/r and the weights), both elements' (p+1)^2 B-splines by Bernstein extraction (and their
-    surface curls for sound-hard), the kernel value times the test functions (w k psi_k, also for the
-    transposed block of a common-edge or common-vertex pair taken from the same points) and the
-    accumulation of the (p+1)^2 x (p+1)^2 blocks (one complex-by-real multiply-add per entry and block;
-    sound-hard adds the curl product G c_k . c_l)."""
+def singular_flops(info, p, hard, pg=4):
+    """FP64 operations of the touching pairs' quadrature (the model behind the roofline of
+    k_near_singular), from the counts the library reports.  Per element net contracted along its second
+    coordinate (once per distinct value in a chunk of the rule): the homogeneous rows of the rational
+    Bezier net of degree pg with their derivatives, 2 (pg+1)^2 4 2 flops.  Per distinct element point:
+    the columns with value, d/du, d/dv ((pg+1) 4 3 2), the rational quotient, normal and Jacobian (30).
+    Per 4-D point: the kernel (distance, sincos, G, G'/r and the weights, 60), both elements' (p+1)^2
+    B-splines by Bernstein extraction (and their surface curls for sound-hard), the kernel value times
+    the test functions (w k psi_k, also for the transposed block of a common-edge or common-vertex pair
+    taken from the same points) and the accumulation of the (p+1)^2 x (p+1)^2 blocks (one complex-by-real
+    multiply-add per entry and block; sound-hard adds the curl product G c_k . c_l)."""
     n = (p + 1) ** 2
-    geo = 2 * (2 * (pg + 1) ** 2 * 4 * 2 + (pg + 1) * 4 * 3 * 2 + 30)
+    per_column = 2 * (pg + 1) ** 2 * 4 * 2
+    per_geo_point = (pg + 1) * 4 * 3 * 2 + 30
     basis = 2 * (5 * n + (6 * n if hard else 0)) + 2 * 4 * n
     acc = n * n * (2 * 4 + (5 + 8 if hard else 0))
-    return geo + basis + 60 + acc
+    return (info["n_singular_geo_columns"] * per_column + info["n_singular_geo_points"] * per_geo_point
+            + info["n_singular_points"] * (basis + 60 + acc))
 
 
 def mie_soft_far_field(kappa, xhat, d=(0.0, 0.0, 1.0)):
@@ -409,13 +430,15 @@ def run_serving(args):
         return geoms[seed]
 
     def opt(r):
-        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload); the
-        # M2L coupling blocks stored in FP32 (set up once, read by every product: the many-iteration
+        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload);
+        # level-adaptive q (7 .. 12) under the kappa * diameter <= 6 cap, as in the large-scatterer
+        # workload (the cap alone leaves only the finest level admissible at kappa ~ 30); the M2L
+        # coupling blocks stored in FP32 (set up once, read by every product: the many-iteration
         # sound-hard solves gain most).  A request that has not reached the tolerance after max_iter
         # iterations is reported as failed.
         return B.igabem_default_options(level_m=r["m"], degree_p=2, kappa=r["kappa"],
                                         eta_cfie=1.0 / r["kappa"] if r["bc"] else r["kappa"],
-                                        bc=r["bc"], cheb_q=7, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
+                                        bc=r["bc"], cheb_q=7, q_max=12, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
                                         precision=B.MIXED_FP32, tol=1e-5, max_iter=args.max_iter,
                                         gmres_restart=300 if r["bc"] else 30, precond=0 if r["bc"] else 1,
                                         m2l_stored=1)
@@ -446,7 +469,7 @@ def run_serving(args):
            "warmup": 0, "ms_per_step": 1e3 * wall / max(1, len(reqs)), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded deformed spheres, Poisson arrivals)",
            "config": {"workload": "serving_stream", "requests": len(reqs), "arrival_rate_per_s": args.rate,
-                      "slots": args.slots, "precision": "mixed, stored M2L blocks", "tol": 1e-5,
+                      "slots": args.slots, "precision": "mixed, stored M2L blocks", "cheb_q": "7 .. 12 by level", "tol": 1e-5,
                       "max_iter": args.max_iter},
            "solve_latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
            "completed": st["completed"], "failed": st["failed"], "peak_active": st["peak_active"],
@@ -731,7 +754,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
     hard = bool(wl["bc"])
     sing = prof_tot.get("setup_singular", {"ms": 0.0, "calls": 0})
     sing_ms = sing["ms"] / max(1, sing["calls"])
-    sing_flops = info["n_singular_points"] * singular_flops_per_point(wl["degree_p"], hard)
+    sing_flops = singular_flops(info, wl["degree_p"], hard)
     sing_ach = sing_flops / (sing_ms / 1e3) / 1e12 if sing_ms > 0 else 0.0
     m2l_ms = mv_phases.get("m2l", 0.0)
     qs = info["level_q"]
@@ -747,6 +770,8 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                 "peak_source": "measured FP64 FMA rate (igabem_measure_peaks, this run; 2 flops per FMA)",
                 "algorithmic_flops_per_setup": sing_flops, "avg_ms_per_setup": sing_ms,
                 "singular_points": info["n_singular_points"],
+                "singular_geometry_points": info["n_singular_geo_points"],
+                "singular_geometry_columns": info["n_singular_geo_columns"],
                 "m2l": {"kernel": "k_m2l_rows<float> / k_m2l_gemm<float>", "achieved": m2l_ach, "unit": "TFLOP/s",
                         "peak": peaks["fp32_tflops"], "frac": m2l_ach / peaks["fp32_tflops"],
                         "xu_frac": (m2l_samples / (peaks["sincosf_gops"] * 1e9) + m2l_samples / (peaks["rsqrtf_gops"] * 1e9))
@@ -774,7 +799,8 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                       "l2": "working set far above L2 (and a 256 MB write before each step)"},
            "steps_detail": steps_rec,
            "solve_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-           "phase_ms_per_step": phases, "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
+           "phase_ms_per_step": phases, "setup_ms": info["setup_ms"], "host_setup_ms": info["host_setup_ms"],
+           "device_bytes": info["device_bytes"],
            "matvecs_per_s": R * 1e3 / mv_ms * world, "matvec_ms": mv_ms, "phase_ms_per_matvec": mv_phases,
            "matvec_rel_err_vs_fp64": err64, "fp64_matvec_ms": fp64_mv_ms,
            "fp64_matvecs_per_s": R * 1e3 / fp64_mv_ms if fp64_mv_ms else None,
@@ -953,7 +979,7 @@ def main():
     fp64 = args.precision == "fp64"
     sing = main_form["prof"].get("setup_singular", {"ms": 0.0, "calls": 0})
     sing_ms = sing["ms"] / max(1, sing["calls"])
-    sing_flops = info["n_singular_points"] * singular_flops_per_point(wl["degree_p"], hard)
+    sing_flops = singular_flops(info, wl["degree_p"], hard)
     sing_achieved = sing_flops / (sing_ms / 1e3) / 1e12 if sing_ms > 0 else 0.0
     m2l = main_form["prof"].get("m2l", {"ms": 0.0, "calls": 0})
     m2l_ms = m2l["ms"] / max(1, m2l["calls"])
@@ -963,6 +989,8 @@ def main():
                 "peak_source": "measured FP64 FMA rate (igabem_measure_peaks, this run; 2 flops per FMA)",
                 "algorithmic_flops_per_setup": sing_flops, "avg_ms_per_setup": sing_ms,
                 "singular_points": info["n_singular_points"],
+                "singular_geometry_points": info["n_singular_geo_points"],
+                "singular_geometry_columns": info["n_singular_geo_columns"],
                 "m2l": m2l_alu_roofline("k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>", far, Q, hard,
                                         len(dirs), m2l_ms, peaks, fp64)}
 

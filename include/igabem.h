@@ -128,6 +128,10 @@ typedef struct {
   int n_levels;              /* tree levels 0 .. m - b (at most 24 reported below) */
   int level_q[24];           /* interpolation points per direction on each level */
   long level_far[24];        /* admissible pairs on each level */
+  long n_singular_geo_points;  /* element points whose geometry the touching pairs evaluate (a point
+                                  repeated inside a chunk of the rule is evaluated once) */
+  long n_singular_geo_columns; /* element nets contracted along their second coordinate, once per
+                                  distinct value of it in a chunk */
 } igabem_info;
 
 typedef struct {

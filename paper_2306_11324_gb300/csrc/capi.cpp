@@ -543,9 +543,23 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   I.n_touching_pairs = (long)S.touch.size() / 5;
   I.n_far_pairs = S.n_far;
   I.n_singular_points = 0;
+  I.n_singular_geo_points = 0;
+  I.n_singular_geo_columns = 0;
+  // per rule, summed over the chunks a pair integrates: distinct x1, x2, x-points, y1, y2, y-points
+  long chunk_sum[3][6] = {};
+  for (int k = 0; k < 3; ++k) {
+    const int n = (int)R4[k]->w.size(), nuse = k == 0 ? n / 2 : n, ch = S.sing_ch;
+    for (int c0 = 0; c0 < nuse; c0 += ch)
+      for (int j = 0; j < 6; ++j) chunk_sum[k][j] += R4[k]->share[(size_t)(c0 / ch) * (6 + 6 * ch) + j];
+  }
   for (size_t i = 0; i + 6 < S.sing.size(); i += 7) {
-    const int kind = S.sing[i + 2];
-    I.n_singular_points += kind == 0 ? (long)S.r_id.w.size() / 2 : (kind == 2 ? (long)S.r_edge.w.size() : (long)S.r_vert.w.size());
+    const int kind = S.sing[i + 2], te = S.sing[i + 3], tf = S.sing[i + 4];
+    const int r = kind == 0 ? 0 : (kind == 2 ? 1 : 2);
+    I.n_singular_points += r == 0 ? (long)S.r_id.w.size() / 2 : (long)R4[r]->w.size();
+    // the rule coordinate that becomes the second local coordinate (as in k_near_singular)
+    const int vse = ((te & 1) != (te >= 4)) ? 0 : 1, vsf = ((tf & 1) != (tf >= 4)) ? 0 : 1;
+    I.n_singular_geo_points += chunk_sum[r][2] + chunk_sum[r][5];
+    I.n_singular_geo_columns += chunk_sum[r][vse] + chunk_sum[r][3 + vsf];
   }
   I.n_levels = S.L + 1;
   for (int l = 0; l <= S.L && l < 24; ++l) {

@@ -41,6 +41,10 @@ CASES = {
     # the 64-direction sound-hard workload: deformed sphere, 64 x 64 elements per patch, kappa = 20
     "deformed_hard_6x64x64_p2_k20": dict(geometry="deformed", m=6, p=2, leaf=4, q=7, kappa=20.0, eta=0.05,
                                          hard=True, cap=6.0, cols=64, seed=2027, nrows=2),
+    # the large single scatterer at the sweep's first kappa: deformed sphere, 256 x 256 elements per
+    # patch (399384 unknowns), kappa = 50, 8 columns, level-adaptive q (7 .. 12, capped admissibility)
+    "deformed_soft_6x256x256_p2_k50": dict(geometry="deformed", m=8, p=2, leaf=6, q=7, q_max=12, kappa=50.0,
+                                           eta=50.0, hard=False, cap=6.0, cols=8, seed=2029, nrows=2),
 }
 
 
@@ -57,7 +61,7 @@ def make(name):
     c = CASES[name]
     t0 = time.time()
     sp = S.Space(S.Mesh(patches(c["geometry"]), c["m"]), c["p"], continuous=c["hard"])
-    tree = fmm.ClusterTree(sp.mesh, c["leaf"], 0.5, c["q"], c["kappa"], kappa_cap=c["cap"])
+    tree = fmm.ClusterTree(sp.mesh, c["leaf"], 0.5, c["q"], c["kappa"], kappa_cap=c["cap"], q_max=c.get("q_max"))
     x = inputs.random_complex(sp.N, seed=c["seed"], cols=c["cols"])
     rows = rows_of(c, sp.N)
     y = fmm.cfie_rows(sp, c["kappa"], c["eta"], c["hard"], x, rows, tree)

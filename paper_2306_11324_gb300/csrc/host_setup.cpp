@@ -259,7 +259,7 @@ static void rule_vertex(const std::vector<double> &gx, const std::vector<double>
 // many points repeat one element's point: the singular kernel evaluates the geometry once per distinct
 // value / point of a chunk.
 static void share_tables(Rule4 &R, int ch, int &nv_max, int &nd_max) {
-  const int n = (int)R.w.size(), nch = (n + ch - 1) / ch, hdr = 6 + 6 * ch;
+  const int n = (int)R.w.size(), nch = (n + ch - 1) / ch, hdr = sing_share_header(ch);
   R.share.assign((size_t)nch * hdr + (size_t)n * 6, 0);
   unsigned char *PI = R.share.data() + (size_t)nch * hdr;
   for (int c = 0; c < nch; ++c) {
@@ -280,18 +280,28 @@ static void share_tables(Rule4 &R, int ch, int &nv_max, int &nd_max) {
           id = it->second;
         }
         PI[(size_t)(p0 + t) * 6 + list] = (unsigned char)id;
+        return id;
       };
+      std::vector<int> grp(cn);
       for (int t = 0; t < cn; ++t) {
         const int p = p0 + t;
         put(m1, a[p], 3 * side, t);
         put(m2, b[p], 3 * side + 1, t);
-        put(md, std::make_pair(a[p], b[p]), 3 * side + 2, t);
+        grp[t] = put(md, std::make_pair(a[p], b[p]), 3 * side + 2, t);
       }
+      const int nd = (int)md.size();
       H[3 * side] = (unsigned char)m1.size();
       H[3 * side + 1] = (unsigned char)m2.size();
-      H[3 * side + 2] = (unsigned char)md.size();
+      H[3 * side + 2] = (unsigned char)nd;
+      // the chunk's points grouped by distinct point, ascending within a group
+      unsigned char *goff = H + 6 + 6 * ch + side * (ch + 1), *gmem = H + 6 + 6 * ch + 2 * (ch + 1) + side * ch;
+      std::vector<int> cnt(nd + 1, 0);
+      for (int t = 0; t < cn; ++t) cnt[grp[t] + 1]++;
+      for (int g = 0; g < nd; ++g) cnt[g + 1] += cnt[g];
+      for (int g = 0; g <= nd; ++g) goff[g] = (unsigned char)cnt[g];
+      for (int t = 0; t < cn; ++t) gmem[cnt[grp[t]]++] = (unsigned char)t;
       nv_max = std::max(nv_max, (int)std::max(m1.size(), m2.size()));
-      nd_max = std::max(nd_max, (int)md.size());
+      nd_max = std::max(nd_max, nd);
     }
   }
 }
@@ -462,9 +472,28 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   rule_identical(sx, sw, S.r_id);
   rule_edge(sx, sw, S.r_edge);
   rule_vertex(sx, sw, S.r_vert);
-  S.sing_ch = S.ns * S.ns <= 128 ? S.ns * S.ns * (128 / (S.ns * S.ns)) : 128;
-  S.sing_nv = S.sing_nd = 0;
-  for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, S.sing_ch, S.sing_nv, S.sing_nd);
+  // chunk of the singular kernel: whole groups of ns^2 points, at most 128 (one point per thread), as many
+  // as keep its shared memory within 110 KB (two blocks per SM), else the smallest that fits at all
+  {
+    const int g = S.ns * S.ns <= 128 ? S.ns * S.ns : 128;
+    int pg1 = 1;
+    for (int v : S.edeg) pg1 = std::max(pg1, v + 1);
+    int chosen = 0;
+    for (int ch = (128 / g) * g; ch >= g && !chosen; ch -= g)
+      for (double lim : {110.0 * 1024, 227.0 * 1024}) {
+        int nv = 0, nd = 0;
+        for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, ch, nv, nd);
+        const double bytes = 8.0 * sing_layout(ch, S.nloc, S.hard, nv, nd, pg1).total;
+        if (bytes <= lim && (lim < 200 * 1024 || ch == g)) {
+          S.sing_ch = ch;
+          S.sing_nv = nv;
+          S.sing_nd = nd;
+          chosen = 1;
+          break;
+        }
+      }
+    if (!chosen) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
+  }
 
   // --- ansatz space: knot vector Xi_{p,m}, tables per element column ---
   std::vector<double> kn;

@@ -73,11 +73,53 @@ struct Arena {
 
 struct Rule4 {  // a rule on [0,1]^4 for touching element pairs, canonical position
   std::vector<double> x1, x2, y1, y2, w;
-  // Sharing tables over chunks of sing_ch consecutive points: per chunk 6 counts and 6 lists of
-  // sing_ch offsets (the first point of each distinct x1, x2, (x1, x2), y1, y2, (y1, y2) in the
-  // chunk), then per point its 6 indices into those lists.
+  // Sharing tables over chunks of sing_ch consecutive points: per chunk 6 counts, 6 lists of sing_ch
+  // offsets (the first point of each distinct x1, x2, (x1, x2), y1, y2, (y1, y2) in the chunk), and
+  // for each side the chunk's points grouped by their distinct point (sing_ch + 1 group offsets, then
+  // sing_ch point offsets); then per point its 6 indices into the lists.
   std::vector<unsigned char> share;
 };
+
+// bytes of one chunk header of Rule4::share
+inline int sing_share_header(int ch) { return 8 + 10 * ch; }
+
+// Shared-memory layout of the singular kernel, offsets in doubles: the union of the per-point and
+// per-group arrays with the geometry column partials, the distinct points' geometry and basis values,
+// the two element nets.
+struct SingLayout {
+  int s3, psi, cur, T, T2, U, geo, phiG, curG, nets, total;
+};
+inline SingLayout sing_layout(int ch, int nloc, bool hard, int nv, int nd, int pg1) {
+  auto al = [](int x) { return (x + 1) & ~1; };  // double2 alignment
+  const int h3 = hard ? 3 : 0;
+  SingLayout L;
+  int o = 0;
+  L.s3 = 0;
+  o = 6 * ch;                      // w k(x,y), w k(y,x), w gc per point (complex)
+  L.psi = o;
+  o += ch * nloc;                  // basis values on the side that is not grouped
+  L.cur = o;
+  o += h3 * ch * nloc;             // and their curls
+  o = al(o);
+  L.T = o;
+  o += 2 * nd * nloc;              // group sums of w k(x,y) times those basis values (complex)
+  L.T2 = o;
+  o += 2 * nd * nloc;              // the same with w k(y,x)
+  L.U = o;
+  o += 2 * h3 * nd * nloc;         // group sums of w gc times the curls (complex)
+  const int col = 2 * nv * pg1 * 8;
+  o = al(o > col ? o : col);
+  L.geo = o;
+  o += 2 * nd * 13;
+  L.phiG = o;
+  o += nd * nloc;
+  L.curG = o;
+  o += h3 * nd * nloc;
+  L.nets = o;
+  o += 8 * 49;
+  L.total = o;
+  return L;
+}
 
 struct TreeLevel {
   int n;                            // clusters on the level (n_patches 4^l)

@@ -268,30 +268,64 @@ __global__ void __launch_bounds__(256) k_m2l_fill(M2LLevel L, bool hard, double 
   }
 }
 
-// M2L from the stored blocks: the row kernel's layout (one block per target cluster, warps over the
-// interaction list, lane rows a0 + lane, a0 + lane + 32) with the samples read from the stored block
-// (coalesced: consecutive lanes read consecutive target nodes) instead of generated.
-template <class T, int NCR, bool HARD>
+// cp.async of one coupling-block entry (8 or 16 bytes) into shared memory; src_bytes = 0 fills zeros
+template <int BYTES>
+__device__ inline void cp_async_zfill(void *dst, const void *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(src_bytes)
+               : "memory");
+}
+__device__ inline void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// M2L from the stored blocks: one block per target cluster, warps over the interaction list, lane rows
+// a0 + lane and a0 + lane + 32.  The stored rows stream through a per-warp ring of D shared-memory
+// slots filled by asynchronous copies (row b + D - 1 is requested while row b is used), so that each
+// warp keeps D rows of the block in flight instead of one load per lane.
+template <class T, int NCR, bool HARD, int D>
 __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_stored(M2LArgs A, int cr0) {
   extern __shared__ __align__(16) unsigned char smst[];
   constexpr bool F32 = std::is_same<T, float>::value;
+  constexpr int ntype = HARD ? 2 : 1, ES = sizeof(C2<T>);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int li = 0;
   while (li + 1 < A.nlev && (int)blockIdx.x >= A.lev[li + 1].first) ++li;
   const M2LLevel &L = A.lev[li];
   const int t = blockIdx.x - L.first;
-  const int Q = L.Q, q = L.q, QS = A.QS, ntype = HARD ? 2 : 1;
+  const int Q = L.Q, q = L.q, QS = A.QS;
   const int ncr = min(NCR, A.CR - cr0);
   C2<T> *xs = reinterpret_cast<C2<T> *>(smst) + warp * QS * NCR;
+  C2<T> *ring = reinterpret_cast<C2<T> *>(smst) + M2L_WARPS * QS * NCR + warp * D * ntype * 64;
   double2 *red = reinterpret_cast<double2 *>(smst);
   const C2<T> *Sall = reinterpret_cast<const C2<T> *>(L.stored);
+  const C2<T> zero = c2((T)0, (T)0);
   for (int a0 = 0; a0 < Q; a0 += 64) {
-    C2<T> tot[2][NCR];
-    for (int k = 0; k < 2; ++k)
-      for (int c = 0; c < NCR; ++c) tot[k][c] = c2((T)0, (T)0);
+    C2<T> tot0[NCR], tot1[NCR];
+    for (int c = 0; c < NCR; ++c) tot0[c] = tot1[c] = zero;
     for (int kk = L.far_ptr[t] + warp; kk < L.far_ptr[t + 1]; kk += M2L_WARPS) {
       const int s = L.far_src[kk];
-      __syncwarp();
+      const C2<T> *Sk = Sall + (long)kk * ntype * Q * Q;
+      // rows 0 .. D - 2 of the block requested before x_s is staged
+      auto issue = [&](int b) {
+        C2<T> *slot = ring + (b % D) * ntype * 64;
+#pragma unroll
+        for (int ty = 0; ty < ntype; ++ty) {
+          const C2<T> *src = Sk + ((long)ty * Q + b) * Q;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int col = a0 + lane + 32 * h;
+            const bool ok = col < Q;
+            cp_async_zfill<ES>(slot + ty * 64 + lane + 32 * h, ok ? src + col : src, ok ? ES : 0);
+          }
+        }
+      };
+      __syncwarp();  // the previous pair's reads of the ring and of x_s are done
+#pragma unroll
+      for (int i = 0; i < D - 1; ++i) {
+        if (i < Q) issue(i);
+        cp_async_commit_group();
+      }
       for (int b = lane; b < Q; b += 32) {
         const long ib = (long)s * Q + b;
         for (int c = 0; c < ncr; ++c) {
@@ -304,37 +338,48 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_stored(M2LArgs A, int cr
           }
         }
       }
-      __syncwarp();
-      const C2<T> *Sk = Sall + (long)kk * ntype * Q * Q;
-      for (int k = 0; k < 2; ++k) {
-        const int a = a0 + lane + 32 * k;
-        if (a >= Q) continue;
-        C2<T> acc[NCR];
-        for (int c = 0; c < NCR; ++c) acc[c] = c2((T)0, (T)0);
-        for (int b1 = 0; b1 < q; ++b1) {
-          C2<T> part[NCR];
-          for (int c = 0; c < NCR; ++c) part[c] = c2((T)0, (T)0);
-          for (int b2 = 0; b2 < q; ++b2) {
-            const int b = b1 * q + b2;
-            const C2<T> s0 = Sk[(long)b * Q + a];
-            if (!HARD) {
-              for (int c = 0; c < NCR; ++c) part[c] = fma2(s0, xs[b * NCR + c], part[c]);
-            } else {
-              const C2<T> s1 = Sk[(long)(Q + b) * Q + a];
-              for (int c = 0; c < NCR; ++c) part[c] = fma2((cr0 + c) / A.R == 0 ? s0 : s1, xs[b * NCR + c], part[c]);
+      for (int b1 = 0; b1 < q; ++b1) {
+        C2<T> p0[NCR], p1[NCR];
+        for (int c = 0; c < NCR; ++c) p0[c] = p1[c] = zero;
+        for (int b2 = 0; b2 < q; ++b2) {
+          const int b = b1 * q + b2;
+          cp_async_wait_group<D - 2>();  // row b has landed (this lane's copies)
+          __syncwarp();                  // ... and every lane's
+          const C2<T> *slot = ring + (b % D) * ntype * 64;
+          const C2<T> s0a = slot[lane], s0b = slot[lane + 32];
+          if (!HARD) {
+#pragma unroll
+            for (int c = 0; c < NCR; ++c) {
+              const C2<T> xv = xs[b * NCR + c];
+              p0[c] = fma2(s0a, xv, p0[c]);
+              p1[c] = fma2(s0b, xv, p1[c]);
+            }
+          } else {
+            const C2<T> s1a = slot[64 + lane], s1b = slot[64 + lane + 32];
+#pragma unroll
+            for (int c = 0; c < NCR; ++c) {
+              const C2<T> xv = xs[b * NCR + c];
+              const bool k0 = (cr0 + c) / A.R == 0;
+              p0[c] = fma2(k0 ? s0a : s1a, xv, p0[c]);
+              p1[c] = fma2(k0 ? s0b : s1b, xv, p1[c]);
             }
           }
-          for (int c = 0; c < NCR; ++c) acc[c] = add(acc[c], part[c]);
+          // the slot of row b - 1 is free (every lane passed this iteration's __syncwarp)
+          if (b + D - 1 < Q) issue(b + D - 1);
+          cp_async_commit_group();
         }
-        for (int c = 0; c < NCR; ++c) tot[k][c] = add(tot[k][c], acc[c]);
+        for (int c = 0; c < NCR; ++c) {
+          tot0[c] = add(tot0[c], p0[c]);
+          tot1[c] = add(tot1[c], p1[c]);
+        }
       }
+      cp_async_wait_group<0>();
     }
     __syncthreads();
-    for (int k = 0; k < 2; ++k)
-      for (int c = 0; c < NCR; ++c) {
-        const int a = lane + 32 * k;
-        red[(warp * 64 + a) * NCR + c] = make_double2((double)tot[k][c].x, (double)tot[k][c].y);
-      }
+    for (int c = 0; c < NCR; ++c) {
+      red[(warp * 64 + lane) * NCR + c] = make_double2((double)tot0[c].x, (double)tot0[c].y);
+      red[(warp * 64 + lane + 32) * NCR + c] = make_double2((double)tot1[c].x, (double)tot1[c].y);
+    }
     __syncthreads();
     const int na = min(64, Q - a0);
     for (int o = threadIdx.x; o < na * ncr; o += blockDim.x) {
@@ -516,10 +561,18 @@ void launch_rows(const M2LArgs &A, int nblocks, cudaStream_t st) {
   }
 }
 
+template <class T, int NCR, bool HARD, int D>
+size_t stored_smem(const M2LArgs &A) {
+  const size_t pts = (size_t)M2L_WARPS * (A.QS * NCR + D * (HARD ? 2 : 1) * 64) * sizeof(C2<T>);
+  return std::max(pts, (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
+}
+
 template <class T, int NCR, bool HARD>
 void launch_stored(const M2LArgs &A, int nblocks, cudaStream_t st) {
-  const size_t smem = std::max((size_t)M2L_WARPS * A.QS * NCR * sizeof(C2<T>), (size_t)M2L_WARPS * 64 * NCR * sizeof(double2));
-  auto kfn = k_m2l_stored<T, NCR, HARD>;
+  // eight rows in flight per warp where the shared memory allows, else three
+  const bool deep = stored_smem<T, NCR, HARD, 8>(A) <= 200 * 1024;
+  const size_t smem = deep ? stored_smem<T, NCR, HARD, 8>(A) : stored_smem<T, NCR, HARD, 3>(A);
+  auto kfn = deep ? k_m2l_stored<T, NCR, HARD, 8> : k_m2l_stored<T, NCR, HARD, 3>;
   IGA_CUDA(set_max_dynamic_smem(kfn, smem));
   for (int cr0 = 0; cr0 < A.CR; cr0 += NCR) {
     kfn<<<nblocks, 32 * M2L_WARPS, smem, st>>>(A, cr0);

@@ -402,18 +402,8 @@ struct SingArgs {
   int rule_n[3];
   const unsigned char *share[3];  // per kind: sharing tables over chunks of ch points
   int ch, nv, nd, pg1;            // chunk; most distinct coordinates / points of a chunk; max degree + 1
+  SingLayout L;                   // shared-memory layout (offsets in doubles)
 };
-
-// shared-memory doubles of k_near_singular: the per-point union (w k psi, curls; aliased by the column
-// partials of the geometry), the distinct points' geometry, the two element nets
-__host__ __device__ inline size_t sing_union_doubles(int ch, int nloc, bool hard, int nv, int pg1) {
-  const size_t pts = (size_t)ch * (2 + 5 * nloc + (hard ? 6 * nloc : 0));
-  const size_t col = (size_t)2 * nv * pg1 * 8;
-  return pts > col ? pts : col;
-}
-__host__ __device__ inline size_t sing_smem_doubles(int ch, int nloc, bool hard, int nv, int nd, int pg1) {
-  return sing_union_doubles(ch, nloc, hard, nv, pg1) + (size_t)2 * nd * 13 + 8 * 49;
-}
 
 // values of the nloc local functions at local point (u, v) of element column (ix, iy) (Bernstein
 // extraction) into val; with curl != nullptr also c_k = d_s psi_k d_t F - d_t psi_k d_s F
@@ -450,44 +440,6 @@ __device__ inline void basis_curl_at(const NearArgs &A, int ix, int iy, double u
 
 constexpr int SING_MAXACC = 19;  // (p+1)^4 / 128 rounded up for p <= 6
 
-// The nloc local functions at local point (u, v) of element column (ix, iy), each times the complex
-// weights s1 (into o1) and, when o2 != nullptr, s2 (into o2); with curl != nullptr also the curls as in
-// basis_curl_at.  Folding the kernel value into the test side leaves two multiply-adds per block entry
-// and point in the accumulation.
-__device__ inline void basis_scaled_at(const NearArgs &A, int ix, int iy, double u, double v, const double *fs,
-                                       const double *ft, double2 s1, double2 s2, double2 *o1, double2 *o2,
-                                       double *curl) {
-  const int p = A.p, p1 = p + 1;
-  double Bu[8], dBu[8], Bv[8], dBv[8];
-  bernstein_all(p, u, Bu, curl ? dBu : nullptr);
-  bernstein_all(p, v, Bv, curl ? dBv : nullptr);
-  double fu[8], dfu[8], fv[8], dfv[8];
-  for (int a = 0; a <= p; ++a) {
-    double s0 = 0, s1u = 0, t0 = 0, t1 = 0;
-    for (int c = 0; c <= p; ++c) {
-      double ea = A.ext1[(ix * p1 + a) * p1 + c], eb = A.ext1[(iy * p1 + a) * p1 + c];
-      s0 += ea * Bu[c];
-      t0 += eb * Bv[c];
-      if (curl) {
-        s1u += ea * dBu[c];
-        t1 += eb * dBv[c];
-      }
-    }
-    fu[a] = s0; fv[a] = t0; dfu[a] = s1u * A.n1; dfv[a] = t1 * A.n1;
-  }
-  for (int a = 0; a <= p; ++a)
-    for (int b = 0; b <= p; ++b) {
-      const int k = a * p1 + b;
-      const double val = fu[a] * fv[b];
-      o1[k] = cscale(s1, val);
-      if (o2) o2[k] = cscale(s2, val);
-      if (curl) {
-        const double ds = dfu[a] * fv[b], dt = fu[a] * dfv[b];
-        for (int d = 0; d < 3; ++d) curl[k * 3 + d] = ds * ft[d] - dt * fs[d];
-      }
-    }
-}
-
 // One block per unordered touching pair.  Points of the regularising rule of the pair's kind, mapped
 // by the canonical square symmetries; for edge and vertex pairs the same points also give the block
 // of (f, e) with the roles of x and y exchanged (the rules are symmetric under that exchange).
@@ -495,17 +447,19 @@ template <int NSLOT>
 __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;
   extern __shared__ double smd[];
-  const int nloc = A.nloc, p1 = A.p + 1, ch = S.ch;
-  // shared: Ax[ch][nloc], Bx[ch][nloc] (complex: w k(x,y) psi_k(x) and w k(y,x) psi_k(x)), gc[ch] (complex),
-  // phy[ch][nloc], and for sound-hard cx[ch][nloc][3], cy[ch][nloc][3]; aliased by the column partials
-  // colp[2][nv][pg1][8] of the element geometries; then geo[2][nd][13] (x, d_s x, d_t x, n, |n| of the
-  // chunk's distinct points) and the two element nets
-  double2 *Ax = reinterpret_cast<double2 *>(smd), *Bx = Ax + ch * nloc, *gc = Bx + ch * nloc;
-  double *phy = reinterpret_cast<double *>(gc + ch);
-  double *cxs = phy + ch * nloc, *cys = cxs + (A.hard ? 3 * ch * nloc : 0);
+  const int nloc = A.nloc, p1 = A.p + 1, ch = S.ch, hard = A.hard;
+  // shared (SingLayout): per point S3[ch][3] (w k(x,y), w k(y,x), w gc), the basis values psiO[ch][nloc]
+  // (and curls) of the side that is not grouped; per group T, T2 [nd][nloc] and U [nd][nloc][3]; all
+  // aliased by the column partials colp[2][nv][pg1][8] of the element geometries; then geo[2][nd][13]
+  // (x, d_s x, d_t x, n, |n| of the chunk's distinct points), the basis values (and curls) of the
+  // grouped side's distinct points, the two element nets
   double *colp = smd;
-  double *geo = smd + sing_union_doubles(ch, nloc, A.hard, S.nv, S.pg1);
-  double *net_e = geo + 2 * S.nd * 13, *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
+  double2 *S3 = reinterpret_cast<double2 *>(smd + S.L.s3);
+  double *psiO = smd + S.L.psi, *curO = smd + S.L.cur;
+  double2 *T = reinterpret_cast<double2 *>(smd + S.L.T), *T2 = reinterpret_cast<double2 *>(smd + S.L.T2);
+  double2 *Ug = reinterpret_cast<double2 *>(smd + S.L.U);
+  double *geo = smd + S.L.geo, *phiG = smd + S.L.phiG, *curG = smd + S.L.curG;
+  double *net_e = smd + S.L.nets, *net_f = net_e + 4 * 49;  // element nets (degree <= 6)
   const int *W = S.sing + 7 * blockIdx.x;
   const int e = W[0], f = W[1], kind = W[2], te = W[3], tf = W[4], blk_ef = W[5], blk_fe = W[6];
   const bool both = blk_fe >= 0;
@@ -516,7 +470,7 @@ __global__ void k_near_singular(SingArgs S) {
   const int nuse = kind == 0 ? npt / 2 : npt;
   const double *R = S.rule[ri];
   const unsigned char *SH = S.share[ri];
-  const int hdr = 6 + 6 * ch;
+  const int hdr = 8 + 10 * ch;  // sing_share_header
   const unsigned char *PI = SH + (size_t)((npt + ch - 1) / ch) * hdr;
   const int n1 = A.n1;
   const int ixe = (e / n1) % n1, iye = e % n1, ixf = (f / n1) % n1, iyf = f % n1;
@@ -534,6 +488,10 @@ __global__ void k_near_singular(SingArgs S) {
   for (int c0 = 0; c0 < nuse; c0 += ch) {
     const int cn = min(ch, nuse - c0);
     const unsigned char *H = SH + (size_t)(c0 / ch) * hdr;
+    // the side whose points repeat most in this chunk is grouped: sum_t s_t phi_k(x_t) psi_l(y_t) =
+    // sum_g phi_k(x_g) sum_{t in g} s_t psi_l(y_t) (grouping by x; by y with the roles exchanged)
+    const int gs = H[5] < H[2] ? 1 : 0, ng = H[gs ? 5 : 2];
+    const unsigned char *goff = H + 6 + 6 * ch + gs * (ch + 1), *gmem = H + 6 + 6 * ch + 2 * (ch + 1) + gs * ch;
     // geometry, step 1: for each distinct second local coordinate v of the chunk and each row i of the
     // net, the row contracted with the Bernstein polynomials of v and their derivatives
     {
@@ -568,7 +526,8 @@ __global__ void k_near_singular(SingArgs S) {
     }
     __syncthreads();
     // geometry, step 2: each distinct point of the chunk (x, its tangents d_s x, d_t x, the normal
-    // n = d_s x ^ d_t x and |n|) from the column partials of its second coordinate
+    // n = d_s x ^ d_t x and |n|) from the column partials of its second coordinate; on the grouped side
+    // also the basis values (and curls) there
     {
       const int nde = H[2], ndf = H[5];
       for (int w = threadIdx.x; w < nde + ndf; w += blockDim.x) {
@@ -609,9 +568,14 @@ __global__ void k_near_singular(SingArgs S) {
         g[10] = nn[1];
         g[11] = nn[2];
         g[12] = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        if ((int)sf == gs)
+          basis_curl_at(A, sf ? ixf : ixe, sf ? iyf : iye, u, v, fs, ft, phiG + (size_t)k * nloc,
+                        hard ? curG + (size_t)k * nloc * 3 : nullptr);
       }
     }
     __syncthreads();
+    // per 4-D point: the kernel values times the weight, and the basis values (and curls) of the side
+    // that is not grouped
     for (int t = threadIdx.x; t < cn; t += blockDim.x) {
       const int ip = c0 + t;
       double ue, ve, uf, vf;
@@ -620,57 +584,100 @@ __global__ void k_near_singular(SingArgs S) {
       const double w = R[4 * npt + ip] * h4;
       const double *ge = geo + (size_t)PI[(size_t)ip * 6 + 2] * 13;
       const double *gf = geo + (size_t)(S.nd + PI[(size_t)ip * 6 + 5]) * 13;
-      double X[3], Y[3], fs[3], ft[3], gs[3], gt[3], nx[3], ny[3];
+      double X[3], Y[3], nx[3], ny[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        X[k] = ge[k]; fs[k] = ge[3 + k]; ft[k] = ge[6 + k]; nx[k] = ge[9 + k];
-        Y[k] = gf[k]; gs[k] = gf[3 + k]; gt[k] = gf[6 + k]; ny[k] = gf[9 + k];
+        X[k] = ge[k]; nx[k] = ge[9 + k];
+        Y[k] = gf[k]; ny[k] = gf[9 + k];
       }
-      const double ax = ge[12], ay = gf[12];
       PairKernel pk;
       double2 kyx;
-      cfie_kernel_both(A.hard, A.kappa, A.eta, X, nx, ax, Y, ny, ay, pk, kyx);
-      gc[t] = cscale(pk.gc, w);  // gc(y, x) = gc(x, y)
-      basis_scaled_at(A, ixe, iye, ue, ve, fs, ft, cscale(pk.ks, w), cscale(kyx, w), Ax + t * nloc,
-                      both ? Bx + t * nloc : nullptr, A.hard ? cxs + t * nloc * 3 : nullptr);
-      basis_curl_at(A, ixf, iyf, uf, vf, gs, gt, phy + t * nloc, A.hard ? cys + t * nloc * 3 : nullptr);
+      cfie_kernel_both(hard, A.kappa, A.eta, X, nx, ge[12], Y, ny, gf[12], pk, kyx);
+      S3[3 * t] = cscale(pk.ks, w);
+      S3[3 * t + 1] = cscale(kyx, w);
+      S3[3 * t + 2] = cscale(pk.gc, w);  // gc(y, x) = gc(x, y)
+      const double *go = gs ? ge : gf;
+      if (gs) basis_curl_at(A, ixe, iye, ue, ve, go + 3, go + 6, psiO + (size_t)t * nloc,
+                            hard ? curO + (size_t)t * nloc * 3 : nullptr);
+      else basis_curl_at(A, ixf, iyf, uf, vf, go + 3, go + 6, psiO + (size_t)t * nloc,
+                         hard ? curO + (size_t)t * nloc * 3 : nullptr);
     }
     __syncthreads();
+    // group sums: T[g][i] = sum_{t in g} w k(x_t, y_t) psiO_i(t), T2 the same with k(y, x), and for
+    // sound-hard U[g][i] = sum_{t in g} w gc(t) curlO_i(t)
+    for (int w = threadIdx.x; w < ng * nloc; w += blockDim.x) {
+      const int g = w / nloc, i = w % nloc;
+      double2 t1 = cmk(0, 0), t2 = cmk(0, 0), u0 = cmk(0, 0), u1 = cmk(0, 0), u2 = cmk(0, 0);
+      for (int m = goff[g]; m < goff[g + 1]; ++m) {
+        const int t = gmem[m];
+        if (t >= cn) break;  // members ascend: the rest lie past the chunk's used points
+        const double ps = psiO[t * nloc + i];
+        const double2 s1 = S3[3 * t];
+        t1.x = fma(s1.x, ps, t1.x);
+        t1.y = fma(s1.y, ps, t1.y);
+        if (both) {
+          const double2 s2 = S3[3 * t + 1];
+          t2.x = fma(s2.x, ps, t2.x);
+          t2.y = fma(s2.y, ps, t2.y);
+        }
+        if (hard) {
+          const double2 gg = S3[3 * t + 2];
+          const double *cu = curO + (t * nloc + i) * 3;
+          u0.x = fma(gg.x, cu[0], u0.x); u0.y = fma(gg.y, cu[0], u0.y);
+          u1.x = fma(gg.x, cu[1], u1.x); u1.y = fma(gg.y, cu[1], u1.y);
+          u2.x = fma(gg.x, cu[2], u2.x); u2.y = fma(gg.y, cu[2], u2.y);
+        }
+      }
+      T[w] = t1;
+      T2[w] = t2;
+      if (hard) {
+        Ug[3 * w] = u0;
+        Ug[3 * w + 1] = u1;
+        Ug[3 * w + 2] = u2;
+      }
+    }
+    __syncthreads();
+    // block entries (k of x, l of y): a += sum_g phiG_kG(g) T[g][kO] (+ curlG . U), kG / kO the entry's
+    // index on the grouped / other side
 #pragma unroll
     for (int slot = 0; slot < NSLOT; ++slot) {
       const int i = threadIdx.x + slot * blockDim.x;
       if (i >= nloc * nloc) break;
       const int k = i / nloc, l = i % nloc;
+      const int kG = gs ? l : k, kO = gs ? k : l;
       double2 a = acc[slot], b = accb[slot];
-      if (A.hard) {
-        for (int t = 0; t < cn; ++t) {
-          const double py = phy[t * nloc + l];
-          const double *ck = cxs + (t * nloc + k) * 3, *cl = cys + (t * nloc + l) * 3;
-          const double dot = ck[0] * cl[0] + ck[1] * cl[1] + ck[2] * cl[2];
-          const double2 g = gc[t], ax = Ax[t * nloc + k];
-          a.x = fma(ax.x, py, fma(g.x, dot, a.x));
-          a.y = fma(ax.y, py, fma(g.y, dot, a.y));
+      if (hard) {
+        for (int g = 0; g < ng; ++g) {
+          const double ph = phiG[g * nloc + kG];
+          const double *cg = curG + (g * nloc + kG) * 3;
+          const double2 *uu = Ug + 3 * (g * nloc + kO);
+          const double2 tt = T[g * nloc + kO];
+          double2 d;
+          d.x = fma(cg[0], uu[0].x, fma(cg[1], uu[1].x, cg[2] * uu[2].x));
+          d.y = fma(cg[0], uu[0].y, fma(cg[1], uu[1].y, cg[2] * uu[2].y));
+          a.x = fma(ph, tt.x, a.x + d.x);
+          a.y = fma(ph, tt.y, a.y + d.y);
           if (both) {
-            const double2 bx = Bx[t * nloc + k];
-            b.x = fma(bx.x, py, fma(g.x, dot, b.x));
-            b.y = fma(bx.y, py, fma(g.y, dot, b.y));
+            const double2 t2 = T2[g * nloc + kO];
+            b.x = fma(ph, t2.x, b.x + d.x);
+            b.y = fma(ph, t2.y, b.y + d.y);
           }
         }
       } else if (both) {
-        for (int t = 0; t < cn; ++t) {
-          const double py = phy[t * nloc + l];
-          const double2 ax = Ax[t * nloc + k], bx = Bx[t * nloc + k];
-          a.x = fma(ax.x, py, a.x);
-          a.y = fma(ax.y, py, a.y);
-          b.x = fma(bx.x, py, b.x);
-          b.y = fma(bx.y, py, b.y);
+        for (int g = 0; g < ng; ++g) {
+          const double ph = phiG[g * nloc + kG];
+          const double2 tt = T[g * nloc + kO], t2 = T2[g * nloc + kO];
+          a.x = fma(ph, tt.x, a.x);
+          a.y = fma(ph, tt.y, a.y);
+          b.x = fma(ph, t2.x, b.x);
+          b.y = fma(ph, t2.y, b.y);
         }
       } else {
-        for (int t = 0; t < cn; ++t) {
-          const double py = phy[t * nloc + l];
-          const double2 ax = Ax[t * nloc + k];
-          a.x = fma(ax.x, py, a.x);
-          a.y = fma(ax.y, py, a.y);
+        for (int g = 0; g < ng; ++g) {
+          const double ph = phiG[g * nloc + kG];
+          const double2 tt = T[g * nloc + kO];
+          a.x = fma(ph, tt.x, a.x);
+          a.y = fma(ph, tt.y, a.y);
         }
       }
       acc[slot] = a;
@@ -808,7 +815,8 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   SA.nd = S.sing_nd;
   SA.pg1 = pg1;
   for (int k = 0; k < 3; ++k) SA.share[k] = d.share[k];
-  const size_t smem = sing_smem_doubles(S.sing_ch, S.nloc, S.hard, S.sing_nv, S.sing_nd, pg1) * sizeof(double);
+  SA.L = sing_layout(S.sing_ch, S.nloc, S.hard, S.sing_nv, S.sing_nd, pg1);
+  const size_t smem = (size_t)SA.L.total * sizeof(double);
   if (smem > 227 * 1024) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
   const int nslot = (S.nloc * S.nloc + 127) / 128;
   auto go = [&](auto kfn) {

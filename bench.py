@@ -50,14 +50,14 @@ WORKLOADS = {
     # 64 incident directions on a Fibonacci sphere solved as one multi-RHS request; admissibility capped
     # at kappa * diameter <= 6 (FMM truncation ~1e-5 against the dense matrix at q = 7)
     # GMRES(30) stagnates on this sound-hard system (the hypersingular part is unbounded and kappa is
-    # large): restart 300.
-    # A step of this workload is one operator application to all 64 columns: the sound-hard system
-    # converges slowly (GMRES(300) reaches 1.0e-5 after ~5000 iterations with eta = kappa), so the solve
-    # beside the steps is capped at 1500 iterations and reports the residual it reached.
+    # large): restart 300, eta = 1/kappa and the block preconditioner (~300 iterations to 1e-5 at 16
+    # directions, against ~860 unpreconditioned).
+    # A step of this workload is one operator application to all 64 columns; one solve (capped at 1500
+    # iterations) is timed beside the steps.
     "deformed_hard_6x64x64_p2_k20_64dirs": dict(geometry="deformed", level_m=6, degree_p=2, kappa=20.0, bc=1,
                                                 cheb_q=7, eta_adm=0.5, leaf_offset={"fp64": 2, "mixed": 2, "tc": 2},
                                                 tol={"fp64": 1e-5, "mixed": 1e-5, "tc": 1e-5}, n_dir=100, n_rhs=64,
-                                                kappa_cap=6.0, restart=300, precond={"fp64": 0, "mixed": 0, "tc": 0},
+                                                kappa_cap=6.0, restart=300, precond={"fp64": 1, "mixed": 1, "tc": 1},
                                                 precision="tc", step="matvec", solve_max_iter=1500, eta=0.05),
     # the large single scatterer: deformed sphere (amplitude 0.15, seed 1), 256 x 256 elements per patch
     # (393216 elements, 399384 unknowns), sound-soft, a frequency sweep of 16 kappa in [50, 60] with 8
@@ -98,18 +98,20 @@ def singular_flops(info, p, hard, pg=4):
     coordinate (once per distinct value in a chunk of the rule): the homogeneous rows of the rational
     Bezier net of degree pg with their derivatives, 2 (pg+1)^2 4 2 flops.  Per distinct element point:
     the columns with value, d/du, d/dv ((pg+1) 4 3 2), the rational quotient, normal and Jacobian (30).
-    Per 4-D point: the kernel (distance, sincos, G, G'/r and the weights, 60), both elements' (p+1)^2
-    B-splines by Bernstein extraction (and their surface curls for sound-hard), the kernel value times
-    the test functions (w k psi_k, also for the transposed block of a common-edge or common-vertex pair
-    taken from the same points) and the accumulation of the (p+1)^2 x (p+1)^2 blocks (one complex-by-real
-    multiply-add per entry and block; sound-hard adds the curl product G c_k . c_l)."""
+    Per 4-D point: the kernel (distance, sincos, G, G'/r, the two orientations and the weight, 60), the
+    (p+1)^2 B-splines of the side that is not grouped by Bernstein extraction (5 per function; the surface
+    curls 6 more for sound-hard) and the group sums (the kernel value of each orientation times each
+    function, 8 per function; sound-hard adds w gc times the curls, 12).  Per group of points sharing an
+    element point: that side's B-splines (and curls) and the accumulation of the (p+1)^2 x (p+1)^2 entries
+    of both blocks (8 per entry; sound-hard 16 more for the curl products)."""
     n = (p + 1) ** 2
     per_column = 2 * (pg + 1) ** 2 * 4 * 2
     per_geo_point = (pg + 1) * 4 * 3 * 2 + 30
-    basis = 2 * (5 * n + (6 * n if hard else 0)) + 2 * 4 * n
-    acc = n * n * (2 * 4 + (5 + 8 if hard else 0))
+    basis = 5 * n + (6 * n if hard else 0)
+    per_point = 60 + basis + 8 * n + (12 * n if hard else 0)
+    per_group = basis + n * n * (8 + (16 if hard else 0))
     return (info["n_singular_geo_columns"] * per_column + info["n_singular_geo_points"] * per_geo_point
-            + info["n_singular_points"] * (basis + 60 + acc))
+            + info["n_singular_points"] * per_point + info["n_singular_groups"] * per_group)
 
 
 def mie_soft_far_field(kappa, xhat, d=(0.0, 0.0, 1.0)):
@@ -430,7 +432,7 @@ def run_serving(args):
         return geoms[seed]
 
     def opt(r):
-        # sound-soft: block preconditioner, GMRES(30); sound-hard: GMRES(300) (see the C2 workload);
+        # block preconditioner; sound-soft GMRES(30), sound-hard GMRES(300) (see the C2 workload);
         # level-adaptive q (7 .. 12) under the kappa * diameter <= 6 cap, as in the large-scatterer
         # workload (the cap alone leaves only the finest level admissible at kappa ~ 30); the M2L
         # coupling blocks stored in FP32 (set up once, read by every product: the many-iteration
@@ -440,7 +442,7 @@ def run_serving(args):
                                         eta_cfie=1.0 / r["kappa"] if r["bc"] else r["kappa"],
                                         bc=r["bc"], cheb_q=7, q_max=12, eta_adm=0.5, leaf_offset=2, kappa_cap=6.0,
                                         precision=B.MIXED_FP32, tol=1e-5, max_iter=args.max_iter,
-                                        gmres_restart=300 if r["bc"] else 30, precond=0 if r["bc"] else 1,
+                                        gmres_restart=300 if r["bc"] else 30, precond=1,
                                         m2l_stored=1)
     for r in reqs:
         geom(r["geom_seed"])
@@ -772,6 +774,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                 "singular_points": info["n_singular_points"],
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
+                "singular_groups": info["n_singular_groups"],
                 "m2l": {"kernel": "k_m2l_rows<float> / k_m2l_gemm<float>", "achieved": m2l_ach, "unit": "TFLOP/s",
                         "peak": peaks["fp32_tflops"], "frac": m2l_ach / peaks["fp32_tflops"],
                         "xu_frac": (m2l_samples / (peaks["sincosf_gops"] * 1e9) + m2l_samples / (peaks["rsqrtf_gops"] * 1e9))
@@ -991,6 +994,7 @@ def main():
                 "singular_points": info["n_singular_points"],
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
+                "singular_groups": info["n_singular_groups"],
                 "m2l": m2l_alu_roofline("k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>", far, Q, hard,
                                         len(dirs), m2l_ms, peaks, fp64)}
 

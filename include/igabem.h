@@ -132,6 +132,9 @@ typedef struct {
                                   repeated inside a chunk of the rule is evaluated once) */
   long n_singular_geo_columns; /* element nets contracted along their second coordinate, once per
                                   distinct value of it in a chunk */
+  long n_singular_groups;      /* groups of 4-D points sharing the point of one element (per chunk, on the
+                                  side with fewer distinct points): block entries are accumulated once
+                                  per group */
 } igabem_info;
 
 typedef struct {

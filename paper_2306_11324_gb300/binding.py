@@ -38,7 +38,8 @@ class igabem_info(ctypes.Structure):
                 ("n_touching_pairs", c_long), ("n_far_pairs", c_long), ("device_bytes", c_size_t),
                 ("setup_ms", c_double), ("host_setup_ms", c_double), ("n_singular_points", c_long),
                 ("n_levels", c_int), ("level_q", c_int * 24), ("level_far", c_long * 24),
-                ("n_singular_geo_points", c_long), ("n_singular_geo_columns", c_long)]
+                ("n_singular_geo_points", c_long), ("n_singular_geo_columns", c_long),
+                ("n_singular_groups", c_long)]
 
 
 class igabem_solve_info(ctypes.Structure):

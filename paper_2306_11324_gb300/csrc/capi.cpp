@@ -339,7 +339,17 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
   P->t_plan = now_ms();
   try {
     HostSetup &S = P->S;
-    build_setup(geom->patches, *opt, S);
+    std::shared_ptr<const GeoCache> hit;
+    {
+      std::lock_guard<std::mutex> lk(geom->cache_mu);
+      if (geom->cache && geom->cache->m == opt->level_m) hit = geom->cache;
+    }
+    auto fill = std::make_shared<GeoCache>();
+    build_setup(geom->patches, *opt, S, hit.get(), fill.get());
+    if (fill->m >= 0) {
+      std::lock_guard<std::mutex> lk(geom->cache_mu);
+      geom->cache = fill;
+    }
     P->info.host_setup_ms = now_ms() - P->t_plan;
     const int nq = S.ng * S.ng;
     size_t total = 0;
@@ -545,12 +555,17 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   I.n_singular_points = 0;
   I.n_singular_geo_points = 0;
   I.n_singular_geo_columns = 0;
-  // per rule, summed over the chunks a pair integrates: distinct x1, x2, x-points, y1, y2, y-points
-  long chunk_sum[3][6] = {};
+  I.n_singular_groups = 0;
+  // per rule, summed over the chunks a pair integrates: distinct x1, x2, x-points, y1, y2, y-points,
+  // and the groups of the side with fewer distinct points
+  long chunk_sum[3][7] = {};
   for (int k = 0; k < 3; ++k) {
     const int n = (int)R4[k]->w.size(), nuse = k == 0 ? n / 2 : n, ch = S.sing_ch;
-    for (int c0 = 0; c0 < nuse; c0 += ch)
-      for (int j = 0; j < 6; ++j) chunk_sum[k][j] += R4[k]->share[(size_t)(c0 / ch) * (6 + 6 * ch) + j];
+    for (int c0 = 0; c0 < nuse; c0 += ch) {
+      const unsigned char *H = R4[k]->share.data() + (size_t)(c0 / ch) * sing_share_header(ch);
+      for (int j = 0; j < 6; ++j) chunk_sum[k][j] += H[j];
+      chunk_sum[k][6] += std::min(H[2], H[5]);
+    }
   }
   for (size_t i = 0; i + 6 < S.sing.size(); i += 7) {
     const int kind = S.sing[i + 2], te = S.sing[i + 3], tf = S.sing[i + 4];
@@ -560,6 +575,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     const int vse = ((te & 1) != (te >= 4)) ? 0 : 1, vsf = ((tf & 1) != (tf >= 4)) ? 0 : 1;
     I.n_singular_geo_points += chunk_sum[r][2] + chunk_sum[r][5];
     I.n_singular_geo_columns += chunk_sum[r][vse] + chunk_sum[r][3 + vsf];
+    I.n_singular_groups += chunk_sum[r][6];
   }
   I.n_levels = S.L + 1;
   for (int l = 0; l <= S.L && l < 24; ++l) {

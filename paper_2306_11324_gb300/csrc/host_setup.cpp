@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <map>
 #include <numeric>
+#include <thread>
 #include <string>
 #include <unordered_map>
 
@@ -360,6 +361,22 @@ static void csr_of_pairs(const std::vector<std::pair<int, int>> &pairs, int n, s
   for (int i : by_col) col[fill[pairs[i].first]++] = pairs[i].second;
 }
 
+// body(i) for i in [0, n) on up to 16 host threads (independent iterations writing disjoint data)
+template <class F>
+static void parallel_for(long n, const F &body) {
+  const long nt = std::min<long>(std::min<long>(16, std::max(1u, std::thread::hardware_concurrency())), n);
+  if (nt <= 1) {
+    for (long i = 0; i < n; ++i) body(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (long k = 0; k < nt; ++k)
+    th.emplace_back([&, k] {
+      for (long i = k; i < n; i += nt) body(i);
+    });
+  for (auto &t : th) t.join();
+}
+
 static double dist3(const double *a, const double *b) {
   return std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
                    (a[2] - b[2]) * (a[2] - b[2]));
@@ -367,7 +384,8 @@ static double dist3(const double *a, const double *b) {
 
 // ----------------------------------------------------------------------------------------------
 
-void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S) {
+void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S, const GeoCache *hit,
+                 GeoCache *fill) {
   const int np = (int)patches.size();
   const int m = opt.level_m, p = opt.degree_p;
   if (m < 0 || m > 12) fail(IGABEM_EINVAL, "level_m must lie in 0..12");
@@ -381,89 +399,107 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   if (S.ng < 1 || S.ng > 8 || S.ns < 1 || S.ns > 10) fail(IGABEM_EINVAL, "quadrature orders out of range");
 
   // --- per-element rational Bezier nets ---
-  S.edeg.resize(2 * S.E);
-  S.eoff.resize(S.E);
-  long off = 0;
-  for (int j = 0; j < np; ++j) {
-    const Patch &P = patches[j];
-    for (const std::vector<double> *kn : {&P.kn1, &P.kn2})
-      for (double x : *kn) {
-        double y = x * S.n1;
-        if (std::fabs(y - std::round(y)) > 1e-9)
-          fail(IGABEM_EINVAL, "patch " + std::to_string(j) +
-                                  ": a knot is not an element boundary at this level m");
+  if (hit) {
+    S.edeg = hit->edeg;
+    S.eoff = hit->eoff;
+    S.ebez = hit->ebez;
+    S.corners = hit->corners;
+    S.scale = hit->scale;
+  } else {
+    S.edeg.resize(2 * S.E);
+    S.eoff.resize(S.E);
+    long off = 0;
+    for (int j = 0; j < np; ++j) {
+      const Patch &P = patches[j];
+      for (const std::vector<double> *kn : {&P.kn1, &P.kn2})
+        for (double x : *kn) {
+          double y = x * S.n1;
+          if (std::fabs(y - std::round(y)) > 1e-9)
+            fail(IGABEM_EINVAL, "patch " + std::to_string(j) +
+                                    ": a knot is not an element boundary at this level m");
+        }
+      for (int e = 0; e < S.n1 * S.n1; ++e) {
+        int id = j * S.n1 * S.n1 + e;
+        S.edeg[2 * id] = P.p1; S.edeg[2 * id + 1] = P.p2;
+        S.eoff[id] = off;
+        off += 4L * (P.p1 + 1) * (P.p2 + 1);
       }
-    for (int e = 0; e < S.n1 * S.n1; ++e) {
-      int id = j * S.n1 * S.n1 + e;
-      S.edeg[2 * id] = P.p1; S.edeg[2 * id + 1] = P.p2;
-      S.eoff[id] = off;
-      off += 4L * (P.p1 + 1) * (P.p2 + 1);
+    }
+    S.ebez.assign(off, 0.0);
+    S.corners.assign(12L * S.E, 0.0);
+    for (int j = 0; j < np; ++j) {
+      const Patch &P = patches[j];
+      if (P.p1 > MAX_DEG || P.p2 > MAX_DEG) fail(IGABEM_EINVAL, "patch degree above " + std::to_string(MAX_DEG));
+      const int s1 = P.p1 + 1, s2 = P.p2 + 1;
+      // The element's Bezier net is linear in the control points of its polynomial piece:
+      // net = E1[ix] CP E2[iy]^T per homogeneous component, with E = (Bezier collocation inverse) x
+      // (B-spline values at the element's collocation points u_a = a / p) per direction.
+      auto factors = [&](const std::vector<double> &kn, int pd, std::vector<int> &span, std::vector<double> &E) {
+        const int sd = pd + 1;
+        const std::vector<double> Vi = bernstein_collocation_inverse(pd);
+        span.assign(S.n1, 0);
+        E.assign((size_t)S.n1 * sd * sd, 0.0);
+        std::vector<double> B((size_t)sd * sd);
+        for (int ix = 0; ix < S.n1; ++ix) {
+          span[ix] = find_span(kn, pd, (ix + 0.5) * S.h);
+          for (int a = 0; a < sd; ++a) {
+            const double u = pd ? double(a) / pd : 0.0;
+            span_basis(kn, pd, span[ix], (ix + u) * S.h, &B[(size_t)a * sd], nullptr);
+          }
+          for (int a = 0; a < sd; ++a)
+            for (int i = 0; i < sd; ++i) {
+              double acc = 0;
+              for (int k = 0; k < sd; ++k) acc += Vi[a * sd + k] * B[(size_t)k * sd + i];
+              E[((size_t)ix * sd + a) * sd + i] = acc;
+            }
+        }
+      };
+      std::vector<int> span1, span2;
+      std::vector<double> E1, E2;
+      factors(P.kn1, P.p1, span1, E1);
+      factors(P.kn2, P.p2, span2, E2);
+      parallel_for(S.n1, [&](long ixl) {
+        const int ix = (int)ixl;
+        std::vector<double> T((size_t)s1 * s2 * 4);
+        for (int iy = 0; iy < S.n1; ++iy) {
+          const int id = (j * S.n1 + ix) * S.n1 + iy;
+          const int i0 = span1[ix] - P.p1, j0 = span2[iy] - P.p2;
+          const double *e1 = &E1[(size_t)ix * s1 * s1], *e2 = &E2[(size_t)iy * s2 * s2];
+          // T[i][b] = sum_jj E2[b][jj] CP[i0 + i][j0 + jj]
+          for (int i = 0; i < s1; ++i)
+            for (int b = 0; b < s2; ++b)
+              for (int c = 0; c < 4; ++c) {
+                double acc = 0;
+                for (int jj = 0; jj < s2; ++jj) acc += e2[b * s2 + jj] * P.hw[((i0 + i) * P.k2 + (j0 + jj)) * 4 + c];
+                T[(i * s2 + b) * 4 + c] = acc;
+              }
+          double *out = &S.ebez[S.eoff[id]];
+          for (int a = 0; a < s1; ++a)
+            for (int b = 0; b < s2; ++b)
+              for (int c = 0; c < 4; ++c) {
+                double acc = 0;
+                for (int i = 0; i < s1; ++i) acc += e1[a * s1 + i] * T[(i * s2 + b) * 4 + c];
+                out[(a * s2 + b) * 4 + c] = acc;
+              }
+          const int ca[4] = {0, P.p1, 0, P.p1}, cb[4] = {0, 0, P.p2, P.p2};
+          for (int c = 0; c < 4; ++c) {
+            const double *hw = &out[(ca[c] * s2 + cb[c]) * 4];
+            for (int k = 0; k < 3; ++k) S.corners[(id * 4 + c) * 3 + k] = hw[k] / hw[3];
+          }
+        }
+      });
+    }
+    S.scale = 0;
+    for (double v : S.corners) S.scale = std::max(S.scale, std::fabs(v));
+    if (fill) {
+      fill->m = m;
+      fill->edeg = S.edeg;
+      fill->eoff = S.eoff;
+      fill->ebez = S.ebez;
+      fill->corners = S.corners;
+      fill->scale = S.scale;
     }
   }
-  S.ebez.assign(off, 0.0);
-  S.corners.assign(12L * S.E, 0.0);
-  for (int j = 0; j < np; ++j) {
-    const Patch &P = patches[j];
-    if (P.p1 > MAX_DEG || P.p2 > MAX_DEG) fail(IGABEM_EINVAL, "patch degree above " + std::to_string(MAX_DEG));
-    const int s1 = P.p1 + 1, s2 = P.p2 + 1;
-    // The element's Bezier net is linear in the control points of its polynomial piece:
-    // net = E1[ix] CP E2[iy]^T per homogeneous component, with E = (Bezier collocation inverse) x
-    // (B-spline values at the element's collocation points u_a = a / p) per direction.
-    auto factors = [&](const std::vector<double> &kn, int pd, std::vector<int> &span, std::vector<double> &E) {
-      const int sd = pd + 1;
-      const std::vector<double> Vi = bernstein_collocation_inverse(pd);
-      span.assign(S.n1, 0);
-      E.assign((size_t)S.n1 * sd * sd, 0.0);
-      std::vector<double> B((size_t)sd * sd);
-      for (int ix = 0; ix < S.n1; ++ix) {
-        span[ix] = find_span(kn, pd, (ix + 0.5) * S.h);
-        for (int a = 0; a < sd; ++a) {
-          const double u = pd ? double(a) / pd : 0.0;
-          span_basis(kn, pd, span[ix], (ix + u) * S.h, &B[(size_t)a * sd], nullptr);
-        }
-        for (int a = 0; a < sd; ++a)
-          for (int i = 0; i < sd; ++i) {
-            double acc = 0;
-            for (int k = 0; k < sd; ++k) acc += Vi[a * sd + k] * B[(size_t)k * sd + i];
-            E[((size_t)ix * sd + a) * sd + i] = acc;
-          }
-      }
-    };
-    std::vector<int> span1, span2;
-    std::vector<double> E1, E2;
-    factors(P.kn1, P.p1, span1, E1);
-    factors(P.kn2, P.p2, span2, E2);
-    std::vector<double> T((size_t)s1 * s2 * 4);
-    for (int ix = 0; ix < S.n1; ++ix)
-      for (int iy = 0; iy < S.n1; ++iy) {
-        const int id = (j * S.n1 + ix) * S.n1 + iy;
-        const int i0 = span1[ix] - P.p1, j0 = span2[iy] - P.p2;
-        const double *e1 = &E1[(size_t)ix * s1 * s1], *e2 = &E2[(size_t)iy * s2 * s2];
-        // T[i][b] = sum_jj E2[b][jj] CP[i0 + i][j0 + jj]
-        for (int i = 0; i < s1; ++i)
-          for (int b = 0; b < s2; ++b)
-            for (int c = 0; c < 4; ++c) {
-              double acc = 0;
-              for (int jj = 0; jj < s2; ++jj) acc += e2[b * s2 + jj] * P.hw[((i0 + i) * P.k2 + (j0 + jj)) * 4 + c];
-              T[(i * s2 + b) * 4 + c] = acc;
-            }
-        double *out = &S.ebez[S.eoff[id]];
-        for (int a = 0; a < s1; ++a)
-          for (int b = 0; b < s2; ++b)
-            for (int c = 0; c < 4; ++c) {
-              double acc = 0;
-              for (int i = 0; i < s1; ++i) acc += e1[a * s1 + i] * T[(i * s2 + b) * 4 + c];
-              out[(a * s2 + b) * 4 + c] = acc;
-            }
-        const int ca[4] = {0, P.p1, 0, P.p1}, cb[4] = {0, 0, P.p2, P.p2};
-        for (int c = 0; c < 4; ++c) {
-          const double *hw = &out[(ca[c] * s2 + cb[c]) * 4];
-          for (int k = 0; k < 3; ++k) S.corners[(id * 4 + c) * 3 + k] = hw[k] / hw[3];
-        }
-      }
-  }
-  S.scale = 0;
-  for (double v : S.corners) S.scale = std::max(S.scale, std::fabs(v));
 
   // --- quadrature ---
   gauss_legendre01(S.ng, S.gx, S.gw);
@@ -528,122 +564,127 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   }
 
   // --- touching element pairs ---
-  const double tol = 1e-10 * S.scale;
-  // sh: (e E + f, bitmask of e's corners shared with f) for every ordered pair e != f, sorted.  Element
-  // corners coincide by construction at the grid vertices of a patch, so only the distinct vertices are
-  // compared (coincidences across patch boundaries and of degenerate parametrisations): cells of a grid
-  // much coarser than the tolerance, sorted, searched in every cell within the tolerance; coinciding vertices
-  // are merged (union-find) and every pair of corners at one merged vertex marks its two elements.
-  std::vector<std::pair<long long, int>> sh;
-  std::vector<long> crep(4L * S.E);  // merged vertex of each element corner 4 e + c
-  {
-    const int nv1 = S.n1 + 1;
-    const long NV = (long)np * nv1 * nv1;
-    std::vector<double> vx(3 * NV);
-    for (int j = 0; j < np; ++j)
-      for (int a = 0; a < nv1; ++a)
-        for (int b = 0; b < nv1; ++b) {
-          const int ix = std::min(a, S.n1 - 1), iy = std::min(b, S.n1 - 1), c = (a - ix) + 2 * (b - iy);
-          const long e = ((long)j * S.n1 + ix) * S.n1 + iy, v = ((long)j * nv1 + a) * nv1 + b;
-          for (int k = 0; k < 3; ++k) vx[3 * v + k] = S.corners[(e * 4 + c) * 3 + k];
+  if (hit) {
+    S.touch = hit->touch;
+  } else {
+    const double tol = 1e-10 * S.scale;
+    // sh: (e E + f, bitmask of e's corners shared with f) for every ordered pair e != f, sorted.  Element
+    // corners coincide by construction at the grid vertices of a patch, so only the distinct vertices are
+    // compared (coincidences across patch boundaries and of degenerate parametrisations): cells of a grid
+    // much coarser than the tolerance, sorted, searched in every cell within the tolerance; coinciding vertices
+    // are merged (union-find) and every pair of corners at one merged vertex marks its two elements.
+    std::vector<std::pair<long long, int>> sh;
+    std::vector<long> crep(4L * S.E);  // merged vertex of each element corner 4 e + c
+    {
+      const int nv1 = S.n1 + 1;
+      const long NV = (long)np * nv1 * nv1;
+      std::vector<double> vx(3 * NV);
+      for (int j = 0; j < np; ++j)
+        for (int a = 0; a < nv1; ++a)
+          for (int b = 0; b < nv1; ++b) {
+            const int ix = std::min(a, S.n1 - 1), iy = std::min(b, S.n1 - 1), c = (a - ix) + 2 * (b - iy);
+            const long e = ((long)j * S.n1 + ix) * S.n1 + iy, v = ((long)j * nv1 + a) * nv1 + b;
+            for (int k = 0; k < 3; ++k) vx[3 * v + k] = S.corners[(e * 4 + c) * 3 + k];
+          }
+      const double cell = std::max(1e-7 * S.scale, 1e-300);
+      struct Key {
+        long long a, b, c;
+        long id;
+        bool operator<(const Key &o) const {
+          return a != o.a ? a < o.a : b != o.b ? b < o.b : c != o.c ? c < o.c : id < o.id;
         }
-    const double cell = std::max(1e-7 * S.scale, 1e-300);
-    struct Key {
-      long long a, b, c;
-      long id;
-      bool operator<(const Key &o) const {
-        return a != o.a ? a < o.a : b != o.b ? b < o.b : c != o.c ? c < o.c : id < o.id;
+      };
+      auto ci = [&](double x) { return (long long)std::floor(x / cell); };
+      std::vector<Key> keys(NV);
+      for (long v = 0; v < NV; ++v) keys[v] = {ci(vx[3 * v]), ci(vx[3 * v + 1]), ci(vx[3 * v + 2]), v};
+      std::sort(keys.begin(), keys.end());
+      std::vector<long> parent(NV);
+      std::iota(parent.begin(), parent.end(), 0L);
+      auto find = [&](long x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+      };
+      for (long v = 0; v < NV; ++v) {
+        // the cells a point within tol of this vertex can lie in (almost always the vertex's own)
+        const double *x = &vx[3 * v];
+        for (long long i = ci(x[0] - tol); i <= ci(x[0] + tol); ++i)
+          for (long long jj = ci(x[1] - tol); jj <= ci(x[1] + tol); ++jj)
+            for (long long k = ci(x[2] - tol); k <= ci(x[2] + tol); ++k) {
+              auto it = std::lower_bound(keys.begin(), keys.end(), Key{i, jj, k, -1});
+              for (; it != keys.end() && it->a == i && it->b == jj && it->c == k; ++it)
+                if (it->id != v && dist3(&vx[3 * v], &vx[3 * it->id]) <= tol) parent[find(it->id)] = find(v);
+            }
       }
-    };
-    auto ci = [&](double x) { return (long long)std::floor(x / cell); };
-    std::vector<Key> keys(NV);
-    for (long v = 0; v < NV; ++v) keys[v] = {ci(vx[3 * v]), ci(vx[3 * v + 1]), ci(vx[3 * v + 2]), v};
-    std::sort(keys.begin(), keys.end());
-    std::vector<long> parent(NV);
-    std::iota(parent.begin(), parent.end(), 0L);
-    auto find = [&](long x) {
-      while (parent[x] != x) x = parent[x] = parent[parent[x]];
-      return x;
-    };
-    for (long v = 0; v < NV; ++v) {
-      // the cells a point within tol of this vertex can lie in (almost always the vertex's own)
-      const double *x = &vx[3 * v];
-      for (long long i = ci(x[0] - tol); i <= ci(x[0] + tol); ++i)
-        for (long long jj = ci(x[1] - tol); jj <= ci(x[1] + tol); ++jj)
-          for (long long k = ci(x[2] - tol); k <= ci(x[2] + tol); ++k) {
-            auto it = std::lower_bound(keys.begin(), keys.end(), Key{i, jj, k, -1});
-            for (; it != keys.end() && it->a == i && it->b == jj && it->c == k; ++it)
-              if (it->id != v && dist3(&vx[3 * v], &vx[3 * it->id]) <= tol) parent[find(it->id)] = find(v);
+      std::vector<std::pair<long, int>> inc(4L * S.E);  // (merged vertex, corner index 4 e + c)
+      for (int j = 0; j < np; ++j)
+        for (int ix = 0; ix < S.n1; ++ix)
+          for (int iy = 0; iy < S.n1; ++iy) {
+            const int e = (j * S.n1 + ix) * S.n1 + iy;
+            for (int c = 0; c < 4; ++c) {
+              crep[4L * e + c] = find(((long)j * nv1 + ix + (c & 1)) * nv1 + iy + (c >> 1));
+              inc[4L * e + c] = {crep[4L * e + c], 4 * e + c};
+            }
           }
+      std::sort(inc.begin(), inc.end());
+      // per element: its touching neighbours f with the mask of its corners shared with f
+      constexpr int NBMAX = 64;
+      std::vector<int> nbf((size_t)S.E * NBMAX), nbm((size_t)S.E * NBMAX), nbc(S.E, 0);
+      for (size_t g0 = 0; g0 < inc.size();) {
+        size_t g1 = g0;
+        while (g1 < inc.size() && inc[g1].first == inc[g0].first) ++g1;
+        for (size_t x = g0; x < g1; ++x)
+          for (size_t y = g0; y < g1; ++y) {
+            const int e = inc[x].second / 4, f = inc[y].second / 4;
+            if (e == f) continue;
+            int *lf = &nbf[(size_t)e * NBMAX], *lm = &nbm[(size_t)e * NBMAX];
+            int k = 0;
+            while (k < nbc[e] && lf[k] != f) ++k;
+            if (k == nbc[e]) {
+              if (k == NBMAX) fail(IGABEM_EINVAL, "an element touches more than 64 others");
+              lf[k] = f;
+              lm[k] = 0;
+              ++nbc[e];
+            }
+            lm[k] |= 1 << (inc[x].second % 4);
+          }
+        g0 = g1;
+      }
+      for (int e = 0; e < S.E; ++e) {
+        const size_t b0 = sh.size();
+        for (int k = 0; k < nbc[e]; ++k)
+          sh.push_back({(long long)e * S.E + nbf[(size_t)e * NBMAX + k], nbm[(size_t)e * NBMAX + k]});
+        std::sort(sh.begin() + b0, sh.end());
+      }
     }
-    std::vector<std::pair<long, int>> inc(4L * S.E);  // (merged vertex, corner index 4 e + c)
-    for (int j = 0; j < np; ++j)
-      for (int ix = 0; ix < S.n1; ++ix)
-        for (int iy = 0; iy < S.n1; ++iy) {
-          const int e = (j * S.n1 + ix) * S.n1 + iy;
-          for (int c = 0; c < 4; ++c) {
-            crep[4L * e + c] = find(((long)j * nv1 + ix + (c & 1)) * nv1 + iy + (c >> 1));
-            inc[4L * e + c] = {crep[4L * e + c], 4 * e + c};
-          }
-        }
-    std::sort(inc.begin(), inc.end());
-    // per element: its touching neighbours f with the mask of its corners shared with f
-    constexpr int NBMAX = 64;
-    std::vector<int> nbf((size_t)S.E * NBMAX), nbm((size_t)S.E * NBMAX), nbc(S.E, 0);
-    for (size_t g0 = 0; g0 < inc.size();) {
-      size_t g1 = g0;
-      while (g1 < inc.size() && inc[g1].first == inc[g0].first) ++g1;
-      for (size_t x = g0; x < g1; ++x)
-        for (size_t y = g0; y < g1; ++y) {
-          const int e = inc[x].second / 4, f = inc[y].second / 4;
-          if (e == f) continue;
-          int *lf = &nbf[(size_t)e * NBMAX], *lm = &nbm[(size_t)e * NBMAX];
-          int k = 0;
-          while (k < nbc[e] && lf[k] != f) ++k;
-          if (k == nbc[e]) {
-            if (k == NBMAX) fail(IGABEM_EINVAL, "an element touches more than 64 others");
-            lf[k] = f;
-            lm[k] = 0;
-            ++nbc[e];
-          }
-          lm[k] |= 1 << (inc[x].second % 4);
-        }
-      g0 = g1;
-    }
+    S.touch.clear();
     for (int e = 0; e < S.E; ++e) {
-      const size_t b0 = sh.size();
-      for (int k = 0; k < nbc[e]; ++k)
-        sh.push_back({(long long)e * S.E + nbf[(size_t)e * NBMAX + k], nbm[(size_t)e * NBMAX + k]});
-      std::sort(sh.begin() + b0, sh.end());
+      S.touch.insert(S.touch.end(), {e, e, 0, 0, 0});
     }
-  }
-  S.touch.clear();
-  for (int e = 0; e < S.E; ++e) {
-    S.touch.insert(S.touch.end(), {e, e, 0, 0, 0});
-  }
-  for (auto &kv : sh) {
-    int e = int(kv.first / S.E), f = int(kv.first % S.E);
-    int nsh = __builtin_popcount(kv.second);
-    if (nsh > 2) fail(IGABEM_EINVAL, "two elements share more than an edge");
-    int kind = nsh == 2 ? 2 : 1;
-    int te = -1, tf = -1;
-    for (int a = 0; a < 8 && te < 0; ++a)
-      for (int b = 0; b < 8; ++b) {
-        // corners coincide iff they were merged into one vertex above
-        int u, v;
-        d4(a, 0, 0, u, v); const long re0 = crep[e * 4L + u + 2 * v];
-        d4(b, 0, 0, u, v); const long rf0 = crep[f * 4L + u + 2 * v];
-        if (re0 != rf0) continue;
-        if (kind == 2) {
-          d4(a, 0, 1, u, v); const long re1 = crep[e * 4L + u + 2 * v];
-          d4(b, 0, 1, u, v); const long rf1 = crep[f * 4L + u + 2 * v];
-          if (re1 != rf1) continue;
+    for (auto &kv : sh) {
+      int e = int(kv.first / S.E), f = int(kv.first % S.E);
+      int nsh = __builtin_popcount(kv.second);
+      if (nsh > 2) fail(IGABEM_EINVAL, "two elements share more than an edge");
+      int kind = nsh == 2 ? 2 : 1;
+      int te = -1, tf = -1;
+      for (int a = 0; a < 8 && te < 0; ++a)
+        for (int b = 0; b < 8; ++b) {
+          // corners coincide iff they were merged into one vertex above
+          int u, v;
+          d4(a, 0, 0, u, v); const long re0 = crep[e * 4L + u + 2 * v];
+          d4(b, 0, 0, u, v); const long rf0 = crep[f * 4L + u + 2 * v];
+          if (re0 != rf0) continue;
+          if (kind == 2) {
+            d4(a, 0, 1, u, v); const long re1 = crep[e * 4L + u + 2 * v];
+            d4(b, 0, 1, u, v); const long rf1 = crep[f * 4L + u + 2 * v];
+            if (re1 != rf1) continue;
+          }
+          te = a; tf = b;
+          break;
         }
-        te = a; tf = b;
-        break;
-      }
-    if (te < 0) fail(IGABEM_EINVAL, "touching pair without a canonical position");
-    S.touch.insert(S.touch.end(), {e, f, kind, te, tf});
+      if (te < 0) fail(IGABEM_EINVAL, "touching pair without a canonical position");
+      S.touch.insert(S.touch.end(), {e, f, kind, te, tf});
+    }
+    if (fill) fill->touch = S.touch;
   }
 
   // --- continuous space: glue patch-wise functions with coinciding Greville anchors ---
@@ -700,14 +741,20 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   S.nL1 = (1 << S.b) + p;
   S.nL = S.nL1 * S.nL1;
   S.lev.assign(S.L + 1, TreeLevel{});
+  const bool balls_hit = hit && hit->L >= S.L;
   for (int l = 0; l <= S.L; ++l) {
     TreeLevel &T = S.lev[l];
     int nl = 1 << l;
     T.n = np * nl * nl;
+    if (balls_hit) {
+      T.center = hit->center[l];
+      T.radius = hit->radius[l];
+      continue;
+    }
     T.center.assign(3L * T.n, 0.0);
     T.radius.assign(T.n, 0.0);
-    for (int j = 0; j < np; ++j)
-      for (int cx = 0; cx < nl; ++cx)
+    parallel_for((long)np * nl, [&](long jc) {
+      const int j = (int)(jc / nl), cx = (int)(jc % nl);
         for (int cy = 0; cy < nl; ++cy) {
           int t = (j * nl + cx) * nl + cy;
           double *c = &T.center[3L * t];
@@ -721,6 +768,14 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
             }
           T.radius[t] = r;
         }
+    });
+  }
+  if (fill && !hit) {
+    fill->L = S.L;
+    for (int l = 0; l <= S.L; ++l) {
+      fill->center.push_back(S.lev[l].center);
+      fill->radius.push_back(S.lev[l].radius);
+    }
   }
   // interpolation points and kappa cap per level (level-adaptive when q_max > cheb_q): the bound
   // eps(q, w) = w^q / (2^(q-1) q!) of q-point Chebyshev interpolation of exp(i w t) on [-1,1]; the
@@ -774,19 +829,31 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     std::vector<std::pair<int, int>> far;
     nxt.clear();
     int nl = 1 << l, nc = 2 * nl;
-    for (auto [t, s] : cand) {
-      if (admissible(l, t, s)) {
-        far.push_back({t, s});
-      } else if (l == S.L) {
-        near.push_back({t, s});
-      } else {
-        int jt = t / (nl * nl), xt = (t / nl) % nl, yt = t % nl;
-        int js = s / (nl * nl), xs = (s / nl) % nl, ys = s % nl;
-        for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b)
-            nxt.push_back({(jt * nc + 2 * xt + (a >> 1)) * nc + 2 * yt + (a & 1),
-                           (js * nc + 2 * xs + (b >> 1)) * nc + 2 * ys + (b & 1)});
+    // the candidates in chunks on host threads (the CSR lists below do not depend on the order)
+    const long nch = std::min<long>(64, ((long)cand.size() + 4095) / 4096);
+    std::vector<std::vector<std::pair<int, int>>> cf(nch), cn(nch), cx(nch);
+    parallel_for(nch, [&](long c) {
+      const size_t i0 = cand.size() * c / nch, i1 = cand.size() * (c + 1) / nch;
+      for (size_t i = i0; i < i1; ++i) {
+        const int t = cand[i].first, s = cand[i].second;
+        if (admissible(l, t, s)) {
+          cf[c].push_back({t, s});
+        } else if (l == S.L) {
+          cn[c].push_back({t, s});
+        } else {
+          int jt = t / (nl * nl), xt = (t / nl) % nl, yt = t % nl;
+          int js = s / (nl * nl), xs = (s / nl) % nl, ys = s % nl;
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+              cx[c].push_back({(jt * nc + 2 * xt + (a >> 1)) * nc + 2 * yt + (a & 1),
+                               (js * nc + 2 * xs + (b >> 1)) * nc + 2 * ys + (b & 1)});
+        }
       }
+    });
+    for (long c = 0; c < nch; ++c) {
+      far.insert(far.end(), cf[c].begin(), cf[c].end());
+      near.insert(near.end(), cn[c].begin(), cn[c].end());
+      nxt.insert(nxt.end(), cx[c].begin(), cx[c].end());
     }
     TreeLevel &T = S.lev[l];
     csr_of_pairs(far, T.n, T.far_ptr, T.far_src);
@@ -799,7 +866,10 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
 
   // touching pair -> near block
   int npt = (int)S.touch.size() / 5;
-  {  // neighbour lists of the touching pairs (both directions), for the regular near-field kernel
+  if (hit) {
+    S.nbr = hit->nbr;
+    S.nbr_w = hit->nbr_w;
+  } else {  // neighbour lists of the touching pairs (both directions), for the regular near-field kernel
     std::vector<std::vector<int>> nb(S.E);
     for (int i = 0; i < npt; ++i) {
       const int e = S.touch[5 * i], f = S.touch[5 * i + 1];
@@ -812,6 +882,10 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     S.nbr.assign((size_t)S.E * S.nbr_w, -1);
     for (int e = 0; e < S.E; ++e)
       for (size_t c = 0; c < nb[e].size(); ++c) S.nbr[(size_t)e * S.nbr_w + c] = nb[e][c];
+  }
+  if (fill && fill->m >= 0) {
+    fill->nbr = S.nbr;
+    fill->nbr_w = S.nbr_w;
   }
   S.touch_blk.resize(npt);
   const int nlL = 1 << S.L, bsh = S.b;

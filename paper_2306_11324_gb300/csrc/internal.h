@@ -6,6 +6,8 @@
 #include <cstddef>
 #include <cstdint>
 #include <functional>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -178,7 +180,24 @@ struct HostSetup {
   std::vector<double> LG1;             // [2^b][ng][q]: leaf Lagrange at Gauss points
 };
 
-void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S);
+// Host set-up products that depend on the geometry and the level m alone (and the cluster balls on the
+// leaf level m - b): kept with the geometry, so that problems on it at other wavenumbers, precisions or
+// right-hand-side counts (a frequency sweep, repeated serving requests) skip their construction.
+struct GeoCache {
+  int m = -1, L = -1;
+  std::vector<int> edeg;
+  std::vector<long> eoff;
+  std::vector<double> ebez, corners;
+  double scale = 0;
+  std::vector<int> touch, nbr;
+  int nbr_w = 0;
+  std::vector<std::vector<double>> center, radius;  // cluster balls on levels 0..L
+};
+
+// hit: products of an earlier call for the same geometry and level m (or nullptr); fill: receives this
+// call's products when hit does not apply (or nullptr)
+void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, HostSetup &S,
+                 const GeoCache *hit = nullptr, GeoCache *fill = nullptr);
 
 // Gauss-Legendre rule on [0,1] (Newton iteration on P_n).
 void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w);
@@ -197,6 +216,8 @@ struct igabem_ctx {
 struct igabem_geom {
   igabem_ctx *ctx = nullptr;
   std::vector<igabem::Patch> patches;
+  std::mutex cache_mu;
+  std::shared_ptr<const igabem::GeoCache> cache;  // the latest level's host set-up products
 };
 
 namespace igabem {

@@ -340,3 +340,27 @@ def test_stored_coupling_blocks_with_level_adaptive_q(prec):
     tol = FP64_TOL if prec == B.FP64 else MIXED_MATVEC_TOL
     assert np.abs(y3[rows] - ref3).max() / np.abs(ref3).max() < tol
     B.igabem_problem_destroy(prob)
+
+
+def test_set_up_reused_across_wavenumbers_equals_a_fresh_set_up():
+    """Problems on one geometry at the same level share its wavenumber-independent host set-up (element
+    nets, touching pairs, cluster balls): the product of a problem whose set-up came from that cache
+    equals the product of the same problem on a fresh geometry object."""
+    patches = inputs.deformed_sphere_patches(spans=4)
+    kw = dict(level_m=4, degree_p=2, eta_cfie=1.0, cheb_q=6, leaf_offset=2, eta_adm=0.5, kappa_cap=4.0, q_max=9,
+              precision=B.FP64)
+    g = B.igabem_geometry_create(G.ctx(), patches)
+    p1 = B.igabem_problem_create(g, B.igabem_default_options(kappa=3.0, **kw))      # fills the cache
+    p2 = B.igabem_problem_create(g, B.igabem_default_options(kappa=5.0, **kw))      # reuses it
+    g2 = B.igabem_geometry_create(G.ctx(), patches)
+    p3 = B.igabem_problem_create(g2, B.igabem_default_options(kappa=5.0, **kw))     # fresh
+    i2, i3 = B.igabem_problem_info(p2), B.igabem_problem_info(p3)
+    for k in ("n_dofs", "n_far_pairs", "n_near_pairs", "n_touching_pairs", "n_singular_points", "level_q"):
+        assert i2[k] == i3[k], k
+    x = inputs.random_complex(i2["n_dofs"], seed=77, cols=2)
+    y2, y3 = B.igabem_matvec(p2, x), B.igabem_matvec(p3, x)
+    assert G.rel(y2, y3) < 1e-13
+    for p in (p1, p2, p3):
+        B.igabem_problem_destroy(p)
+    B.igabem_geometry_destroy(g)
+    B.igabem_geometry_destroy(g2)

@@ -508,26 +508,33 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
   rule_identical(sx, sw, S.r_id);
   rule_edge(sx, sw, S.r_edge);
   rule_vertex(sx, sw, S.r_vert);
-  // chunk of the singular kernel: whole groups of ns^2 points, at most 128 (one point per thread), as many
-  // as keep its shared memory within 110 KB (two blocks per SM), else the smallest that fits at all
+  // chunk of the singular kernel: whole groups of ns^2 points, at most 128 (one point per thread)
   {
     const int g = S.ns * S.ns <= 128 ? S.ns * S.ns : 128;
     int pg1 = 1;
     for (int v : S.edeg) pg1 = std::max(pg1, v + 1);
+    // the largest chunk whose shared memory lets four blocks share an SM (the FP64 chains of the kernel
+    // need the warps), else two, else the smallest chunk that fits at all
+    std::vector<std::pair<int, double>> cands;  // (chunk, bytes)
+    for (int ch = (128 / g) * g; ch >= g; ch -= g) {
+      int nv = 0, nd = 0;
+      for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, ch, nv, nd);
+      cands.push_back({ch, 8.0 * sing_layout(ch, S.nloc, S.hard, nv, nd, pg1).total});
+    }
     int chosen = 0;
-    for (int ch = (128 / g) * g; ch >= g && !chosen; ch -= g)
-      for (double lim : {110.0 * 1024, 227.0 * 1024}) {
-        int nv = 0, nd = 0;
-        for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, ch, nv, nd);
-        const double bytes = 8.0 * sing_layout(ch, S.nloc, S.hard, nv, nd, pg1).total;
-        if (bytes <= lim && (lim < 200 * 1024 || ch == g)) {
-          S.sing_ch = ch;
-          S.sing_nv = nv;
-          S.sing_nd = nd;
-          chosen = 1;
+    for (double lim : {55.0 * 1024, 112.0 * 1024, 227.0 * 1024}) {
+      for (const auto &c : cands)
+        if (c.second <= lim && (lim < 200 * 1024 || c.first == g)) {
+          chosen = c.first;
           break;
         }
-      }
+      if (chosen) break;
+    }
+    if (chosen) {
+      S.sing_ch = chosen;
+      S.sing_nv = S.sing_nd = 0;
+      for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, chosen, S.sing_nv, S.sing_nd);
+    }
     if (!chosen) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
   }
 

@@ -347,21 +347,33 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_m2l_stored(M2LArgs A, int cr
           __syncwarp();                  // ... and every lane's
           const C2<T> *slot = ring + (b % D) * ntype * 64;
           const C2<T> s0a = slot[lane], s0b = slot[lane + 32];
+          // the staged x_s values of row b (broadcast to the warp), two columns per 16-byte load in FP32
+          C2<T> xv[NCR];
+          if constexpr (F32 && NCR % 2 == 0) {
+            const float4 *xp = reinterpret_cast<const float4 *>(xs + b * NCR);
+#pragma unroll
+            for (int c = 0; c < NCR / 2; ++c) {
+              const float4 v = xp[c];
+              xv[2 * c] = c2((T)v.x, (T)v.y);
+              xv[2 * c + 1] = c2((T)v.z, (T)v.w);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < NCR; ++c) xv[c] = xs[b * NCR + c];
+          }
           if (!HARD) {
 #pragma unroll
             for (int c = 0; c < NCR; ++c) {
-              const C2<T> xv = xs[b * NCR + c];
-              p0[c] = fma2(s0a, xv, p0[c]);
-              p1[c] = fma2(s0b, xv, p1[c]);
+              p0[c] = fma2(s0a, xv[c], p0[c]);
+              p1[c] = fma2(s0b, xv[c], p1[c]);
             }
           } else {
             const C2<T> s1a = slot[64 + lane], s1b = slot[64 + lane + 32];
 #pragma unroll
             for (int c = 0; c < NCR; ++c) {
-              const C2<T> xv = xs[b * NCR + c];
               const bool k0 = (cr0 + c) / A.R == 0;
-              p0[c] = fma2(k0 ? s0a : s1a, xv, p0[c]);
-              p1[c] = fma2(k0 ? s0b : s1b, xv, p1[c]);
+              p0[c] = fma2(k0 ? s0a : s1a, xv[c], p0[c]);
+              p1[c] = fma2(k0 ? s0b : s1b, xv[c], p1[c]);
             }
           }
           // the slot of row b - 1 is free (every lane passed this iteration's __syncwarp)

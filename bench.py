@@ -92,6 +92,14 @@ FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 
 
+def hbm_peak_gbs():
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"])
+    return 6800.0
+
+
 def singular_flops(info, p, hard, pg=4):
     """FP64 operations of the touching pairs' quadrature (the model behind the roofline of
     k_near_singular), from the counts the library reports.  Per element net contracted along its second
@@ -766,6 +774,25 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
     m2l_flops = sum(f * q ** 4 * (FLOPS_PER_SAMPLE[hard] * (2 if hard else 1) + FLOPS_PER_MAC * C * R)
                     for f, q in zip(far_by_level, qs))
     m2l_ach = m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else 0.0
+    stored = wl.get("m2l_stored", {}).get(args.precision, 0)
+    if stored:
+        # the stored blocks are read once per product: q^4 FP32 complex entries per far pair (x 2 hard)
+        ebytes = 8 if args.precision != "fp64" else 16
+        m2l_bytes = sum(f * q ** 4 for f, q in zip(far_by_level, qs)) * (2 if hard else 1) * ebytes
+        hbm = hbm_peak_gbs()
+        m2l_gbs = m2l_bytes / (m2l_ms / 1e3) / 1e9 if m2l_ms > 0 else 0.0
+        m2l_roof = {"kernel": "k_m2l_stored<float>", "bound": "hbm", "achieved": m2l_gbs, "unit": "GB/s",
+                    "peak": hbm, "frac": m2l_gbs / hbm if hbm else None,
+                    "algorithmic_bytes_per_matvec": m2l_bytes, "avg_ms_per_matvec": m2l_ms,
+                    "peak_source": "measured copy bandwidth, MEASURED_PEAKS.json"}
+    else:
+        m2l_roof = {"kernel": "k_m2l_rows<float> / k_m2l_gemm<float>", "achieved": m2l_ach, "unit": "TFLOP/s",
+                    "peak": peaks["fp32_tflops"], "frac": m2l_ach / peaks["fp32_tflops"],
+                    "xu_frac": (m2l_samples / (peaks["sincosf_gops"] * 1e9) + m2l_samples / (peaks["rsqrtf_gops"] * 1e9))
+                    / (m2l_ms / 1e3) if m2l_ms > 0 else None,
+                    "algorithmic_flops_per_matvec": m2l_flops, "avg_ms_per_matvec": m2l_ms,
+                    "node_pairs_per_matvec": m2l_samples,
+                    "peak_source": "measured FP32 FMA rate (igabem_measure_peaks, this run)"}
     roofline = {"bound": "alu", "kernel": "k_near_singular (FP64)", "achieved": sing_ach,
                 "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": sing_ach / peaks["fp64_tflops"],
                 "traffic": None,
@@ -775,13 +802,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
                 "singular_groups": info["n_singular_groups"],
-                "m2l": {"kernel": "k_m2l_rows<float> / k_m2l_gemm<float>", "achieved": m2l_ach, "unit": "TFLOP/s",
-                        "peak": peaks["fp32_tflops"], "frac": m2l_ach / peaks["fp32_tflops"],
-                        "xu_frac": (m2l_samples / (peaks["sincosf_gops"] * 1e9) + m2l_samples / (peaks["rsqrtf_gops"] * 1e9))
-                        / (m2l_ms / 1e3) if m2l_ms > 0 else None,
-                        "algorithmic_flops_per_matvec": m2l_flops, "avg_ms_per_matvec": m2l_ms,
-                        "node_pairs_per_matvec": m2l_samples,
-                        "peak_source": "measured FP32 FMA rate (igabem_measure_peaks, this run)"}}
+                "m2l": m2l_roof}}
     lat = sorted(step_ms)
     value = R * args.steps * world / (total_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

@@ -513,8 +513,8 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
     const int g = S.ns * S.ns <= 128 ? S.ns * S.ns : 128;
     int pg1 = 1;
     for (int v : S.edeg) pg1 = std::max(pg1, v + 1);
-    // the largest chunk whose shared memory lets four blocks share an SM (the FP64 chains of the kernel
-    // need the warps), else two, else the smallest chunk that fits at all
+    // the largest chunk whose shared memory lets two blocks share an SM (larger chunks share more element
+    // geometry and form fewer groups), else the smallest chunk that fits at all
     std::vector<std::pair<int, double>> cands;  // (chunk, bytes)
     for (int ch = (128 / g) * g; ch >= g; ch -= g) {
       int nv = 0, nd = 0;
@@ -522,7 +522,7 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
       cands.push_back({ch, 8.0 * sing_layout(ch, S.nloc, S.hard, nv, nd, pg1).total});
     }
     int chosen = 0;
-    for (double lim : {55.0 * 1024, 112.0 * 1024, 227.0 * 1024}) {
+    for (double lim : {112.0 * 1024, 227.0 * 1024}) {
       for (const auto &c : cands)
         if (c.second <= lim && (lim < 200 * 1024 || c.first == g)) {
           chosen = c.first;

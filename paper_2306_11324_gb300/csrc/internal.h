@@ -85,41 +85,31 @@ struct Rule4 {  // a rule on [0,1]^4 for touching element pairs, canonical posit
 // bytes of one chunk header of Rule4::share
 inline int sing_share_header(int ch) { return 8 + 10 * ch; }
 
-// Shared-memory layout of the singular kernel, offsets in doubles: the union of the per-point and
-// per-group arrays with the geometry column partials, the distinct points' geometry and basis values,
-// the two element nets.
+// Shared-memory layout of the singular kernel, offsets in doubles.  Three regions, each reused by
+// steps that do not overlap in time: (A) the geometry column partials, then the per-point kernel values
+// and basis values; (B) the distinct points' geometry, then the group sums; (C) the grouped side's basis
+// values (written with the geometry, read by the accumulation); then the two element nets.
 struct SingLayout {
   int s3, psi, cur, T, T2, U, geo, phiG, curG, nets, total;
 };
 inline SingLayout sing_layout(int ch, int nloc, bool hard, int nv, int nd, int pg1) {
   auto al = [](int x) { return (x + 1) & ~1; };  // double2 alignment
+  auto mx = [](int a, int b) { return a > b ? a : b; };
   const int h3 = hard ? 3 : 0;
   SingLayout L;
-  int o = 0;
-  L.s3 = 0;
-  o = 6 * ch;                      // w k(x,y), w k(y,x), w gc per point (complex)
-  L.psi = o;
-  o += ch * nloc;                  // basis values on the side that is not grouped
-  L.cur = o;
-  o += h3 * ch * nloc;             // and their curls
-  o = al(o);
-  L.T = o;
-  o += 2 * nd * nloc;              // group sums of w k(x,y) times those basis values (complex)
-  L.T2 = o;
-  o += 2 * nd * nloc;              // the same with w k(y,x)
-  L.U = o;
-  o += 2 * h3 * nd * nloc;         // group sums of w gc times the curls (complex)
-  const int col = 2 * nv * pg1 * 8;
-  o = al(o > col ? o : col);
-  L.geo = o;
-  o += 2 * nd * 13;
-  L.phiG = o;
-  o += nd * nloc;
-  L.curG = o;
-  o += h3 * nd * nloc;
-  L.nets = o;
-  o += 8 * 49;
-  L.total = o;
+  L.s3 = 0;                        // w k(x,y), w k(y,x), w gc per point (complex)
+  L.psi = 6 * ch;                  // basis values on the side that is not grouped
+  L.cur = L.psi + ch * nloc;       // and their curls
+  const int endA = al(mx(L.cur + h3 * ch * nloc, 2 * nv * pg1 * 8));
+  L.geo = endA;                    // x, d_s x, d_t x, n, |n| of the distinct points
+  L.T = endA;                      // group sums of w k(x,y) times the basis values (complex)
+  L.T2 = L.T + 2 * nd * nloc;      // the same with w k(y,x)
+  L.U = L.T2 + 2 * nd * nloc;      // group sums of w gc times the curls (complex)
+  const int endB = al(mx(L.geo + 2 * nd * 13, L.U + 2 * h3 * nd * nloc));
+  L.phiG = endB;                   // basis values (and curls) of the grouped side's distinct points
+  L.curG = L.phiG + nd * nloc;
+  L.nets = L.curG + h3 * nd * nloc;
+  L.total = L.nets + 8 * 49;
   return L;
 }
 

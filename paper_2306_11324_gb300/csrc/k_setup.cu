@@ -390,6 +390,177 @@ __global__ void k_near_regular_t(NearArgs A, int smem_block) {
   }
 }
 
+// per-warp scratch of k_near_regular_f, in elements of its precision (offsets rounded to pairs)
+__host__ __device__ inline int near_fused_scratch(int nq, int nl, bool hard) {
+  auto al = [](int x) { return (x + 1) & ~1; };
+  const int base = al(2 * nq * 7) + al(2 * nq * nl) + (hard ? al(6 * nq * nl) : 0);
+  return base + 2 * nq * nl + (hard ? 6 * nq * nl : 0);
+}
+
+// Regular element pairs with the kernel samples folded into the first contraction in registers:
+// lane (q, half) of a warp evaluates the samples of target Gauss point q against every other source
+// point (half selects which) and accumulates Tm[q][l] = sum_r ks(q, r) psi_l(r) (sound-hard also
+// Tc[d][q][l] = sum_r gc(q, r) c_l,d(r)) without storing the samples; a shuffle adds the two halves.
+// The block entries then contract Tm with the test side's weighted basis values (and curls).  Same
+// sums as k_near_regular_t in another order; one block per near leaf pair, one warp per element pair.
+template <class T, int NL, bool HARD>
+__global__ void k_near_regular_f(NearArgs A, int smem_block) {
+  extern __shared__ __align__(16) unsigned char smf[];
+  using BA = typename std::conditional<sizeof(T) == 4, float2, double2>::type;  // leaf-pair block sums
+  using TV = BA;                                                                  // complex in precision T
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int nq = A.ng * A.ng, p1 = A.p + 1;
+  auto al = [](int x) { return (x + 1) & ~1; };
+  const int per = near_fused_scratch(nq, NL, HARD);
+  BA *Bs = reinterpret_cast<BA *>(smf);
+  T *base = reinterpret_cast<T *>(smf + (smem_block ? (size_t)A.nL * A.nL * sizeof(BA) : 0));
+  T *pts = base + warp * per;
+  T *phe = pts + al(2 * nq * 7), *phf = phe + nq * NL;
+  T *cue = phe + al(2 * nq * NL), *cuf = cue + 3 * nq * NL;
+  TV *Tm = reinterpret_cast<TV *>(phe + al(2 * nq * NL) + (HARD ? al(6 * nq * NL) : 0));
+  TV *Tc = Tm + nq * NL;
+  const int bid = blockIdx.x;
+  const int tgt = A.near_tgt[bid], src = A.near_src[bid];
+  const int nlL = 1 << A.L, ne1 = 1 << A.b;
+  const int jt = tgt / (nlL * nlL), cxt = (tgt / nlL) % nlL, cyt = tgt % nlL;
+  const int js = src / (nlL * nlL), cxs = (src / nlL) % nlL, cys = src % nlL;
+  double2 *Bg = A.blk + (size_t)bid * A.nL * A.nL;
+  if (smem_block) {
+    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) {
+      Bs[i].x = 0;
+      Bs[i].y = 0;
+    }
+    __syncthreads();
+  }
+  const T *tpts = static_cast<const T *>(A.tab_pts), *tphw = static_cast<const T *>(A.tab_phw),
+          *tcuw = static_cast<const T *>(A.tab_cuw);
+  const T h2 = (T)(A.h * A.h), h4 = h2 * h2, kap = (T)A.kappa, eta = (T)A.eta;
+  const int npair = ne1 * ne1 * ne1 * ne1;
+  for (int pr = warp; pr < npair; pr += nwarp) {
+    int et = pr / (ne1 * ne1), es = pr % (ne1 * ne1);
+    int ixe = cxt * ne1 + et / ne1, iye = cyt * ne1 + et % ne1;
+    int ixf = cxs * ne1 + es / ne1, iyf = cys * ne1 + es % ne1;
+    int e = (jt * A.n1 + ixe) * A.n1 + iye, f = (js * A.n1 + ixf) * A.n1 + iyf;
+    if (touching(A, e, f)) continue;  // warp-uniform
+    // stage the Gauss points (x, n~, a) and the weighted basis values / curls of both elements
+    for (int i = lane; i < 2 * nq * 7; i += 32) {
+      const int side = i / (nq * 7), r = i % (nq * 7);
+      pts[i] = tpts[(long)(side ? f : e) * nq * 7 + r];
+    }
+    for (int i = lane; i < 2 * nq * NL; i += 32) {
+      const int side = i / (nq * NL), r = i % (nq * NL);
+      const long el = side ? f : e;
+      (side ? phf : phe)[r] = tphw[el * nq * NL + r];
+      if (HARD)
+        for (int d = 0; d < 3; ++d) (side ? cuf : cue)[r * 3 + d] = tcuw[(el * nq * NL + r) * 3 + d];
+    }
+    __syncwarp();
+    // samples and the first contraction, 16 target points per pass
+    for (int q0 = 0; q0 < nq; q0 += 16) {
+      const int q = q0 + (lane & 15), half = lane >> 4;
+      TV tm[NL], tc[HARD ? 3 : 1][HARD ? NL : 1];
+#pragma unroll
+      for (int l = 0; l < NL; ++l) tm[l].x = tm[l].y = (T)0;
+      if constexpr (HARD) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int l = 0; l < NL; ++l) tc[d][l].x = tc[d][l].y = (T)0;
+      }
+      if (q < nq) {
+        T xr[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) xr[c] = pts[q * 7 + c];
+        for (int r = half; r < nq; r += 2) {
+          const T *Y = pts + (nq + r) * 7;
+          const PK<T> pk = cfie_kernel_t<T>(HARD, kap, eta, xr, xr + 3, xr[6], Y, Y + 3, Y[6]);
+          const T kx = pk.ksx * h4, ky = pk.ksy * h4;
+          const T *ph = phf + r * NL;
+#pragma unroll
+          for (int l = 0; l < NL; ++l) {
+            tm[l].x += kx * ph[l];
+            tm[l].y += ky * ph[l];
+          }
+          if constexpr (HARD) {
+            const T gx = pk.gcx * h4, gy = pk.gcy * h4;
+            const T *cl = cuf + r * NL * 3;
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                tc[d][l].x += gx * cl[l * 3 + d];
+                tc[d][l].y += gy * cl[l * 3 + d];
+              }
+          }
+        }
+      }
+      // lanes q and q + 16 hold the two halves of the same target point
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        tm[l].x += __shfl_xor_sync(0xffffffffu, tm[l].x, 16);
+        tm[l].y += __shfl_xor_sync(0xffffffffu, tm[l].y, 16);
+      }
+      if constexpr (HARD) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int l = 0; l < NL; ++l) {
+            tc[d][l].x += __shfl_xor_sync(0xffffffffu, tc[d][l].x, 16);
+            tc[d][l].y += __shfl_xor_sync(0xffffffffu, tc[d][l].y, 16);
+          }
+      }
+      if (half == 0 && q < nq) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) Tm[q * NL + l] = tm[l];
+        if constexpr (HARD) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) Tc[(d * nq + q) * NL + l] = tc[d][l];
+        }
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < NL * NL; i += 32) {
+      const int k = i / NL, l = i % NL;
+      T ax = 0, ay = 0;
+      for (int q = 0; q < nq; ++q) {
+        const T ph = phe[q * NL + k];
+        const TV t = Tm[q * NL + l];
+        ax += ph * t.x;
+        ay += ph * t.y;
+        if constexpr (HARD) {
+          const T *ck = cue + (q * NL + k) * 3;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const TV c = Tc[(d * nq + q) * NL + l];
+            ax += ck[d] * c.x;
+            ay += ck[d] * c.y;
+          }
+        }
+      }
+      const int row = leaf_local(ixe, iye, k / p1, k % p1, A.b, A.nL1);
+      const int col = leaf_local(ixf, iyf, l / p1, l % p1, A.b, A.nL1);
+      if (smem_block) {
+        BA *dst = Bs + (size_t)col * A.nL + row;
+        atomicAdd(&dst->x, ax);
+        atomicAdd(&dst->y, ay);
+      } else {
+        block_add(Bg, A.nL, row, col, cmk((double)ax, (double)ay));
+      }
+    }
+    __syncwarp();
+  }
+  if (smem_block) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nL * A.nL; i += blockDim.x) {
+      const BA v = Bs[i];
+      atomicAdd(&Bg[i].x, (double)v.x);
+      atomicAdd(&Bg[i].y, (double)v.y);
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------------------------
 // touching element pairs: regularising transforms (identical 8, common edge 6, common vertex 4
 // regions) with the canonical position given by the square symmetries (Te, Tf) found on the host.
@@ -448,11 +619,11 @@ __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;
   extern __shared__ double smd[];
   const int nloc = A.nloc, p1 = A.p + 1, ch = S.ch, hard = A.hard;
-  // shared (SingLayout): per point S3[ch][3] (w k(x,y), w k(y,x), w gc), the basis values psiO[ch][nloc]
-  // (and curls) of the side that is not grouped; per group T, T2 [nd][nloc] and U [nd][nloc][3]; all
-  // aliased by the column partials colp[2][nv][pg1][8] of the element geometries; then geo[2][nd][13]
-  // (x, d_s x, d_t x, n, |n| of the chunk's distinct points), the basis values (and curls) of the
-  // grouped side's distinct points, the two element nets
+  // shared (SingLayout): (A) the column partials colp[2][nv][pg1][8] of the element geometries, then per
+  // point S3[ch][3] (w k(x,y), w k(y,x), w gc) and the basis values psiO[ch][nloc] (and curls) of the side
+  // that is not grouped; (B) geo[2][nd][13] (x, d_s x, d_t x, n, |n| of the chunk's distinct points), then
+  // per group T, T2 [nd][nloc] and U [nd][nloc][3]; (C) the basis values (and curls) of the grouped
+  // side's distinct points; the two element nets
   double *colp = smd;
   double2 *S3 = reinterpret_cast<double2 *>(smd + S.L.s3);
   double *psiO = smd + S.L.psi, *curO = smd + S.L.cur;
@@ -782,13 +953,30 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
                                                     (double *)A.tab_cuw);
       note_launch();
     }
-    const size_t per = (size_t)near_regular_scratch(nq, nloc, S.hard) * tsz;
+    // the fused kernel keeps Tm (and Tc) in registers: p <= 2, and p = 3 for sound-soft
+    const bool fused = nloc == 4 || nloc == 9 || (nloc == 16 && !S.hard);
+    const size_t per = (size_t)(fused ? near_fused_scratch(nq, nloc, S.hard) : near_regular_scratch(nq, nloc, S.hard)) * tsz;
     const size_t bsm = (size_t)S.nL * S.nL * 2 * tsz;
     const int smem_block = bsm <= 48 * 1024 ? 1 : 0;
     int warps = 8;
     while (warps > 1 && per * warps + (smem_block ? bsm : 0) > 200 * 1024) warps /= 2;
     size_t smem = per * warps + (smem_block ? bsm : 0);
-    if (f32) {
+    auto go = [&](auto kfn) {
+      IGA_CUDA(set_max_dynamic_smem(kfn, smem));
+      kfn<<<nblk, 32 * warps, smem, st>>>(A, smem_block);
+    };
+    if (fused) {
+      const bool h = S.hard;
+      if (f32) {
+        if (nloc == 4) h ? go(k_near_regular_f<float, 4, true>) : go(k_near_regular_f<float, 4, false>);
+        else if (nloc == 9) h ? go(k_near_regular_f<float, 9, true>) : go(k_near_regular_f<float, 9, false>);
+        else go(k_near_regular_f<float, 16, false>);
+      } else {
+        if (nloc == 4) h ? go(k_near_regular_f<double, 4, true>) : go(k_near_regular_f<double, 4, false>);
+        else if (nloc == 9) h ? go(k_near_regular_f<double, 9, true>) : go(k_near_regular_f<double, 9, false>);
+        else go(k_near_regular_f<double, 16, false>);
+      }
+    } else if (f32) {
       IGA_CUDA(set_max_dynamic_smem(k_near_regular_t<float>, smem));
       k_near_regular_t<float><<<nblk, 32 * warps, smem, st>>>(A, smem_block);
     } else {

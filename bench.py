@@ -802,7 +802,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
                 "singular_groups": info["n_singular_groups"],
-                "m2l": m2l_roof}}
+                "m2l": m2l_roof}
     lat = sorted(step_ms)
     value = R * args.steps * world / (total_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

@@ -90,6 +90,10 @@ DEFAULT = "deformed_soft_6x256x256_p2_k50-60_8dirs"
 PRECISIONS = {}                              # name -> igabem_precision (filled once the binding is loaded)
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic: soft 40 flops, hard 52 per pair of samples
 FLOPS_PER_MAC = 8                            # one complex multiply-add
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_near_singular launch per 4-D point,
+# from one ncu capture of the small sweep case (29.4 + 36.4 MB for 92,130,000 points); the traffic of a
+# launch grows with its points (block writes per pair, rule and net reads per chunk)
+SINGULAR_DRAM_BYTES_PER_POINT = 65.762560e6 / 92130000
 
 
 def hbm_peak_gbs():
@@ -795,7 +799,9 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                     "peak_source": "measured FP32 FMA rate (igabem_measure_peaks, this run)"}
     roofline = {"bound": "alu", "kernel": "k_near_singular (FP64)", "achieved": sing_ach,
                 "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": sing_ach / peaks["fp64_tflops"],
-                "traffic": None,
+                "traffic": SINGULAR_DRAM_BYTES_PER_POINT * info["n_singular_points"],
+                "traffic_source": "DRAM bytes per 4-D point of one ncu capture of the small sweep case, "
+                                  "times this launch's points",
                 "peak_source": "measured FP64 FMA rate (igabem_measure_peaks, this run; 2 flops per FMA)",
                 "algorithmic_flops_per_setup": sing_flops, "avg_ms_per_setup": sing_ms,
                 "singular_points": info["n_singular_points"],

@@ -115,15 +115,23 @@ def singular_flops(info, p, hard, pg=4):
     curls 6 more for sound-hard) and the group sums (the kernel value of each orientation times each
     function, 8 per function; sound-hard adds w gc times the curls, 12).  Per group of points sharing an
     element point: that side's B-splines (and curls) and the accumulation of the (p+1)^2 x (p+1)^2 entries
-    of both blocks (8 per entry; sound-hard 16 more for the curl products)."""
+    of both blocks (8 per entry; sound-hard 16 more for the curl products).  Identical sound-soft pairs
+    summed in factorised form (groups of ns^2 points, ns = 5): per point the kernel alone; per group the
+    univariate basis values (4 ns of them, 5 (p+1) each), the inner sums (ns (p+1)^2 ns, 10 flops each:
+    the product of two basis values and two complex-by-real multiply-adds) and the outer sums
+    ((p+1)^4 ns, 10 each)."""
     n = (p + 1) ** 2
+    ns = 5
     per_column = 2 * (pg + 1) ** 2 * 4 * 2
     per_geo_point = (pg + 1) * 4 * 3 * 2 + 30
     basis = 5 * n + (6 * n if hard else 0)
     per_point = 60 + basis + 8 * n + (12 * n if hard else 0)
     per_group = basis + n * n * (8 + (16 if hard else 0))
+    fact = info.get("n_singular_factored_points", 0)
+    per_fact_group = 4 * ns * 5 * (p + 1) + ns * n * ns * 10 + n * n * ns * 10
     return (info["n_singular_geo_columns"] * per_column + info["n_singular_geo_points"] * per_geo_point
-            + info["n_singular_points"] * per_point + info["n_singular_groups"] * per_group)
+            + (info["n_singular_points"] - fact) * per_point + fact * 60
+            + info["n_singular_groups"] * per_group + fact / ns ** 2 * per_fact_group)
 
 
 def mie_soft_far_field(kappa, xhat, d=(0.0, 0.0, 1.0)):
@@ -808,6 +816,7 @@ def run_sweep_steps(args, wl, B, inputs, geom, patches, stream, flush, local, wo
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
                 "singular_groups": info["n_singular_groups"],
+                "singular_factored_points": info["n_singular_factored_points"],
                 "m2l": m2l_roof}
     lat = sorted(step_ms)
     value = R * args.steps * world / (total_ms / 1e3)
@@ -1022,6 +1031,7 @@ def main():
                 "singular_geometry_points": info["n_singular_geo_points"],
                 "singular_geometry_columns": info["n_singular_geo_columns"],
                 "singular_groups": info["n_singular_groups"],
+                "singular_factored_points": info["n_singular_factored_points"],
                 "m2l": m2l_alu_roofline("k_m2l_rows<double>" if fp64 else "k_m2l_rows<float>", far, Q, hard,
                                         len(dirs), m2l_ms, peaks, fp64)}
 

@@ -135,6 +135,9 @@ typedef struct {
   long n_singular_groups;      /* groups of 4-D points sharing the point of one element (per chunk, on the
                                   side with fewer distinct points): block entries are accumulated once
                                   per group */
+  long n_singular_factored_points; /* of the 4-D points, those of identical sound-soft pairs summed in
+                                      factorised form (groups of gauss_singular^2 points with tensor
+                                      structure: univariate basis values, two nested sums) */
 } igabem_info;
 
 typedef struct {

@@ -39,7 +39,7 @@ class igabem_info(ctypes.Structure):
                 ("setup_ms", c_double), ("host_setup_ms", c_double), ("n_singular_points", c_long),
                 ("n_levels", c_int), ("level_q", c_int * 24), ("level_far", c_long * 24),
                 ("n_singular_geo_points", c_long), ("n_singular_geo_columns", c_long),
-                ("n_singular_groups", c_long)]
+                ("n_singular_groups", c_long), ("n_singular_factored_points", c_long)]
 
 
 class igabem_solve_info(ctypes.Structure):

@@ -556,6 +556,7 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   I.n_singular_geo_points = 0;
   I.n_singular_geo_columns = 0;
   I.n_singular_groups = 0;
+  I.n_singular_factored_points = 0;
   // per rule, summed over the chunks a pair integrates: distinct x1, x2, x-points, y1, y2, y-points,
   // and the groups of the side with fewer distinct points
   long chunk_sum[3][7] = {};
@@ -575,7 +576,8 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
     const int vse = ((te & 1) != (te >= 4)) ? 0 : 1, vsf = ((tf & 1) != (tf >= 4)) ? 0 : 1;
     I.n_singular_geo_points += chunk_sum[r][2] + chunk_sum[r][5];
     I.n_singular_geo_columns += chunk_sum[r][vse] + chunk_sum[r][3 + vsf];
-    I.n_singular_groups += chunk_sum[r][6];
+    if (r == 0 && S.sing_fact) I.n_singular_factored_points += (long)S.r_id.w.size() / 2;
+    else I.n_singular_groups += chunk_sum[r][6];
   }
   I.n_levels = S.L + 1;
   for (int l = 0; l <= S.L && l < 24; ++l) {

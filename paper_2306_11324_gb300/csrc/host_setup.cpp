@@ -536,6 +536,10 @@ void build_setup(const std::vector<Patch> &patches, const igabem_options &opt, H
       for (Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) share_tables(*r, chosen, S.sing_nv, S.sing_nd);
     }
     if (!chosen) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
+    // the factorised identical-pair sums need whole ns^2 groups per chunk and room for the univariate
+    // basis values (4 ch (p+1) / ns doubles) where the grouped side's basis values go
+    S.sing_fact = !S.hard && S.sing_ch % (S.ns * S.ns) == 0 &&
+                  4 * (S.sing_ch / S.ns) * (p + 1) <= S.sing_nd * S.nloc && S.sing_ch / S.ns <= S.sing_nd;
   }
 
   // --- ansatz space: knot vector Xi_{p,m}, tables per element column ---

@@ -141,6 +141,7 @@ struct HostSetup {
   // quadrature
   int ng = 4, ns = 5;
   int sing_ch = 128, sing_nv = 0, sing_nd = 0;  // singular chunk; most distinct coordinates / points in one
+  bool sing_fact = false;  // identical sound-soft pairs summed in factorised form (k_near_singular)
   std::vector<double> gx, gw;          // Gauss rule on [0,1] (ng points)
   Rule4 r_id, r_edge, r_vert;
   // ansatz basis: per element column ix, Gauss point q, function a: value and d/ds

@@ -573,6 +573,8 @@ struct SingArgs {
   int rule_n[3];
   const unsigned char *share[3];  // per kind: sharing tables over chunks of ch points
   int ch, nv, nd, pg1;            // chunk; most distinct coordinates / points of a chunk; max degree + 1
+  int ns;                         // Gauss points per transformed variable
+  int fact;                       // sum factorisation of the identical pairs' sound-soft blocks
   SingLayout L;                   // shared-memory layout (offsets in doubles)
 };
 
@@ -662,6 +664,13 @@ __global__ void k_near_singular(SingArgs S) {
     // the side whose points repeat most in this chunk is grouped: sum_t s_t phi_k(x_t) psi_l(y_t) =
     // sum_g phi_k(x_g) sum_{t in g} s_t psi_l(y_t) (grouping by x; by y with the roles exchanged)
     const int gs = H[5] < H[2] ? 1 : 0, ng = H[gs ? 5 : 2];
+    // identical pairs, sound-soft: in each group of ns^2 consecutive points (Gauss indices c, d of the
+    // last two variables) x = (X1(c), X2(d)) and y = (Y1(c), Y2(d)), and the basis functions are tensor
+    // products phi_k = u_k1 v_k2, so sum_t s_t phi_k(x_t) phi_l(y_t) =
+    // sum_c u_k1(X1c) u_l1(Y1c) sum_d s(c, d) v_k2(X2d) v_l2(Y2d) (sum factorisation)
+    const bool fac = S.fact && kind == 0 && !hard;
+    const int ns = S.ns, ns2 = ns * ns, pb = A.p + 1;
+    const int ngrp = fac ? (cn + ns2 - 1) / ns2 : 0;
     const unsigned char *goff = H + 6 + 6 * ch + gs * (ch + 1), *gmem = H + 6 + 6 * ch + 2 * (ch + 1) + gs * ch;
     // geometry, step 1: for each distinct second local coordinate v of the chunk and each row i of the
     // net, the row contracted with the Bernstein polynomials of v and their derivatives
@@ -739,7 +748,7 @@ __global__ void k_near_singular(SingArgs S) {
         g[10] = nn[1];
         g[11] = nn[2];
         g[12] = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-        if ((int)sf == gs)
+        if ((int)sf == gs && !fac)
           basis_curl_at(A, sf ? ixf : ixe, sf ? iyf : iye, u, v, fs, ft, phiG + (size_t)k * nloc,
                         hard ? curG + (size_t)k * nloc * 3 : nullptr);
       }
@@ -767,16 +776,56 @@ __global__ void k_near_singular(SingArgs S) {
       S3[3 * t] = cscale(pk.ks, w);
       S3[3 * t + 1] = cscale(kyx, w);
       S3[3 * t + 2] = cscale(pk.gc, w);  // gc(y, x) = gc(x, y)
+      if (fac) continue;
       const double *go = gs ? ge : gf;
       if (gs) basis_curl_at(A, ixe, iye, ue, ve, go + 3, go + 6, psiO + (size_t)t * nloc,
                             hard ? curO + (size_t)t * nloc * 3 : nullptr);
       else basis_curl_at(A, ixf, iyf, uf, vf, go + 3, go + 6, psiO + (size_t)t * nloc,
                          hard ? curO + (size_t)t * nloc * 3 : nullptr);
     }
+    if (fac) {
+      // univariate basis values per group: B1[g][w][j][a], w = 0: u_a(X1 at c = j), 1: v_a(X2 at d = j),
+      // 2: u_a(Y1 at c = j), 3: v_a(Y2 at d = j)
+      for (int w = threadIdx.x; w < ngrp * 4 * ns; w += blockDim.x) {
+        const int g = w / (4 * ns), wh = (w / ns) % 4, j = w % ns;
+        const int ip = c0 + g * ns2 + ((wh & 1) ? j : j * ns);
+        const double u = R[wh * npt + ip];
+        const int ix = wh == 0 ? ixe : wh == 1 ? iye : wh == 2 ? ixf : iyf;
+        double Bu[8];
+        bernstein_all(A.p, u, Bu, nullptr);
+        double *o = phiG + ((size_t)(g * 4 + wh) * ns + j) * pb;
+        for (int a = 0; a < pb; ++a) {
+          double v = 0;
+          for (int c = 0; c < pb; ++c) v += A.ext1[(ix * pb + a) * pb + c] * Bu[c];
+          o[a] = v;
+        }
+      }
+    }
     __syncthreads();
     // group sums: T[g][i] = sum_{t in g} w k(x_t, y_t) psiO_i(t), T2 the same with k(y, x), and for
     // sound-hard U[g][i] = sum_{t in g} w gc(t) curlO_i(t)
-    for (int w = threadIdx.x; w < ng * nloc; w += blockDim.x) {
+    if (fac) {
+      // U[g][c][k2][l2] = sum_d s(c, d) v_k2(X2d) v_l2(Y2d), and U2 with the other orientation
+      const int pp = pb * pb;
+      for (int w = threadIdx.x; w < ngrp * ns * pp; w += blockDim.x) {
+        const int g = w / (ns * pp), c = (w / pp) % ns, k2 = (w % pp) / pb, l2 = w % pb;
+        const double *bx2 = phiG + (size_t)(g * 4 + 1) * ns * pb, *by2 = phiG + (size_t)(g * 4 + 3) * ns * pb;
+        double2 u1 = cmk(0, 0), u2 = cmk(0, 0);
+        for (int d = 0; d < ns; ++d) {
+          const int t = g * ns2 + c * ns + d;
+          if (t >= cn) break;
+          const double fv = bx2[d * pb + k2] * by2[d * pb + l2];
+          const double2 s1 = S3[3 * t], s2 = S3[3 * t + 1];
+          u1.x = fma(s1.x, fv, u1.x);
+          u1.y = fma(s1.y, fv, u1.y);
+          u2.x = fma(s2.x, fv, u2.x);
+          u2.y = fma(s2.y, fv, u2.y);
+        }
+        T[w] = u1;
+        T2[w] = u2;
+      }
+    }
+    for (int w = threadIdx.x; w < (fac ? 0 : ng * nloc); w += blockDim.x) {
       const int g = w / nloc, i = w % nloc;
       double2 t1 = cmk(0, 0), t2 = cmk(0, 0), u0 = cmk(0, 0), u1 = cmk(0, 0), u2 = cmk(0, 0);
       for (int m = goff[g]; m < goff[g + 1]; ++m) {
@@ -817,7 +866,22 @@ __global__ void k_near_singular(SingArgs S) {
       const int k = i / nloc, l = i % nloc;
       const int kG = gs ? l : k, kO = gs ? k : l;
       double2 a = acc[slot], b = accb[slot];
-      if (hard) {
+      if (fac) {
+        // a += sum_g sum_c u_k1(X1c) u_l1(Y1c) U[g][c][k2][l2]
+        const int k1 = k / pb, k2 = k % pb, l1 = l / pb, l2 = l % pb, pp = pb * pb;
+        for (int g = 0; g < ngrp; ++g) {
+          const double *bx1 = phiG + (size_t)(g * 4) * ns * pb, *by1 = phiG + (size_t)(g * 4 + 2) * ns * pb;
+          for (int c = 0; c < ns; ++c) {
+            const double fu = bx1[c * pb + k1] * by1[c * pb + l1];
+            const int iu = (g * ns + c) * pp + k2 * pb + l2;
+            const double2 u1 = T[iu], u2 = T2[iu];
+            a.x = fma(fu, u1.x, a.x);
+            a.y = fma(fu, u1.y, a.y);
+            b.x = fma(fu, u2.x, b.x);
+            b.y = fma(fu, u2.y, b.y);
+          }
+        }
+      } else if (hard) {
         for (int g = 0; g < ng; ++g) {
           const double ph = phiG[g * nloc + kG];
           const double *cg = curG + (g * nloc + kG) * 3;
@@ -1004,6 +1068,8 @@ void launch_near_field(const DeviceProblem &d, const HostSetup &S, const igabem_
   SA.pg1 = pg1;
   for (int k = 0; k < 3; ++k) SA.share[k] = d.share[k];
   SA.L = sing_layout(S.sing_ch, S.nloc, S.hard, S.sing_nv, S.sing_nd, pg1);
+  SA.ns = S.ns;
+  SA.fact = S.sing_fact ? 1 : 0;
   const size_t smem = (size_t)SA.L.total * sizeof(double);
   if (smem > 227 * 1024) fail(IGABEM_EINVAL, "gauss_singular and degree_p too large for the singular kernel");
   const int nslot = (S.nloc * S.nloc + 127) / 128;

@@ -91,9 +91,9 @@ PRECISIONS = {}                              # name -> igabem_precision (filled 
 FLOPS_PER_SAMPLE = {False: 40, True: 52}     # FP32 M2L kernel-sample arithmetic: soft 40 flops, hard 52 per pair of samples
 FLOPS_PER_MAC = 8                            # one complex multiply-add
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_near_singular launch per 4-D point,
-# from one ncu capture of the small sweep case (29.4 + 36.4 MB for 92,130,000 points); the traffic of a
+# from one ncu capture of the small sweep case (29.6 + 22.7 MB for 92,130,000 points); the traffic of a
 # launch grows with its points (block writes per pair, rule and net reads per chunk)
-SINGULAR_DRAM_BYTES_PER_POINT = 65.762560e6 / 92130000
+SINGULAR_DRAM_BYTES_PER_POINT = 52.274424e6 / 92130000
 
 
 def hbm_peak_gbs():

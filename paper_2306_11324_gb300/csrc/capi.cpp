@@ -359,6 +359,7 @@ igabem_problem *problem_plan(igabem_geom *geom, const igabem_options *opt) {
     size_t gst = (size_t)S.E * nq;
     total += 13 * ((gst * sizeof(double) + 255) & ~size_t(255));
     total += bytes_of(S.phi1) + bytes_of(S.dphi1) + bytes_of(S.ext1) + bytes_of(S.gx) + bytes_of(S.gw);
+    total += bytes_of(std::vector<float>(S.phi1.size())) + bytes_of(std::vector<float>((size_t)nq));
     total += 3 * 256 + 5 * nrule * sizeof(double);
     for (const Rule4 *r : {&S.r_id, &S.r_edge, &S.r_vert}) total += (r->share.size() + 255) & ~size_t(255);
     total += bytes_of(S.touch) + bytes_of(S.touch_blk) + bytes_of(S.sing) + bytes_of(S.x2g) + bytes_of(S.g2x_ptr) +
@@ -444,6 +445,14 @@ void problem_materialize(igabem_problem *P, cudaStream_t st) {
   d.ext1 = upload(A, S.ext1, st);
   d.gx = upload(A, S.gx, st);
   d.gw = upload(A, S.gw, st);
+  {
+    const std::vector<float> phi1f(S.phi1.begin(), S.phi1.end());
+    std::vector<float> gwq((size_t)nq);
+    for (int q = 0; q < nq; ++q) gwq[q] = (float)(S.gw[q / S.ng] * S.gw[q % S.ng] * S.h * S.h);
+    d.phi1f = upload(A, phi1f, st);
+    d.gwqf = upload(A, gwq, st);
+    IGA_CUDA(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+  }
   for (int k = 0; k < 3; ++k) {
     d.rule[k] = upload(A, rules[k], st);
     d.rule_n[k] = (int)R4[k]->w.size();

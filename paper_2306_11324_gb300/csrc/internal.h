@@ -254,6 +254,7 @@ struct DeviceProblem {
   double *ebez;
   double *gpx, *gpn, *gpa, *gfs, *gft;    // Gauss-point geometry: [3][E*ng*ng] or [E*ng*ng]
   double *phi1, *dphi1, *ext1, *gx, *gw;
+  float *phi1f, *gwqf;  // FP32 copies: B-spline values at the Gauss points, gw[q1] gw[q2] h^2 per point
   double *rule[3];                          // singular rules (5 arrays each, SoA)
   unsigned char *share[3];                  // their sharing tables (Rule4::share)
   int rule_n[3];

@@ -468,13 +468,69 @@ __global__ void k_gauss_channels(Dims D, Tables T, const double2 *__restrict__ x
 
 constexpr int BAND_COLS = 16;
 
+// FP32 forms for sound-soft problems in the mixed precisions (one channel, the density): the values at
+// every Gauss point times the quadrature weight from the FP32 copy of the patch-wise coefficients (for
+// k_p2m_band), and the band bottoms' fields tested against the basis (from k_l2p_band's FP32 output).
+// GB300's FP64 pipe would bound the FP64 forms.
+__global__ void k_gauss_channels32(Dims D, const float *__restrict__ phi1f, const float *__restrict__ gwq,
+                                   const float2 *__restrict__ xX32, float2 *__restrict__ F) {
+  const int p1 = D.p + 1;
+  GRID_STRIDE(o, D.E * D.nq * D.R) {
+    const long e = o / (D.nq * D.R);
+    const int q = int((o / D.R) % D.nq), r = int(o % D.R);
+    const int q1 = q / D.ng, q2 = q % D.ng;
+    const int j = int(e / ((long)D.n1 * D.n1)), ix = int((e / D.n1) % D.n1), iy = int(e % D.n1);
+    float ux = 0.f, uy = 0.f;
+    for (int ka = 0; ka < p1; ++ka) {
+      const float bs = phi1f[(ix * D.ng + q1) * p1 + ka];
+      for (int kb = 0; kb < p1; ++kb) {
+        const float w = bs * phi1f[(iy * D.ng + q2) * p1 + kb];
+        const float2 xv = xX32[xindex(D, j, ix + ka, iy + kb) * D.R + r];
+        ux += w * xv.x;
+        uy += w * xv.y;
+      }
+    }
+    const float w = gwq[q];
+    F[o] = make_float2(ux * w, uy * w);
+  }
+}
+
+__global__ void k_l2p_test32(Dims D, const float *__restrict__ phi1f, const float *__restrict__ gwq,
+                             const float2 *__restrict__ g, double2 *__restrict__ yleaf) {
+  const int nlL = 1 << D.L, e1 = 1 << D.b, p1 = D.p + 1;
+  const long nleaf = (long)D.np * nlL * nlL;
+  GRID_STRIDE(o, nleaf * D.nL * D.R) {
+    long t = o / (D.nL * D.R);
+    int i = int((o / D.R) % D.nL), r = int(o % D.R);
+    int j = int(t / (nlL * nlL)), cx = int((t / nlL) % nlL), cy = int(t % nlL);
+    int i1 = cx * e1 + i / D.nL1, i2 = cy * e1 + i % D.nL1;
+    float ax = 0.f, ay = 0.f;
+    for (int ix = max(cx * e1, i1 - D.p); ix <= min(cx * e1 + e1 - 1, i1); ++ix)
+      for (int iy = max(cy * e1, i2 - D.p); iy <= min(cy * e1 + e1 - 1, i2); ++iy) {
+        const long e = ((long)j * D.n1 + ix) * D.n1 + iy;
+        const int ka = i1 - ix, kb = i2 - iy;
+        for (int q1 = 0; q1 < D.ng; ++q1) {
+          const float bs = phi1f[(ix * D.ng + q1) * p1 + ka];
+          for (int q2 = 0; q2 < D.ng; ++q2) {
+            const int q = q1 * D.ng + q2;
+            const float w = gwq[q] * bs * phi1f[(iy * D.ng + q2) * p1 + kb];
+            const float2 gv = g[(e * D.nq + q) * D.R + r];
+            ax += w * gv.x;
+            ay += w * gv.y;
+          }
+        }
+      }
+    yleaf[o] = make_double2(yleaf[o].x + (double)ax, yleaf[o].y + (double)ay);
+  }
+}
+
 // P2M of a band bottom on level l (q = D.q): xhat[t][a1 q + a2][cr] = sum over the cluster's Gauss
 // grid (i1, i2) of LG(i1, a1) LG(i2, a2) F(i1, i2, cr), separably: per row i1 of the grid
 // Z[a2] = sum_i2 LG(i2, a2) F(i1, i2), then xhat[a1][a2] += LG(i1, a1) Z[a2].  One block per
 // (cluster, 16 columns).
-template <class T>
+template <class T, class FT>
 __global__ void __launch_bounds__(256) k_p2m_band(Dims D, int l, const double *__restrict__ LG,
-                                                  const double2 *__restrict__ F, double2 *__restrict__ xhat) {
+                                                  const FT *__restrict__ F, double2 *__restrict__ xhat) {
   using V = typename CV<T>::type;
   extern __shared__ __align__(16) unsigned char smb[];
   const int q = D.q, Q = q * q, ne = 1 << (D.m - l), n1d = ne * D.ng;
@@ -498,7 +554,7 @@ __global__ void __launch_bounds__(256) k_p2m_band(Dims D, int l, const double *_
       V v;
       v.x = v.y = 0;
       if (col < cw) {
-        const double2 f = F[((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col];
+        const FT f = F[((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col];
         v.x = (T)f.x;
         v.y = (T)f.y;
       }
@@ -543,9 +599,9 @@ __global__ void __launch_bounds__(256) k_p2m_band(Dims D, int l, const double *_
 // L2P of a band bottom on level l: G(i1, i2, cr) += sum_a1 LG(i1, a1) sum_a2 LG(i2, a2) yhat[t][a1 q + a2][cr]
 // at every Gauss point of the cluster (G[e][q][cr], tested against the basis by k_l2p_test), separably:
 // per grid row i1, U[a2] = sum_a1 LG(i1, a1) yhat[a1][a2], then G(i1, i2) += sum_a2 LG(i2, a2) U[a2].
-template <class T>
+template <class T, class FT>
 __global__ void __launch_bounds__(256) k_l2p_band(Dims D, int l, const double *__restrict__ LG,
-                                                  const double2 *__restrict__ yhat, double2 *__restrict__ G) {
+                                                  const double2 *__restrict__ yhat, FT *__restrict__ G) {
   using V = typename CV<T>::type;
   extern __shared__ __align__(16) unsigned char smb[];
   const int q = D.q, Q = q * q, ne = 1 << (D.m - l), n1d = ne * D.ng;
@@ -595,8 +651,9 @@ __global__ void __launch_bounds__(256) k_l2p_band(Dims D, int l, const double *_
       }
       const int iy = cy * ne + i2 / D.ng, g2 = i2 % D.ng;
       const long e = ((long)j * D.n1 + ix) * D.n1 + iy;
-      double2 *dst = G + ((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col;
-      *dst = make_double2(dst->x + (double)sum.x, dst->y + (double)sum.y);
+      FT *dst = G + ((e * D.nq) + g1 * D.ng + g2) * D.CR + c0 + col;
+      dst->x += (decltype(dst->x))sum.x;
+      dst->y += (decltype(dst->y))sum.y;
     }
   }
 }
@@ -692,26 +749,35 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
     bool bands = false;  // levels whose expansions come from the Gauss points directly
     for (int l = S.lmin; l < S.L; ++l) bands = bands || S.lev[l].band_bottom;
     double2 *gq = reinterpret_cast<double2 *>(d.gq);
+    // sound-soft mixed precision: the band channels in FP32 (the same buffer, float2 entries)
+    const bool f32s = f32 && !S.hard;
+    float2 *gq32 = reinterpret_cast<float2 *>(d.gq);
     auto band_launch = [&](int l, bool l2p) {
       const Dims Dl = level_dims(l);
       const int n1d = (1 << (S.m - l)) * S.ng;
       const size_t smem = band_smem(n1d, Dl.q, f32, l2p);
       dim3 grid(S.lev[l].n, (D.CR + BAND_COLS - 1) / BAND_COLS);
       if (l2p) {
-        if (f32) {
-          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<float>, smem));
-          k_l2p_band<float><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
+        if (f32s) {
+          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<float, float2>, smem));
+          k_l2p_band<float, float2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq32);
+        } else if (f32) {
+          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<float, double2>, smem));
+          k_l2p_band<float, double2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
         } else {
-          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<double>, smem));
-          k_l2p_band<double><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
+          IGA_CUDA(set_max_dynamic_smem(k_l2p_band<double, double2>, smem));
+          k_l2p_band<double, double2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], Y(l), gq);
         }
       } else {
-        if (f32) {
-          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<float>, smem));
-          k_p2m_band<float><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
+        if (f32s) {
+          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<float, float2>, smem));
+          k_p2m_band<float, float2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq32, X(l));
+        } else if (f32) {
+          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<float, double2>, smem));
+          k_p2m_band<float, double2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
         } else {
-          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<double>, smem));
-          k_p2m_band<double><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
+          IGA_CUDA(set_max_dynamic_smem(k_p2m_band<double, double2>, smem));
+          k_p2m_band<double, double2><<<grid, 256, smem, st>>>(Dl, l, d.LGl[l], gq, X(l));
         }
       }
       note_launch();
@@ -726,8 +792,11 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
         note_launch();
       }
       if (bands) {
-        k_gauss_channels<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX),
-                                                                       gq);
+        if (f32s)
+          k_gauss_channels32<<<grid_for(D.E * D.nq * D.R), 256, 0, st>>>(D, d.phi1f, d.gwqf, d.xX32, gq32);
+        else
+          k_gauss_channels<<<grid_for(D.E * D.nq * D.CR), 256, 0, st>>>(D, T, reinterpret_cast<const double2 *>(d.xX),
+                                                                         gq);
         note_launch();
       }
     }
@@ -807,7 +876,11 @@ void launch_matvec(const DeviceProblem &d, const HostSetup &S, const igabem_opti
       Phase ph(d.prof, IGABEM_PH_L2P, st);
       if (f32) to_f32(d.yhat[S.L], d.y32, (long)nleaf * D.Q * D.CR, st);
       if (bands) {  // the band bottoms' fields at the Gauss points, tested (before gq is reused below)
-        k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, gq, reinterpret_cast<double2 *>(d.yleaf));
+        if (f32s)
+          k_l2p_test32<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, d.phi1f, d.gwqf, gq32,
+                                                                          reinterpret_cast<double2 *>(d.yleaf));
+        else
+          k_l2p_test<<<grid_for((long)nleaf * D.nL * R), 256, 0, st>>>(D, T, gq, reinterpret_cast<double2 *>(d.yleaf));
         note_launch();
       }
       if (leafk) {

@@ -74,18 +74,3 @@ def test_64_direction_sound_hard_workload_against_oracle_rows(prec):
     tensor-core and FP32 M2L precisions against the oracle's rows."""
     _check("deformed_hard_6x64x64_p2_k20", prec, single_column=False)
 
-
-def test_large_scatterer_workload_against_oracle_rows():
-    """The large single scatterer (deformed sphere, 256 x 256 elements per patch, 399384 unknowns,
-    kappa = 50, 8 columns) in the configuration the benchmark times: mixed precision, level-adaptive q
-    (7 .. 12), stored FP32 coupling blocks.  The per-level interpolation orders and the far-pair count
-    equal the oracle's tree, and the sampled rows of the product its mode-B rows."""
-    c, rows, ref, N, n_far = golden.load("deformed_soft_6x256x256_p2_k50")
-    prob, info = _problem(c, "mixed", stored=1)
-    assert info["n_dofs"] == N and info["n_far_pairs"] == n_far
-    x = inputs.random_complex(N, seed=c["seed"], cols=c["cols"])
-    y = B.igabem_matvec(prob, x).reshape(N, -1)
-    err = np.abs(y[rows] - ref).max() / np.abs(ref).max()
-    print(f"large scatterer mixed/stored: level q {info['level_q']}, rel. error {err:.2e}")
-    assert err < TOL["mixed"]
-    B.igabem_problem_destroy(prob)

@@ -42,7 +42,9 @@ CASES = {
     "deformed_hard_6x64x64_p2_k20": dict(geometry="deformed", m=6, p=2, leaf=4, q=7, kappa=20.0, eta=0.05,
                                          hard=True, cap=6.0, cols=64, seed=2027, nrows=2),
     # the large single scatterer at the sweep's first kappa: deformed sphere, 256 x 256 elements per
-    # patch (399384 unknowns), kappa = 50, 8 columns, level-adaptive q (7 .. 12, capped admissibility)
+    # patch (399384 unknowns), kappa = 50, 8 columns, level-adaptive q (7 .. 12, capped admissibility).
+    # Not stored: two rows take the oracle more than four hours on one core (every far cluster's mode-B
+    # block of the row's element is formed); run it explicitly to produce the file
     "deformed_soft_6x256x256_p2_k50": dict(geometry="deformed", m=8, p=2, leaf=6, q=7, q_max=12, kappa=50.0,
                                            eta=50.0, hard=False, cap=6.0, cols=8, seed=2029, nrows=2),
 }
@@ -99,5 +101,5 @@ def load(name):
 
 
 if __name__ == "__main__":
-    for name in sys.argv[1:] or list(CASES):
+    for name in sys.argv[1:] or [c for c in CASES if c != "deformed_soft_6x256x256_p2_k50"]:
         make(name)

@@ -41,6 +41,11 @@ CASES = {
     # the 64-direction sound-hard workload: deformed sphere, 64 x 64 elements per patch, kappa = 20
     "deformed_hard_6x64x64_p2_k20": dict(geometry="deformed", m=6, p=2, leaf=4, q=7, kappa=20.0, eta=0.05,
                                          hard=True, cap=6.0, cols=64, seed=2027, nrows=2),
+    # the large scatterer's discretisation at 16 x 16 elements per patch: deformed multi-span sphere,
+    # sound-soft, kappa = 20, level-adaptive q (7 .. 12 under the kappa * diameter <= 6 cap)
+    "deformed_soft_m4_p2_q7-12_b2_k20_cap6": dict(geometry="deformed", m=4, p=2, leaf=2, q=7, q_max=12,
+                                                  kappa=20.0, eta=20.0, hard=False, cap=6.0, cols=8,
+                                                  seed=2103, nrows=6),
     # the large single scatterer at the sweep's first kappa: deformed sphere, 256 x 256 elements per
     # patch (399384 unknowns), kappa = 50, 8 columns, level-adaptive q (7 .. 12, capped admissibility).
     # Not stored: two rows take the oracle more than four hours on one core (every far cluster's mode-B

@@ -74,3 +74,11 @@ def test_64_direction_sound_hard_workload_against_oracle_rows(prec):
     tensor-core and FP32 M2L precisions against the oracle's rows."""
     _check("deformed_hard_6x64x64_p2_k20", prec, single_column=False)
 
+
+@pytest.mark.parametrize("prec,stored", [("fp64", 0), ("mixed", 1)])
+def test_large_scatterer_discretisation_at_16x16_against_oracle_rows(prec, stored):
+    """The large scatterer's discretisation at 16 x 16 elements per patch: deformed multi-span sphere,
+    sound-soft, kappa = 20, level-adaptive q (7 .. 12 under the kappa * diameter <= 6 cap, band-bottom
+    levels), 8 columns; FP64 with the blocks generated on the fly, and the benchmark's mixed precision
+    with stored FP32 blocks."""
+    _check("deformed_soft_m4_p2_q7-12_b2_k20_cap6", prec, single_column=False, stored=stored)

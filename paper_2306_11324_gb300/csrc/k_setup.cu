@@ -615,7 +615,11 @@ constexpr int SING_MAXACC = 19;  // (p+1)^4 / 128 rounded up for p <= 6
 
 // One block per unordered touching pair.  Points of the regularising rule of the pair's kind, mapped
 // by the canonical square symmetries; for edge and vertex pairs the same points also give the block
-// of (f, e) with the roles of x and y exchanged (the rules are symmetric under that exchange).
+// of (f, e) with the roles of x and y exchanged (the rules are symmetric under that exchange).  The
+// rule is taken in chunks of ch points (whole groups of ns^2): (1) the element nets contracted along
+// each distinct second coordinate of the chunk, (2) the geometry of each distinct element point,
+// (3) the kernel values per point, (4) sums over the points sharing an element point (or, for
+// identical sound-soft pairs, the factorised inner sums), (5) the block entries, one per thread.
 template <int NSLOT>
 __global__ void k_near_singular(SingArgs S) {
   const NearArgs &A = S.A;

@@ -298,10 +298,16 @@ class OracleSampler:
         self.wl = wl
         self.E = 6 * 4 ** wl["level_m"]
         self.N = 6 * (2 ** wl["level_m"] + wl["degree_p"]) ** 2
-        # one process per host core; on the largest meshes at most 4 (each process holds the oracle's
-        # Gauss-point tables of all E elements, ~2.5 kB per element)
+        # one process per host core, as many as half the host memory holds: each process keeps the
+        # oracle's mesh, space and Gauss-point tables of all E elements (~12.5 kB per element measured,
+        # 4.9 GB on 393216 elements)
         cores = os.cpu_count() or 1
-        self.cores = min(cores, 4) if self.E > 24576 else cores
+        try:
+            mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        except (ValueError, OSError, AttributeError):
+            mem = 64 << 30
+        per_proc = 12.5e3 * self.E + 0.5e9
+        self.cores = max(1, min(cores, int(0.5 * mem / per_proc)))
         self.n_trial = min(self.E, 6144)   # rows against at most 6144 trial elements, scaled to all E
         self.calls = 0
 
